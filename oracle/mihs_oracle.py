@@ -1,0 +1,484 @@
+"""Oracle for the Momentum Iterative Hessian Sketch (M-IHS) ridge solver.
+
+TEST INFRASTRUCTURE ONLY: plain numpy, fp64 unless a function says otherwise,
+no blocking or fusion beyond what the cited definition states.  Imported only
+by the tests, by ``__graft_entry__.smoke()`` and by the benchmark's CPU
+baseline / reference legs.  Shares no code with the CUDA path.
+
+Problem (Section 1, Eq. "intro"):  x* = argmin ½‖Ax−b‖² + (λ/2)‖x‖²,
+A ∈ R^{n×d}, n ≥ d, λ > 0  ⇒  x* = (AᵀA + λI)⁻¹ Aᵀ b, unique.
+
+Contents and the passage each follows:
+  philox4x32_10 ........ Salmon, Moraes, Dror, Shaw (SC'11), "Parallel random
+                          numbers: as easy as 1, 2, 3", Philox-4x32 with 10 rounds.
+  box_muller ........... Box & Muller (1958) on 24-bit uniforms.
+  sketch_* ............. the three families of Lemma 3 used here: (i) sparse
+                          embedding with one ±1 per column (CountSketch),
+                          (iii) SRHT, (iv) Gaussian with entries N(0, 1/m)
+                          (proof of Lemma 3), all with E[SᵀS] = I (Section 3.1,
+                          text after Algorithm 1).
+  exact_solve .......... the plain definition (Cholesky of AᵀA+λI, fp64).
+  svd_solve ............ closed form x* = Σ σᵢ²/(σᵢ²+λ)·(uᵢᵀb/σᵢ)·vᵢ (Eq. tsvdsol).
+  stat_dim ............. sd_λ(A) = Σ σᵢ²/(σᵢ²+λ) (Section 1; proof of Lemma 3).
+  gradient ............. g = Aᵀ(b − Ax) − λx (Algorithm 1, gradient step).
+  aab_solve ............ AAb_Solver (Algorithm 5, Section 3.6).
+  momentum_params ...... β = sd/m, α = (1−β)² (Corollary 3, Algorithm 1).
+  theorem1_params ...... β*, α*, rate of Theorem 1.
+  mihs ................. Algorithm 1 (M-IHS for n ≥ d).
+  heavy_ball ........... x⁺ = x + αΔ + β(x − x⁻) (Eq. mihs1).
+  characteristic_rate .. roots of u² − (1+β−αμ)u + β (proof of Theorem 1).
+
+Readings of the paper taken where it is silent or garbled (each is listed in
+the design notes with its justification):
+  * Algorithm 5 initial rotation sine is s = √λ/ρ̄ (the text's s_k = λ̄_k/ρ̄_k
+    with λ̄₁ = √λ), not √(λ/ρ̄).
+  * The Eq. after Algorithm 5's derivation is the *unsquared* residual norm.
+  * x⁰ = x¹ (no momentum on the first step).
+  * SRHT: S = √(n_p/m)·P·(H/√n_p)·D with n_p = 2^⌈log₂ n⌉ (zero-padded rows),
+    P sampling m rows uniformly with replacement.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11).  Vectorised over numpy uint64 arrays
+# that hold 32-bit words.
+# ---------------------------------------------------------------------------
+_MASK = np.uint64(0xFFFFFFFF)
+_PHILOX_M0 = np.uint64(0xD2511F53)
+_PHILOX_M1 = np.uint64(0xCD9E8D57)
+_PHILOX_W0 = np.uint64(0x9E3779B9)
+_PHILOX_W1 = np.uint64(0xBB67AE85)
+
+# Counter word 2 tags the stream a family draws from, so that no two uses of
+# one seed share a counter.
+TAG_GAUSSIAN = 0
+TAG_COUNTSKETCH = 1
+TAG_SRHT_SIGNS = 2
+TAG_SRHT_ROWS = 3
+
+GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
+FAMILY_NAMES = {GAUSSIAN: "gaussian", COUNTSKETCH: "countsketch", SRHT: "srht"}
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Ten Philox-4x32 rounds.  Each round multiplies words 0 and 2 by the two
+    round multipliers, and the new counter is (hi(M1·c2) ⊕ c1 ⊕ k0, lo(M1·c2),
+    hi(M0·c0) ⊕ c3 ⊕ k1, lo(M0·c0)); the key is bumped by the Weyl constants
+    before every round but the first."""
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & _MASK for c in (c0, c1, c2, c3))
+    c0, c1, c2, c3 = np.broadcast_arrays(c0, c1, c2, c3)
+    k0 = np.uint64(int(k0) & 0xFFFFFFFF)
+    k1 = np.uint64(int(k1) & 0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + _PHILOX_W0) & _MASK
+            k1 = (k1 + _PHILOX_W1) & _MASK
+        p0 = _PHILOX_M0 * c0
+        p1 = _PHILOX_M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return c0, c1, c2, c3
+
+
+def seed_key(seed: int):
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return seed & 0xFFFFFFFF, seed >> 32
+
+
+def box_muller(wa, wb):
+    """Two N(0,1) values from two 32-bit words: u1 = (⌊wa/2⁸⌋+1)·2⁻²⁴ ∈ (0,1],
+    u2 = ⌊wb/2⁸⌋·2⁻²⁴ ∈ [0,1) (both exact in fp32), r = √(−2 ln u1),
+    z = (r cos 2πu2, r sin 2πu2)."""
+    u1 = ((np.asarray(wa, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 1.0) * 2.0 ** -24
+    u2 = (np.asarray(wb, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)
+
+
+# ---------------------------------------------------------------------------
+# Sketch families (Lemma 3; E[SᵀS] = I after Algorithm 1)
+# ---------------------------------------------------------------------------
+def gaussian_sketch_rows(rows, n: int, m: int, seed: int) -> np.ndarray:
+    """Rows `rows` of the Gaussian sketch S ∈ R^{m×n}, S_ij ~ N(0, 1/m).
+    Entry (i, j) comes from Philox counter (⌊j/4⌋, i, TAG_GAUSSIAN, 0): the
+    four words give two Box–Muller pairs, (w0,w1) → (cos, sin) for
+    j ≡ 0, 1 (mod 4) and (w2,w3) → (cos, sin) for j ≡ 2, 3."""
+    rows = np.atleast_1d(np.asarray(rows, dtype=np.int64))
+    k0, k1 = seed_key(seed)
+    q = np.arange((n + 3) // 4, dtype=np.uint64)
+    out = np.empty((rows.size, 4 * q.size), dtype=np.float64)
+    for t, i in enumerate(rows):
+        w0, w1, w2, w3 = philox4x32_10(q, np.uint64(i), TAG_GAUSSIAN, 0, k0, k1)
+        za, zb = box_muller(w0, w1)
+        zc, zd = box_muller(w2, w3)
+        out[t, 0::4], out[t, 1::4], out[t, 2::4], out[t, 3::4] = za, zb, zc, zd
+    return out[:, :n] / math.sqrt(m)
+
+
+def gaussian_sketch_matrix(m: int, n: int, seed: int) -> np.ndarray:
+    return gaussian_sketch_rows(np.arange(m), n, m, seed)
+
+
+def countsketch_hash(n: int, m: int, seed: int):
+    """Bucket h(j) ∈ [0, m) and sign s(j) = ±1 of column j of the one-nonzero-
+    per-column sparse embedding: Philox counter (j, 0, TAG_COUNTSKETCH, 0),
+    h = ⌊w0·m / 2³²⌋, s = +1 if w1 is even else −1."""
+    k0, k1 = seed_key(seed)
+    j = np.arange(n, dtype=np.uint64)
+    w0, w1, _, _ = philox4x32_10(j, 0, TAG_COUNTSKETCH, 0, k0, k1)
+    h = ((w0 * np.uint64(m)) >> np.uint64(32)).astype(np.int64)
+    s = np.where((w1 & np.uint64(1)) == 0, 1.0, -1.0)
+    return h, s
+
+
+def countsketch_matrix(m: int, n: int, seed: int) -> np.ndarray:
+    h, s = countsketch_hash(n, m, seed)
+    S = np.zeros((m, n))
+    S[h, np.arange(n)] = s
+    return S
+
+
+def srht_params(n: int, m: int, seed: int):
+    """n_p = 2^⌈log₂ n⌉; D_j = ±1 from counter (j, 0, TAG_SRHT_SIGNS, 0)
+    (w0 even → +1); sampled Hadamard rows r_i = ⌊w0 / 2^(32−L)⌋ from counter
+    (i, 0, TAG_SRHT_ROWS, 0), n_p = 2^L (uniform, with replacement)."""
+    L = max(0, int(math.ceil(math.log2(max(n, 1)))))
+    n_p = 1 << L
+    k0, k1 = seed_key(seed)
+    w0, _, _, _ = philox4x32_10(np.arange(n, dtype=np.uint64), 0, TAG_SRHT_SIGNS, 0, k0, k1)
+    D = np.where((w0 & np.uint64(1)) == 0, 1.0, -1.0)
+    r0, _, _, _ = philox4x32_10(np.arange(m, dtype=np.uint64), 0, TAG_SRHT_ROWS, 0, k0, k1)
+    rows = (r0 >> np.uint64(32 - L)).astype(np.int64) if L > 0 else np.zeros(m, np.int64)
+    return n_p, D, rows
+
+
+def hadamard_entry(r, j):
+    """Sylvester–Hadamard entry H[r, j] = (−1)^popcount(r AND j), broadcast
+    over r and j."""
+    x = np.bitwise_and(np.asarray(r, dtype=np.int64), np.asarray(j, dtype=np.int64))
+    pc = np.zeros(np.shape(x), dtype=np.int64)
+    while np.any(x):
+        pc += x & 1
+        x = x >> 1
+    return np.where(pc % 2 == 0, 1.0, -1.0)
+
+
+def srht_rows(rows_idx, n: int, m: int, seed: int) -> np.ndarray:
+    """Rows of S = √(n_p/m)·P·(H_{n_p}/√n_p)·D restricted to the n real
+    columns (the padded columns multiply zero rows of A)."""
+    n_p, D, rows = srht_params(n, m, seed)
+    rows_idx = np.atleast_1d(np.asarray(rows_idx, dtype=np.int64))
+    H = hadamard_entry(rows[rows_idx][:, None], np.arange(n)[None, :])
+    return H * D[None, :] / math.sqrt(m)
+
+
+def srht_matrix(m: int, n: int, seed: int) -> np.ndarray:
+    return srht_rows(np.arange(m), n, m, seed)
+
+
+def sketch_rows(family: int, rows, A: np.ndarray, m: int, seed: int,
+                col_chunk: int | None = None) -> np.ndarray:
+    """Rows `rows` of SA = S·A, by the definition of S, in fp64."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    rows = np.atleast_1d(np.asarray(rows, dtype=np.int64))
+    if family == COUNTSKETCH:
+        h, s = countsketch_hash(n, m, seed)
+        out = np.zeros((rows.size, A.shape[1]))
+        for t, i in enumerate(rows):
+            sel = np.nonzero(h == i)[0]
+            out[t] = s[sel] @ A[sel]
+        return out
+    if family == GAUSSIAN:
+        S = gaussian_sketch_rows(rows, n, m, seed)
+    elif family == SRHT:
+        S = srht_rows(rows, n, m, seed)
+    else:
+        raise ValueError(f"unknown sketch family {family}")
+    return S @ A
+
+
+def sketch_apply(family: int, A: np.ndarray, m: int, seed: int, row_block: int = 64) -> np.ndarray:
+    """SA = S·A for the whole sketch (row blocks keep S's memory bounded)."""
+    out = np.empty((m, np.shape(A)[1]))
+    for r0 in range(0, m, row_block):
+        r1 = min(m, r0 + row_block)
+        out[r0:r1] = sketch_rows(family, np.arange(r0, r1), A, m, seed)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The ridge solution and its certificates
+# ---------------------------------------------------------------------------
+def gradient(A, b, x, lam):
+    """g = Aᵀ(b − Ax) − λx in fp64 (Algorithm 1, gradient step)."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    r = np.asarray(b, dtype=np.float64) - A @ x
+    return A.T @ r - lam * x
+
+
+def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16):
+    """x* = (AᵀA + λI)⁻¹Aᵀb: fp64 Gram matrix (row blocks summed in order),
+    Cholesky, two triangular solves, then `refine` steps of iterative
+    refinement x += H⁻¹(Aᵀ(b−Ax) − λx)."""
+    n, d = np.shape(A)
+    H = np.zeros((d, d))
+    Atb = np.zeros(d)
+    for r0 in range(0, n, row_block):
+        Ab = np.asarray(A[r0:r0 + row_block], dtype=np.float64)
+        H += Ab.T @ Ab
+        Atb += Ab.T @ np.asarray(b[r0:r0 + row_block], dtype=np.float64)
+    H[np.diag_indices(d)] += lam
+    L = np.linalg.cholesky(H)
+
+    def hsolve(v):
+        y = np.linalg.solve(L, v)          # forward substitution (L lower)
+        return np.linalg.solve(L.T, y)     # back substitution
+
+    x = hsolve(Atb)
+    for _ in range(refine):
+        x = x + hsolve(gradient_blocked(A, b, x, lam, row_block))
+    return x
+
+
+def gradient_blocked(A, b, x, lam, row_block: int = 1 << 16):
+    n = np.shape(A)[0]
+    g = -lam * np.asarray(x, dtype=np.float64)
+    for r0 in range(0, n, row_block):
+        Ab = np.asarray(A[r0:r0 + row_block], dtype=np.float64)
+        g += Ab.T @ (np.asarray(b[r0:r0 + row_block], dtype=np.float64) - Ab @ x)
+    return g
+
+
+def svd_solve(A, b, lam):
+    """Closed form of Eq. tsvdsol: x* = Σ σᵢ²/(σᵢ²+λ) (uᵢᵀb/σᵢ) vᵢ."""
+    U, s, Vt = np.linalg.svd(np.asarray(A, dtype=np.float64), full_matrices=False)
+    coef = (s ** 2 / (s ** 2 + lam)) * (U.T @ np.asarray(b, dtype=np.float64)) / s
+    return Vt.T @ coef
+
+
+def stat_dim(sigma, lam):
+    """sd_λ(A) = Σ σᵢ²/(σᵢ²+λ)."""
+    s2 = np.asarray(sigma, dtype=np.float64) ** 2
+    return float(np.sum(s2 / (s2 + lam)))
+
+
+def stat_dim_of(A, lam):
+    return stat_dim(np.linalg.svd(np.asarray(A, dtype=np.float64), compute_uv=False), lam)
+
+
+def certify(A, b, x, lam):
+    """Upper bound on ‖x − x*‖ from H ⪰ λI: ‖x − x*‖ ≤ ‖g(x)‖/λ."""
+    return float(np.linalg.norm(gradient_blocked(A, b, x, lam)) / lam)
+
+
+def rel_error(x, xstar):
+    x = np.asarray(x, dtype=np.float64)
+    xstar = np.asarray(xstar, dtype=np.float64)
+    return float(np.linalg.norm(x - xstar) / np.linalg.norm(xstar))
+
+
+# ---------------------------------------------------------------------------
+# AAb_Solver (Algorithm 5): approximately solve (SAᵀSA + λI) x = g
+# ---------------------------------------------------------------------------
+def aab_solve(SA, g, lam, eps, max_iter=None, dtype=np.float64, history=False,
+              s_init="sqrt_lam_over_rhobar"):
+    """Upper bidiagonalisation of SA started at θ₁v = g, Eldén's Givens fold of
+    √λ into the bidiagonal, the analytic φ recursion and the forward
+    substitution update of Section 3.6.
+
+    `max_iter` caps the number of loop passes (each pass = one product with
+    SAᵀ and one with SA); the cap is also min(m, d) (finite termination).
+    Returns (x, passes[, list of t]).  `dtype=np.float32` emulates fp32.
+    `s_init` selects the reading of the initial sine (only for the test that
+    shows the garbled form breaks the residual identity).
+    """
+    SA = np.asarray(SA, dtype=dtype)
+    g = np.asarray(g, dtype=dtype)
+    lam = dtype(lam)
+    m, d = SA.shape
+    cap = min(m, d) if max_iter is None else min(int(max_iter), min(m, d))
+    theta1 = np.sqrt(np.sum(g * g, dtype=dtype))
+    ts = []
+    if theta1 == 0:
+        return (np.zeros(d, dtype), 0, ts) if history else (np.zeros(d, dtype), 0)
+    v = g / theta1                                   # θ₁ v = b
+    w = SA @ v                                       # ρ p = A v
+    rho = np.sqrt(np.sum(w * w, dtype=dtype))
+    p = w / rho
+    rhobar = np.sqrt(rho * rho + lam)
+    c = rho / rhobar
+    s = np.sqrt(lam) / rhobar if s_init == "sqrt_lam_over_rhobar" else np.sqrt(lam / rhobar)
+    phi = theta1 / rhobar
+    dv = v / rhobar
+    x = phi * dv
+    t = np.inf
+    k = 0
+    while t >= eps and k < cap:
+        z = SA.T @ p - rho * v                       # θ v := Aᵀp − ρ v
+        theta = np.sqrt(np.sum(z * z, dtype=dtype))
+        if not theta > 0:
+            break                                    # invariant subspace reached
+        v = z / theta
+        w = SA @ v - theta * p                       # ρ p := A v − θ p
+        rho = np.sqrt(np.sum(w * w, dtype=dtype))
+        lambar = np.sqrt(lam + (s * theta) ** 2)     # λ̄² = λ + (sθ)²
+        thetabar = c * theta                         # θ̄ = cθ
+        rhobar = np.sqrt(rho * rho + lambar * lambar)
+        c = rho / rhobar
+        s = lambar / rhobar
+        dv = (v - thetabar * dv) / rhobar
+        phi = -phi * thetabar / rhobar
+        x = x + phi * dv
+        t = abs(phi * rhobar) / theta1
+        ts.append(float(t))
+        k += 1
+        if not rho > 0:
+            break
+        p = w / rho
+    return (x, k, ts) if history else (x, k)
+
+
+# ---------------------------------------------------------------------------
+# Momentum parameters and convergence theory
+# ---------------------------------------------------------------------------
+def momentum_params(sd, m):
+    """Corollary 3: β = sd/m, α = (1 − β)²."""
+    beta = float(sd) / float(m)
+    return (1.0 - beta) ** 2, beta
+
+
+def theorem1_params(eps):
+    """Theorem 1: β* = (ε/(1+√(1−ε²)))², α* = (1−β*)√(1−ε²), rate √β*."""
+    rate = eps / (1.0 + math.sqrt(1.0 - eps * eps))
+    beta = rate * rate
+    alpha = (1.0 - beta) * math.sqrt(1.0 - eps * eps)
+    return alpha, beta, rate
+
+
+def theorem1_alpha_alt(eps):
+    """Second form of α* in the proof of Theorem 1: 4(1−ε²)/(√(1+ε)+√(1−ε))²."""
+    return 4.0 * (1.0 - eps * eps) / (math.sqrt(1.0 + eps) + math.sqrt(1.0 - eps)) ** 2
+
+
+def corollary3_iters(eta, beta):
+    """Corollary 3: at most log(η)/log(√β) iterations for an η-optimal x."""
+    return math.log(eta) / math.log(math.sqrt(beta))
+
+
+def corollary2_iters(eta, C, eps):
+    """Corollary 2 under the reading ⌈log(η/C)/log(ε/(1+√(1−ε²)))⌉."""
+    return int(math.ceil(math.log(eta / C) / math.log(eps / (1.0 + math.sqrt(1.0 - eps * eps)))))
+
+
+def predicted_error(C, beta, N):
+    """Corollary 3 applied to a start error of C (in units of the target
+    norm): C·(√β)^N, the form used in the captions of Section 4."""
+    return C * math.sqrt(beta) ** N
+
+
+def characteristic_roots(mu, alpha, beta):
+    """Roots of u² − (1 + β − αμ)u + β = 0 (proof of Theorem 1)."""
+    mu = np.atleast_1d(np.asarray(mu, dtype=np.float64))
+    tr = 1.0 + beta - alpha * mu
+    disc = np.sqrt((tr * tr - 4.0 * beta).astype(np.complex128))
+    return (tr + disc) / 2.0, (tr - disc) / 2.0
+
+
+def characteristic_rate(mu, alpha, beta):
+    """Spectral radius of the heavy-ball transition: max root modulus."""
+    r1, r2 = characteristic_roots(mu, alpha, beta)
+    return float(np.max(np.maximum(np.abs(r1), np.abs(r2))))
+
+
+def underdamped(mu, alpha, beta):
+    """Condition β ≥ (1 − √(αμ))² of the proof of Theorem 1."""
+    mu = np.asarray(mu, dtype=np.float64)
+    return beta >= (1.0 - np.sqrt(alpha * mu)) ** 2
+
+
+def sketched_hessian_eigs(A, SA, lam):
+    """μᵢ = eig((SAᵀSA + λI)⁻¹(AᵀA + λI)), the eigenvalues in the proof of
+    Theorem 1 (similar to (ÂᵀŜᵀŜÂ)⁻¹)."""
+    A = np.asarray(A, dtype=np.float64)
+    SA = np.asarray(SA, dtype=np.float64)
+    d = A.shape[1]
+    H = A.T @ A + lam * np.eye(d)
+    HS = SA.T @ SA + lam * np.eye(d)
+    Lc = np.linalg.cholesky(HS)
+    Li = np.linalg.inv(Lc)
+    return np.sort(np.linalg.eigvalsh(Li @ H @ Li.T))
+
+
+def mp_edges(sd, m):
+    """Limits (1 ± √(sd/m))⁻² of the extreme μ (proof of Corollary 3)."""
+    r = math.sqrt(sd / m)
+    return (1.0 + r) ** -2, (1.0 - r) ** -2
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1: M-IHS for n ≥ d
+# ---------------------------------------------------------------------------
+def heavy_ball(x, x_prev, delta, alpha, beta):
+    """x⁺ = x + αΔ + β(x − x⁻) (Eq. mihs1); returns (x⁺, new x⁻ = x)."""
+    return x + alpha * delta + beta * (x - x_prev), x
+
+
+def mihs(A, b, lam, SA, sd, N, x1=None, eps_sub=0.1, tol=None, inner="aab",
+         max_inner=None, dtype=np.float64, record=False):
+    """Algorithm 1 with the given SA.
+
+    Each of at most N iterations: g = Aᵀ(b − Ax) − λx; stop if tol is set and
+    ‖g‖ ≤ tol·‖Aᵀb‖; Δ from AAb_Solver(SA, g, λ, ε_sub) (or, with
+    inner="exact", from a Cholesky solve of SAᵀSA + λI — the exact scheme);
+    x ← x + αΔ + β(x − x⁻).  x⁰ = x¹.
+    Returns (x, info) with info = {outer, inner_total, resid, history}.
+    """
+    A = np.asarray(A, dtype=dtype)
+    b = np.asarray(b, dtype=dtype)
+    SA = np.asarray(SA, dtype=dtype)
+    m, d = SA.shape
+    alpha, beta = momentum_params(sd, m)
+    alpha, beta = dtype(alpha), dtype(beta)
+    x = np.zeros(d, dtype) if x1 is None else np.asarray(x1, dtype=dtype).copy()
+    x_prev = x.copy()
+    gnorm0 = float(np.linalg.norm(A.T.astype(np.float64) @ b.astype(np.float64)))
+    if inner == "exact":
+        HS = SA.astype(np.float64).T @ SA.astype(np.float64) + lam * np.eye(d)
+        Lc = np.linalg.cholesky(HS)
+    hist = []
+    inner_total = 0
+    outer = 0
+    resid = float("nan")
+    for i in range(N):
+        g = A.T @ (b - A @ x) - dtype(lam) * x
+        resid = float(np.linalg.norm(g.astype(np.float64))) / gnorm0 if gnorm0 > 0 else 0.0
+        if record:
+            hist.append((x.astype(np.float64).copy(), resid))
+        if tol is not None and resid <= tol:
+            break
+        if inner == "exact":
+            delta = np.linalg.solve(Lc.T, np.linalg.solve(Lc, g.astype(np.float64))).astype(dtype)
+            k = 0
+        else:
+            delta, k = aab_solve(SA, g, lam, eps_sub, max_iter=max_inner, dtype=dtype)
+        inner_total += k
+        x, x_prev = heavy_ball(x, x_prev, delta, alpha, beta)
+        outer += 1
+    info = dict(outer=outer, inner_total=inner_total, resid=resid, history=hist,
+                alpha=float(alpha), beta=float(beta))
+    return x.astype(np.float64), info
+
+
+def mihs_solve(A, b, lam, family, m, sd, seed, N=200, tol=1e-6, eps_sub=0.1,
+               max_inner=None, dtype=np.float64):
+    """Sketch (RP_fun) then Algorithm 1: the whole path on the CPU."""
+    SA = sketch_apply(family, A, m, seed)
+    return mihs(A, b, lam, SA, sd, N, eps_sub=eps_sub, tol=tol,
+                max_inner=max_inner, dtype=dtype)

@@ -1,0 +1,374 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types an oracle formula: each compares the oracle with a
+library routine, a closed form, an invariant, a printed number or brute force
+chosen so that a dropped term, a wrong sign or a transposed operand fails.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.stats
+
+from oracle import mihs_oracle as o
+from paper_1912_03514_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = o.philox4x32_10(*v[:4], *v[4:6])
+        assert [int(w) for w in out] == v[6:10]
+
+
+def test_philox_vectorised_equals_scalar():
+    c0 = np.arange(17, dtype=np.uint64)
+    vec = o.philox4x32_10(c0, 5, 1, 0, 123, 456)
+    for i in range(17):
+        sc = o.philox4x32_10(i, 5, 1, 0, 123, 456)
+        assert [int(w[i]) for w in vec] == [int(w) for w in sc]
+
+
+# ------------------------------------------------------------ Box-Muller
+def test_box_muller_closed_forms():
+    # u1 = 1 exactly -> radius 0
+    z0, z1 = o.box_muller(np.uint64(0xFFFFFFFF), np.uint64(12345 << 8))
+    assert z0 == 0.0 and z1 == 0.0
+    # u1 = 2^-24 (smallest), u2 = 1/4 -> (0, sqrt(2*24*ln 2))
+    z0, z1 = o.box_muller(np.uint64(0), np.uint64(1 << 30))
+    r = math.sqrt(2.0 * 24.0 * math.log(2.0))
+    assert abs(z0) < 1e-12 and abs(z1 - r) < 1e-12
+
+
+def test_box_muller_is_standard_normal():
+    w0, w1, w2, w3 = o.philox4x32_10(np.arange(1 << 16, dtype=np.uint64), 0, 0, 0, 7, 9)
+    z = np.concatenate(o.box_muller(w0, w1) + o.box_muller(w2, w3))
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / z.size)
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-4
+
+
+# ---------------------------------------------------------------- sketches
+def _mc_isotropy(make_S, n, seeds):
+    acc = np.zeros((n, n))
+    for s in seeds:
+        S = make_S(s)
+        acc += S.T @ S
+    return acc / len(seeds)
+
+
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_sketch_expectation_identity(family):
+    """E[SᵀS] = I (text after Algorithm 1): Monte-Carlo mean over seeds."""
+    n, m, T = 24, 8, 600
+    mk = {o.GAUSSIAN: lambda s: o.gaussian_sketch_matrix(m, n, s),
+          o.COUNTSKETCH: lambda s: o.countsketch_matrix(m, n, s),
+          o.SRHT: lambda s: o.srht_matrix(m, n, s)}[family]
+    E = _mc_isotropy(mk, n, range(T))
+    assert np.max(np.abs(np.diag(E) - 1)) < 0.25
+    off = E - np.diag(np.diag(E))
+    assert np.max(np.abs(off)) < 0.25
+    # a scaling mistake (e.g. 1/m instead of 1/sqrt(m)) moves the diagonal far
+    assert abs(np.mean(np.diag(E)) - 1) < 0.05
+
+
+def test_gaussian_entries_variance_and_independence():
+    m, n = 64, 4096
+    S = o.gaussian_sketch_matrix(m, n, 2024)
+    z = S.ravel() * math.sqrt(m)
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-4
+    # each of the four counter slots is a standard normal on its own
+    for t in range(4):
+        zt = (S[:, t::4] * math.sqrt(m)).ravel()
+        assert abs(zt.var() - 1) < 0.05
+    C = np.corrcoef(S)
+    assert np.max(np.abs(C - np.eye(m))) < 0.1
+
+
+def test_countsketch_structure_and_exact_sum():
+    n, m, d = 5000, 37, 6
+    S = o.countsketch_matrix(m, n, 11)
+    assert np.all(np.sum(S != 0, axis=0) == 1)
+    assert set(np.unique(S[S != 0])) <= {-1.0, 1.0}
+    h, s = o.countsketch_hash(n, m, 11)
+    assert h.min() >= 0 and h.max() < m
+    counts = np.bincount(h, minlength=m)
+    assert scipy.stats.chisquare(counts).pvalue > 1e-4
+    A = W.randint_matrix((n, d), 3).numpy().astype(np.float64)
+    SA = o.sketch_apply(o.COUNTSKETCH, A, m, 11)
+    brute = np.zeros((m, d))
+    for j in range(n):                       # SA[h(j)] += s(j) A[j]
+        brute[h[j]] += s[j] * A[j]
+    assert np.array_equal(SA, brute)
+
+
+def test_hadamard_matches_scipy():
+    for L in range(0, 8):
+        Hs = scipy.linalg.hadamard(1 << L)
+        r = np.arange(1 << L)
+        assert np.array_equal(o.hadamard_entry(r[:, None], r[None, :]), Hs)
+
+
+def test_srht_definition():
+    n, m = 100, 16                       # n not a power of two -> n_p = 128
+    n_p, D, rows = o.srht_params(n, m, 5)
+    assert n_p == 128 and rows.min() >= 0 and rows.max() < 128
+    H = scipy.linalg.hadamard(n_p)
+    Dfull = np.concatenate([D, np.ones(n_p - n)])
+    Sfull = math.sqrt(n_p / m) * (H[rows] / math.sqrt(n_p)) * Dfull[None, :]
+    assert np.allclose(o.srht_matrix(m, n, 5), Sfull[:, :n], atol=0, rtol=1e-15)
+    rr = o.srht_params(1 << 12, 20000, 1)[2]
+    assert scipy.stats.chisquare(np.bincount(rr >> 6, minlength=64)).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_sketch_rows_equal_full_product(family):
+    n, d, m = 300, 7, 12
+    A = W.randn((n, d), 4).numpy()
+    S = {o.GAUSSIAN: o.gaussian_sketch_matrix, o.COUNTSKETCH: o.countsketch_matrix,
+         o.SRHT: o.srht_matrix}[family](m, n, 99)
+    SA = o.sketch_apply(family, A, m, 99, row_block=5)
+    assert np.allclose(SA, S @ A.astype(np.float64), rtol=1e-13, atol=1e-13)
+
+
+# ----------------------------------------------------------- ridge solution
+def _small(n=400, d=40, lam=1e-2, seed=0):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((n, d)))
+    V, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    s = np.logspace(0, -3, d)
+    A = (U * s) @ V.T
+    b = rng.standard_normal(n)
+    return A, b, lam, s
+
+
+def test_exact_solve_matches_lstsq_and_svd():
+    A, b, lam, _ = _small()
+    x = o.exact_solve(A, b, lam)
+    n, d = A.shape
+    Aug = np.vstack([A, math.sqrt(lam) * np.eye(d)])
+    x_ls = np.linalg.lstsq(Aug, np.concatenate([b, np.zeros(d)]), rcond=None)[0]
+    assert o.rel_error(x, x_ls) < 1e-11
+    assert o.rel_error(o.svd_solve(A, b, lam), x_ls) < 1e-11
+    # first-order optimality
+    assert np.linalg.norm(o.gradient(A, b, x, lam)) < 1e-11 * np.linalg.norm(A.T @ b)
+
+
+def test_exact_solve_blocked_rows_same_result():
+    A, b, lam, _ = _small(n=1000, d=20)
+    assert o.rel_error(o.exact_solve(A, b, lam, row_block=37), o.exact_solve(A, b, lam)) < 1e-13
+
+
+def test_stat_dim_identities():
+    A, b, lam, s = _small()
+    n, d = A.shape
+    sd = o.stat_dim_of(A, lam)
+    assert abs(sd - o.stat_dim(s, lam)) < 1e-9
+    # definition tr(A (AᵀA+λI)⁻¹ Aᵀ)
+    tr = np.trace(A @ np.linalg.solve(A.T @ A + lam * np.eye(d), A.T))
+    assert abs(sd - tr) < 1e-9
+    # ‖U1‖_F² with U1 the first n rows of an orthonormal basis of [A; √λ I]
+    Q, _ = np.linalg.qr(np.vstack([A, math.sqrt(lam) * np.eye(d)]))
+    assert abs(sd - np.sum(Q[:n] ** 2)) < 1e-9
+    # λ → 0: the rank
+    assert abs(o.stat_dim(s, 0.0) - d) < 1e-12
+
+
+def test_gradient_brute_force():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((5, 3)); b = rng.standard_normal(5); x = rng.standard_normal(3)
+    lam = 0.7
+    g = np.zeros(3)
+    for j in range(3):
+        acc = 0.0
+        for i in range(5):
+            ri = b[i] - sum(A[i, k] * x[k] for k in range(3))
+            acc += A[i, j] * ri
+        g[j] = acc - lam * x[j]
+    assert np.allclose(o.gradient(A, b, x, lam), g, rtol=1e-14, atol=1e-14)
+    # g is minus the derivative of f (central differences)
+    f = lambda z: 0.5 * np.sum((A @ z - b) ** 2) + 0.5 * lam * np.sum(z ** 2)
+    num = np.array([(f(x + 1e-6 * e) - f(x - 1e-6 * e)) / 2e-6 for e in np.eye(3)])
+    assert np.allclose(-num, g, atol=1e-7)
+
+
+# -------------------------------------------------------------- AAb_Solver
+def _aab_case(m=40, d=30, lam=0.3, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((m, d)), rng.standard_normal(d), lam
+
+
+def test_aab_residual_identity():
+    """Section 3.6: the loop's t equals ‖(SAᵀSA+λI)x − g‖/‖g‖ of the iterate
+    held before the pass (the unsquared norm)."""
+    SA, g, lam = _aab_case()
+    d = SA.shape[1]
+    H = SA.T @ SA + lam * np.eye(d)
+    _, _, ts = o.aab_solve(SA, g, lam, 0.0, max_iter=12, history=True)
+    for k in range(12):
+        xk, _ = o.aab_solve(SA, g, lam, 0.0, max_iter=k)
+        true = np.linalg.norm(H @ xk - g) / np.linalg.norm(g)
+        assert abs(ts[k] - true) <= 1e-10 * true
+
+
+def test_aab_garbled_initial_sine_breaks_identity():
+    """The printed initial sine √(λ/ρ̄) violates the residual identity, which is
+    how the reading s = √λ/ρ̄ is pinned."""
+    SA, g, lam = _aab_case()
+    d = SA.shape[1]
+    H = SA.T @ SA + lam * np.eye(d)
+    _, _, ts = o.aab_solve(SA, g, lam, 0.0, max_iter=6, history=True, s_init="garbled")
+    x5, _ = o.aab_solve(SA, g, lam, 0.0, max_iter=5, s_init="garbled")
+    true = np.linalg.norm(H @ x5 - g) / np.linalg.norm(g)
+    assert abs(ts[5] - true) > 1e-6 * true
+
+
+def test_aab_finite_termination_and_stop_rule():
+    SA, g, lam = _aab_case(m=25, d=18, lam=0.5)
+    d = SA.shape[1]
+    H = SA.T @ SA + lam * np.eye(d)
+    x_direct = np.linalg.solve(H, g)
+    x, k = o.aab_solve(SA, g, lam, 0.0)
+    assert k <= min(SA.shape)
+    assert o.rel_error(x, x_direct) < 1e-9
+    # forcing term: the pass that stops has t < eps, and that t certifies the
+    # previous iterate, so the returned one is at least as good in practice
+    for eps in (0.5, 0.1, 1e-3):
+        x, k, ts = o.aab_solve(SA, g, lam, eps, history=True)
+        assert ts[-1] < eps and all(t >= eps for t in ts[:-1])
+        assert np.linalg.norm(H @ x - g) / np.linalg.norm(g) < eps
+
+
+def test_aab_zero_rhs_and_fp32_mode():
+    SA, g, lam = _aab_case()
+    x, k = o.aab_solve(SA, np.zeros_like(g), lam, 0.1)
+    assert k == 0 and not np.any(x)
+    x32, _ = o.aab_solve(SA, g, lam, 1e-4, dtype=np.float32)
+    x64, _ = o.aab_solve(SA, g, lam, 1e-4)
+    assert x32.dtype == np.float32 and o.rel_error(x32, x64) < 1e-4
+
+
+# ------------------------------------------------------- momentum & rates
+@pytest.mark.parametrize("eps", [0.05, 0.3, 0.5, 0.9])
+def test_theorem1_parameters(eps):
+    alpha, beta, rate = o.theorem1_params(eps)
+    assert abs(alpha - o.theorem1_alpha_alt(eps)) < 1e-12
+    # rate = min over α of max{1 − √α/√(1+ε), √α/√(1−ε) − 1} (brute force)
+    a = np.linspace(1e-6, 2.0, 400001)
+    worst = np.maximum(1 - np.sqrt(a) / math.sqrt(1 + eps), np.sqrt(a) / math.sqrt(1 - eps) - 1)
+    i = np.argmin(worst)
+    assert abs(worst[i] - rate) < 1e-5
+    assert abs(a[i] - alpha) < 1e-4
+    assert abs(math.sqrt(beta) - rate) < 1e-15
+    # with μ spanning [1/(1+ε), 1/(1−ε)] every mode is under-damped
+    mu = np.linspace(1 / (1 + eps), 1 / (1 - eps), 101)
+    assert np.all(o.underdamped(mu, alpha, beta + 1e-12))
+    assert abs(o.characteristic_rate(mu, alpha, beta) - rate) < 1e-6
+
+
+@pytest.mark.parametrize("ratio", [0.1, 0.25, 0.5])
+def test_corollary3_marchenko_pastur_edges(ratio):
+    """With α = (1−β)², β = sd/m, both MP edges (1 ± √β)⁻² sit exactly on the
+    under-damped boundary, so every μ between them has root modulus √β."""
+    alpha, beta = o.momentum_params(ratio * 400, 400)
+    lo, hi = o.mp_edges(ratio * 400, 400)
+    for mu in (lo, hi):
+        assert abs((1 - math.sqrt(alpha * mu)) ** 2 - beta) < 1e-12
+    mu = np.linspace(lo, hi, 57)
+    assert abs(o.characteristic_rate(mu, alpha, beta) - math.sqrt(beta)) < 1e-6
+    # outside the edges the rate is strictly worse (over-damped mode)
+    assert o.characteristic_rate([hi * 1.5], alpha, beta) > math.sqrt(beta) + 1e-3
+
+
+def test_worked_number_no_reg_caption():
+    rows = [l.split("|") for l in open(os.path.join(GOLDEN, "paper_worked_numbers.txt"))
+            if l.strip() and not l.startswith("#")]
+    (name, inputs, printed, _), = rows
+    kv = dict(t.split("=") for t in inputs.split())
+    d, m, N, kappa = int(kv["d"]), int(kv["m"]), int(kv["N"]), float(kv["kappa"])
+    sd = o.stat_dim(np.ones(d), 0.0)                 # λ = 0 → rank
+    _, beta = o.momentum_params(sd, m)
+    val = o.predicted_error(kappa, beta, N)
+    assert float(f"{val:.0e}") == float(printed)
+
+
+def test_corollary2_reading_is_consistent_with_theorem1():
+    eps, C, eta = 0.4, 50.0, 1e-8
+    N = o.corollary2_iters(eta, C, eps)
+    rate = o.theorem1_params(eps)[2]
+    assert C * rate ** N <= eta < C * rate ** (N - 1)
+
+
+# ------------------------------------------------------------- Algorithm 1
+def _problem(n=3000, d=60, seed=5, sd_frac=0.2):
+    p = W.problem_scaled(n, d, seed, decades=3.0, sd_frac=sd_frac)
+    return p.A.numpy().astype(np.float64), p.b.numpy().astype(np.float64), p
+
+
+def test_exact_inner_rate_equals_characteristic_rate():
+    """Exact M-IHS error decays at the spectral radius of the heavy-ball
+    transition computed from μ = eig((SAᵀSA+λI)⁻¹(AᵀA+λI))."""
+    A, b, p = _problem()
+    SA = o.sketch_apply(o.GAUSSIAN, A, p.m, 77)
+    xs = o.exact_solve(A, b, p.lam)
+    alpha, beta = o.momentum_params(p.sd, p.m)
+    mu = o.sketched_hessian_eigs(A, SA, p.lam)
+    pred = o.characteristic_rate(mu, alpha, beta)
+    _, info = o.mihs(A, b, p.lam, SA, p.sd, 45, inner="exact", record=True)
+    errs = np.array([np.linalg.norm(h[0] - xs) for h in info["history"]])
+    k0, k1 = 10, 40
+    obs = (errs[k1] / errs[k0]) ** (1.0 / (k1 - k0))
+    assert abs(obs - pred) < 0.08 * pred
+    # and a wrong β (momentum dropped) predicts a visibly different rate
+    assert abs(o.characteristic_rate(mu, alpha, 0.0) - obs) > 0.05
+
+
+def test_rate_is_sqrt_sd_over_m_statistically():
+    """Corollary 3: rate √(sd/m), averaged over 8 Gaussian sketches."""
+    A, b, p = _problem(n=4000, d=80, seed=6)
+    xs = o.exact_solve(A, b, p.lam)
+    sd = o.stat_dim_of(A, p.lam)
+    rates = []
+    for seed in range(8):
+        SA = o.sketch_apply(o.GAUSSIAN, A, p.m, 100 + seed)
+        _, info = o.mihs(A, b, p.lam, SA, sd, 30, inner="exact", record=True)
+        e = np.array([np.linalg.norm(h[0] - xs) for h in info["history"]])
+        rates.append((e[25] / e[5]) ** (1 / 20))
+    assert abs(np.mean(rates) - math.sqrt(sd / p.m)) < 0.2 * math.sqrt(sd / p.m)
+
+
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_inexact_mihs_reaches_exact_solution(family):
+    p = W.problem_small()
+    A = p.A.numpy().astype(np.float64)
+    b = p.b.numpy().astype(np.float64)
+    xs = o.exact_solve(A, b, p.lam)
+    x, info = o.mihs_solve(A, b, p.lam, family, p.m, p.sd, seed=31, N=120, tol=1e-13)
+    assert o.rel_error(x, xs) < 1e-10
+    assert info["outer"] < 80
+    assert o.certify(A, b, x, p.lam) < 1e-9 * np.linalg.norm(xs)
+
+
+def test_fp32_mode_floor_on_small_problem():
+    p = W.problem_small()
+    A = p.A.numpy()
+    b = p.b.numpy()
+    xs = o.exact_solve(A, b, p.lam)
+    SA = o.sketch_apply(o.GAUSSIAN, A, p.m, 31).astype(np.float32)
+    x, info = o.mihs(A, b, p.lam, SA, p.sd, 100, tol=1e-6, dtype=np.float32)
+    assert info["resid"] <= 1e-6
+    assert o.rel_error(x, xs) < 1e-5
+
+
+def test_nominal_sd_close_to_actual():
+    p = W.problem_small()
+    sd = o.stat_dim_of(p.A.numpy(), p.lam)
+    assert abs(sd - 64.0) < 2.0 and abs(p.sd - 64.0) < 1e-9
