@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark: ridge solves/s of M-IHS (Algorithm 1) on one GB300 per rank.
+
+Workload (the bandwidth-scale plain-FP32 problem): A = G·diag(σ)·Vᵀ/√n with
+n = 262144, d = 1024, σ_i = 1/i, λ = 1e-4, b = A x0 + ω at 40 dB SNR, sketch
+size m = 4·sd = 588 (sd = 146.85).  One step = one full solve (sketch + outer
+iterations until ‖g‖ ≤ tol·‖Aᵀb‖) with each of the three sketch families
+(Gaussian, CountSketch, SRHT).  A is 1.07 GB (> L2), so every pass streams
+from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mihs|reference]
+
+Prints one JSON line (rank 0).  `value` is device time with A and b resident;
+`e2e` is the one-call API with host (pinned) inputs, copies inside the timed
+region; `roofline` is the gradient A-pass kernel, timed with CUDA events on
+its stream; `cpu_baseline` is the oracle on the host cores (bounded sample).
+Under torchrun (N > 1) every rank solves its own replica (weak scaling; the
+method needs no collective on one problem per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FAMILIES = ["gaussian", "countsketch", "srht"]
+METRIC = "ridge solves/s at stated rel. error"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mihs", "reference"], default="mihs")
+    ap.add_argument("--families", default=",".join(FAMILIES))
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-outer", type=int, default=200)
+    ap.add_argument("--n", type=int, default=262144)
+    ap.add_argument("--d", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- plumbing
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gpu_uuid():
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(torch.cuda.current_device())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(A_host, b_host, p, families, iters_per_family, quick=False):
+    """Bounded sample of the oracle on the host cores: the sketch of a few rows
+    of SA per family (scaled to m rows) plus `n_it` fp64 M-IHS iterations on
+    the full problem (scaled to the iteration count the solve needs)."""
+    import numpy as np
+
+    from oracle import mihs_oracle as o
+    fam_id = {"gaussian": o.GAUSSIAN, "countsketch": o.COUNTSKETCH, "srht": o.SRHT}
+    A = A_host.numpy()
+    b = b_host.numpy()
+    rows = 2 if quick else 6
+    n_it = 1 if quick else 2
+    t0 = time.perf_counter()
+    SA = o.sketch_apply(o.COUNTSKETCH, A, p.m, 7)          # cheap, full SA for the inner solves
+    t_cs_full = time.perf_counter() - t0
+    sketch_s = {}
+    for f in families:
+        if f == "countsketch":
+            sketch_s[f] = t_cs_full
+            continue
+        t0 = time.perf_counter()
+        o.sketch_rows(fam_id[f], np.arange(rows), A, p.m, 7)
+        sketch_s[f] = (time.perf_counter() - t0) * p.m / rows
+    t0 = time.perf_counter()
+    o.mihs(A, b, p.lam, SA, p.sd, n_it, eps_sub=0.1)
+    t_it = (time.perf_counter() - t0) / n_it
+    total = sum(sketch_s[f] + (iters_per_family[f] + 1) * t_it for f in families)
+    sample = (f"oracle (numpy fp64) on the full {p.n}x{p.d} problem: {rows} rows of SA per dense "
+              f"family scaled to m={p.m}, full CountSketch SA, {n_it} M-IHS iterations scaled to "
+              f"the iteration counts {iters_per_family} of this run")
+    return len(families) / total, sample, {"sketch_s": sketch_s, "iter_s": t_it}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    import torch
+    ws, rank, local = dist_setup()
+    families = [f for f in args.families.split(",") if f]
+
+    from paper_1912_03514_gb300 import workloads as W
+
+    if args.impl == "reference":
+        return run_reference(args, ws, rank, families)
+
+    from paper_1912_03514_gb300 import mihs
+
+    dev = torch.device("cuda", local)
+    p = W.problem_bandwidth(device=str(dev), seed=1001 + rank, n=args.n, d=args.d)
+    A, b = p.A, p.b
+    n, d, m = p.n, p.d, p.m
+    seed = 0x5EED0000 + rank
+    sketches = {f: mihs.Sketch(A, f, m, seed) for f in families}
+    xs = {f: torch.empty(d, dtype=torch.float32, device=dev) for f in families}
+    kw = dict(tol=args.tol, max_outer=args.max_outer, eps_sub=0.1)
+
+    def step(want_info=False):
+        infos = {}
+        for f in families:
+            sk = sketches[f]
+            sk.resketch(A, seed)
+            _, infos[f] = sk.solve(A, b, p.lam, p.sd, x=xs[f], want_info=want_info, **kw)
+        return infos
+
+    # Warm-up; the last warm-up step reports iteration counts.
+    for _ in range(max(args.warmup - 1, 0)):
+        step()
+    infos = step(want_info=True)
+    for f, inf in infos.items():
+        if inf.status != mihs.OK:
+            raise SystemExit(f"{f}: solve did not converge: {inf}")
+    # Launches per step: sketch kernels (counted by the library) + ctl init +
+    # 3 per outer iteration (+1 final gradient) in the device-side loop.
+    c0 = mihs.launch_count()
+    for f in families:
+        sketches[f].resketch(A, seed)
+    torch.cuda.synchronize()
+    sketch_launches = mihs.launch_count() - c0
+    launches_per_step = sketch_launches + sum(1 + 3 * (inf.outer_iters + 1) for inf in infos.values())
+
+    # ---------------- timed region (device-resident inputs)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(gpu_uuid())
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_host0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t_host0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms, ws)
+    value = ws * len(families) / (ms / 1e3)
+
+    # ---------------- per-family and per-kernel times (event timing, one extra step)
+    mihs.timing(True)
+    per_family = {}
+    for f in families:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sketches[f].resketch(A, seed)
+        sketches[f].solve(A, b, p.lam, p.sd, x=xs[f], want_info=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_family[f] = round(e0.elapsed_time(e1), 4)
+    apass_ms, apass_n = mihs.timing_read(mihs.TIMER_APASS)
+    aab_ms, aab_n = mihs.timing_read(mihs.TIMER_AAB)
+    sk_ms, sk_n = mihs.timing_read(mihs.TIMER_SKETCH)
+    mihs.timing(False)
+    apass_avg_s = apass_ms / 1e3 / max(apass_n, 1)
+    bytes_per_pass = 4 * (n * d + n + 2 * d)          # A, b, x read; g written
+    achieved = bytes_per_pass / apass_avg_s / 1e9
+    peaks, peak_src = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": "apass_partial_kernel (gradient g = Aᵀ(b−Ax) − λx)",
+                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": f"{peak_src} hbm_gbs",
+                "traffic": None, "bytes_per_launch": bytes_per_pass,
+                "avg_launch_us": round(apass_avg_s * 1e6, 2), "launches_timed": apass_n}
+
+    # ---------------- accuracy vs the oracle's exact solution
+    accuracy = None
+    A_host = b_host = None
+    if rank == 0 and not args.no_accuracy:
+        from oracle import mihs_oracle as o
+        A_host, b_host = A.cpu(), b.cpu()
+        xstar = o.exact_solve(A_host.numpy(), b_host.numpy(), p.lam)
+        accuracy = {}
+        for f in families:
+            _, inf = sketches[f].solve(A, b, p.lam, p.sd, x=xs[f], want_info=True, **kw)
+            accuracy[f] = {"rel_err_vs_oracle": float(f"{o.rel_error(xs[f].cpu().double().numpy(), xstar):.3e}"),
+                           "rel_resid": float(f"{inf.rel_resid:.3e}"), "outer_iters": inf.outer_iters,
+                           "inner_iters": inf.inner_iters_total}
+
+    # ---------------- end to end through the one-call API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        if A_host is None:
+            A_host, b_host = A.cpu(), b.cpu()
+        A_pin, b_pin = A_host.pin_memory(), b_host.pin_memory()
+        outs = {f: torch.empty(d, dtype=torch.float32, pin_memory=True) for f in families}
+
+        def e2e_step():
+            for f in families:
+                mihs.solve(A_pin, b_pin, p.lam, f, m, p.sd, seed=seed, out=outs[f],
+                           want_info=False, **kw)
+
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+        e2e = {"value": round(ws * len(families) / (ms_e2e / 1e3), 3), "unit": "solves/s",
+               "ms_per_step": round(ms_e2e, 4),
+               "h2d_bytes_per_step": len(families) * 4 * (n * d + n),
+               "d2h_bytes_per_step": len(families) * 4 * d}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        if A_host is None:
+            A_host, b_host = A.cpu(), b.cpu()
+        iters = {f: infos[f].outer_iters for f in families}
+        v, sample, detail = oracle_sample(A_host, b_host, p, families, iters)
+        cpu = {"value": round(v, 5), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample, "detail": detail}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{p.name}, SNR 40 dB, m={m} (4·sd, sd={p.sd:.2f}), "
+                                   f"one solve per family {families}",
+                       "n": n, "d": d, "m": m, "lambda": p.lam, "sd": round(p.sd, 3), "tol": args.tol,
+                       "stop": "‖Aᵀ(b−Ax)−λx‖ ≤ tol·‖Aᵀb‖", "eps_sub": 0.1,
+                       "families": families, "l2": "inputs larger than L2 (A = %.2f GB)" % (4 * n * d / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "gpu_launches": launches_per_step * args.steps,
+            "per_family_ms": per_family,
+            "kernel_ms": {"apass_avg": round(apass_avg_s * 1e3, 4), "aab_avg": round(aab_ms / max(aab_n, 1), 4),
+                          "aab_launches": aab_n, "sketch_total": round(sk_ms, 4)},
+            "roofline": roofline,
+            "accuracy": accuracy,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "host_wall_s_timed": round(wall, 3),
+        }
+        print(json.dumps(out), flush=True)
+    for sk in sketches.values():
+        sk.close()
+
+
+def run_reference(args, ws, rank, families):
+    """The oracle, as it stands, on the host cores (bounded sample per step)."""
+    if rank != 0:
+        return
+    from paper_1912_03514_gb300 import workloads as W
+    p = W.problem_bandwidth(device="cpu", seed=1001, n=args.n, d=args.d)
+    iters = {f: 25 for f in families}  # fixed iteration budget per solve for the estimate
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, sample, _ = oracle_sample(p.A, p.b, p, families, iters, quick=True)
+        if k >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "solves/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{p.name}, SNR 40 dB, m={p.m}, one solve per family {families}",
+                      "n": p.n, "d": p.d, "m": p.m, "families": families},
+           "cpu_baseline": {"value": round(v, 5), "unit": "solves/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": sample + " (25 iterations assumed per solve)"},
+           "e2e": {"value": round(v, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mihs.h — C ABI of the GB300 Momentum Iterative Hessian Sketch (M-IHS) ridge
+ * solver (Ozaslan, Pilanci, Arikan, "M-IHS: A Momentum-based Iterative
+ * Hessian Sketch ...", arXiv 1912.03514).
+ *
+ * Problem (Section 1, Eq. "intro"):
+ *     x* = argmin_x  ½‖Ax − b‖² + (λ/2)‖x‖²,   A ∈ R^{n×d}, n ≥ d, λ > 0.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are fp32, row-major, with a leading dimension (row pitch, in
+ *     elements) `ld* ≥ columns`; `lda` must be a multiple of 4 and `A` 16-byte
+ *     aligned (the kernels read rows with 128-bit loads).  Vectors are fp32.
+ *   - Every pointer to array data is DEVICE memory owned by the caller unless
+ *     the argument says otherwise.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; only calls that return
+ *     host-visible results (an `info` struct, a host scalar) synchronise it.
+ *   - Return value: MIHS_OK (0) on success, MIHS_NOT_CONVERGED (+1) when a
+ *     solve stopped at its iteration cap (the output is still written), or a
+ *     negative MIHS_ERR_* code.  mihs_last_error() gives a message for the
+ *     most recent failure on the calling host thread.  No C++ exception
+ *     crosses this boundary.
+ *   - Limits: 1 ≤ d ≤ 2048, d ≤ n < 2^31, 1 ≤ m ≤ n.
+ */
+#ifndef MIHS_H
+#define MIHS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MIHS_OK = 0,
+  MIHS_NOT_CONVERGED = 1,
+  MIHS_ERR_INVALID_ARG = -1,
+  MIHS_ERR_CUDA = -2,
+  MIHS_ERR_OOM = -3,
+  MIHS_ERR_TIMEOUT = -4,
+  MIHS_ERR_NUMERIC = -5,
+  MIHS_ERR_UNSUPPORTED = -6
+};
+
+/* Sketch families of Lemma 3 (cases iv, i, iii).  All satisfy E[SᵀS] = I
+ * (text after Algorithm 1).  S is never stored: it is a function of (family,
+ * seed, m, n) through the counter-based generator Philox4x32-10.
+ *   MIHS_GAUSSIAN    S_ij ~ N(0, 1/m) (proof of Lemma 3, case iv).  Entry
+ *                    (i, j) is a Box–Muller normal from Philox counter
+ *                    (⌊j/4⌋, i, 0, 0), key (seed mod 2³², seed div 2³²).
+ *   MIHS_COUNTSKETCH one ±1 per column (Lemma 3, case i): column j goes to
+ *                    row h(j) = ⌊w0·m/2³²⌋ with sign + if w1 even, from
+ *                    counter (j, 0, 1, 0).
+ *   MIHS_SRHT        S = √(n_p/m)·P·(H/√n_p)·D (Lemma 3, case iii) with
+ *                    n_p = 2^⌈log₂ n⌉ (A zero-padded), D_j from counter
+ *                    (j, 0, 2, 0), P's m rows drawn with replacement from
+ *                    counter (i, 0, 3, 0).                                  */
+enum { MIHS_GAUSSIAN = 0, MIHS_COUNTSKETCH = 1, MIHS_SRHT = 2 };
+
+/* Human-readable name of a return code (static string). */
+const char* mihs_strerror(int code);
+/* Message describing the last failure on this host thread ("" if none). */
+const char* mihs_last_error(void);
+/* Number of kernels this library has launched in this process so far. */
+uint64_t mihs_launch_count(void);
+
+/* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
+ * the records and starts recording CUDA events on the launching stream around
+ * every gradient A-pass kernel (timer 0), AAb_Solver kernel (timer 1) and
+ * sketch call (timer 2); while it is on, mihs_solve runs its steps as host-
+ * driven launches and reads the stop flag back after each step, so only
+ * launches that did work are recorded.  mihs_timing(0) stops recording.
+ * mihs_timing_read synchronises on the recorded events and returns the summed
+ * duration (ms) and the number of launches of one timer. */
+int mihs_timing(int on);
+int mihs_timing_read(int which, double* total_ms, int64_t* count);
+
+/* ------------------------------------------------------------------------
+ * Building blocks: one call per step of Algorithm 1.
+ * ---------------------------------------------------------------------- */
+
+/* RP_fun of Algorithm 1 (sketch step): SA = S·A.
+ *   A      n×d, leading dimension lda.
+ *   SA     output, m×d, leading dimension ldsa ≥ d (overwritten).
+ *   family MIHS_GAUSSIAN | MIHS_COUNTSKETCH | MIHS_SRHT; seed keys S.
+ * May allocate stream-ordered scratch (cudaMallocAsync) that it frees on the
+ * same stream.  Errors: INVALID_ARG (sizes, alignment, family), CUDA, OOM. */
+int mihs_sketch_apply(const float* A, int64_t n, int64_t d, int64_t lda,
+                      int family, int64_t m, uint64_t seed,
+                      float* SA, int64_t ldsa, void* stream);
+
+/* Gradient step of Algorithm 1: g = Aᵀ(b − Ax) − λx, reading A once.
+ *   b (n), x (d) inputs; g (d) output.  λ ≥ 0.
+ * Allocates stream-ordered scratch for the split-K partial sums (one d-vector
+ * per thread block) and frees it on the same stream.  The reduction order is
+ * fixed, so repeated calls give bit-identical g.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda,
+                  const float* b, const float* x, double lambda, float* g,
+                  void* stream);
+
+/* AAb_Solver (Algorithm 5, Section 3.6): approximately solve
+ *     (SAᵀSA + λI) Δ = g
+ * by upper bidiagonalisation of SA, stopping when the relative residual
+ * estimate t < eps_sub or after `max_inner` loop passes (≤ 0: min(m, d)).
+ *   SA m×d (ld ldsa), g (d) inputs; delta (d) output.
+ *   passes: optional DEVICE int* receiving the number of loop passes.
+ * Runs as one thread-block cluster; allocates nothing.
+ * Errors: INVALID_ARG (λ ≤ 0, eps_sub < 0, sizes), CUDA. */
+int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa,
+                   const float* g, double lambda, double eps_sub, int max_inner,
+                   float* delta, int* passes, void* stream);
+
+/* AAb_Solver followed by the heavy-ball step of Eq. mihs1:
+ *     x⁺ = x + αΔ + β(x − x⁻),  then x⁻ ← x, x ← x⁺   (in place).
+ * Same arguments as mihs_aab_solve plus α, β and the DEVICE d-vectors x and
+ * x_prev (both read and overwritten).  Δ is not written out. */
+int mihs_aab_heavy_ball(const float* SA, int64_t m, int64_t d, int64_t ldsa,
+                        const float* g, double lambda, double eps_sub,
+                        int max_inner, double alpha, double beta,
+                        float* x, float* x_prev, int* passes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * The solver (Algorithm 1, M-IHS for n ≥ d).
+ * ---------------------------------------------------------------------- */
+
+typedef struct mihs_sketch_s* mihs_sketch_t;
+
+/* Form and keep SA = S·A (Algorithm 1, sketch step) for later solves with
+ * the same A.  The handle owns SA and the solver's workspace (allocated here
+ * with cudaMalloc; freed by mihs_sketch_destroy).  `A` itself is not kept.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family,
+                int64_t m, uint64_t seed, void* stream, mihs_sketch_t* out);
+
+/* Recompute the handle's SA for a new matrix of the same shape (n×d) and/or
+ * a new seed, reusing its memory (no allocation of the handle's own buffers;
+ * the sketch kernels' stream-ordered scratch as in mihs_sketch_apply).
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed,
+                  void* stream);
+
+/* Read-only view of a handle: device pointer to SA (m×d, leading dimension
+ * d rounded up to a multiple of 4) and sizes.
+ * Any output pointer may be NULL. */
+int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m,
+                     int64_t* d, int64_t* n, int* family);
+
+/* Copy the handle's SA (m×d) into the caller's DEVICE buffer `dst` with
+ * leading dimension ldd ≥ d, on `stream`. */
+int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream);
+
+/* Release a handle (synchronises the device first).  NULL is a no-op. */
+int mihs_sketch_destroy(mihs_sketch_t sk);
+
+typedef struct {
+  double tol;       /* stop when ‖g‖ ≤ tol·‖Aᵀb‖ (relative normal-equation
+                       residual; checked after every gradient step); ≤ 0
+                       disables the test                                   */
+  int max_outer;    /* N of Algorithm 1: at most this many momentum steps   */
+  double eps_sub;   /* forcing term ε_sub of AAb_Solver (0.1 in the paper)  */
+  int max_inner;    /* cap on AAb_Solver passes per step (≤ 0: min(m, d))   */
+  double sd;        /* statistical dimension estimate, 0 < sd < m; gives
+                       β = sd/m and α = (1 − β)² (Corollary 3)             */
+  int warm_start;   /* 0: x is ignored and the iteration starts at 0;
+                       1: x holds x¹ (costs one extra pass over A for ‖Aᵀb‖) */
+} mihs_opts;
+
+typedef struct {
+  int outer_iters;        /* momentum steps taken                          */
+  int inner_iters_total;  /* AAb_Solver passes summed over the steps       */
+  double rel_resid;       /* ‖g(x)‖/‖Aᵀb‖ of the returned x                */
+  int status;             /* MIHS_OK, MIHS_NOT_CONVERGED or MIHS_ERR_NUMERIC */
+} mihs_info;
+
+/* Default options: tol 1e-6, max_outer 100, eps_sub 0.1, max_inner 0,
+ * sd must still be set by the caller. */
+mihs_opts mihs_default_opts(void);
+
+/* Run Algorithm 1 with the handle's SA on the problem (A, b, λ).
+ * The outer loop runs on the device: a CUDA graph with a conditional WHILE
+ * node (body: gradient A-pass, partial-sum reduce, AAb_Solver + heavy ball)
+ * that the AAb kernel stops when the test fires, so a solve costs one graph
+ * launch plus two small launches.  The graph is cached in the handle and
+ * rebuilt when A, lda, b, x, λ, α, β, eps_sub or max_inner change.  Setting
+ * the environment variable MIHS_NO_GRAPH makes the host drive the steps.
+ *   A     n×d (same n, d as the handle), leading dimension lda.
+ *   b     n-vector.  λ > 0.
+ *   x     d-vector: x¹ on entry if opts->warm_start, the solution on exit.
+ *   info  optional HOST struct; when non-NULL the call synchronises the
+ *         stream and fills it, and the return value reflects convergence
+ *         (MIHS_NOT_CONVERGED / MIHS_ERR_NUMERIC).  When NULL the call only
+ *         enqueues work and returns MIHS_OK.
+ * A handle must not be used by two solves that overlap in time.
+ * Errors: INVALID_ARG (λ ≤ 0, sd ∉ (0, m), sizes), CUDA, NUMERIC. */
+int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
+               double lambda, const mihs_opts* opts, float* x, mihs_info* info,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MIHS_H */

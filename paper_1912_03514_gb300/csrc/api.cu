@@ -1,0 +1,553 @@
+// C ABI of libmihs: argument checks, handles and the host side of Algorithm 1.
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace mihs {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int num_sms() {
+  static std::mutex mu;
+  static std::vector<int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+  if (cache[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+namespace {
+
+struct Timing {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> ev[kNumTimers];  // (start, stop) pairs
+  size_t used[kNumTimers] = {0, 0, 0};
+};
+Timing& timing_state() {
+  static Timing* t = new Timing();  // never destroyed: events outlive static teardown
+  return *t;
+}
+
+}  // namespace
+
+bool timing_on() { return timing_state().on; }
+
+void timing_begin(int which, cudaStream_t s) {
+  Timing& t = timing_state();
+  if (!t.on) return;
+  std::lock_guard<std::mutex> lk(t.mu);
+  const size_t i = t.used[which];
+  while (t.ev[which].size() < 2 * i + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    t.ev[which].push_back(e);
+  }
+  cudaEventRecord(t.ev[which][2 * i], s);
+}
+
+void timing_end(int which, cudaStream_t s) {
+  Timing& t = timing_state();
+  if (!t.on) return;
+  std::lock_guard<std::mutex> lk(t.mu);
+  const size_t i = t.used[which];
+  if (t.ev[which].size() < 2 * i + 2) return;
+  cudaEventRecord(t.ev[which][2 * i + 1], s);
+  t.used[which] = i + 1;
+}
+
+namespace {
+
+__global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol) {
+  SolveCtl c = {};
+  c.max_outer = max_outer;
+  c.tol = tol;
+  c.status = MIHS_OK;
+  *ctl = c;
+}
+
+// ‖g‖ for the warm-start reference norm ‖Aᵀb‖ (one block, fixed order).
+__global__ void ctl_set_gnorm0_kernel(SolveCtl* ctl, const float* g, int d) {
+  __shared__ float red[32];
+  float s = 0.f;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s = fmaf(g[j], g[j], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    ctl->gnorm0 = sqrtf(t);
+    ctl->gnorm0_known = 1;
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_matrix(const float* A, int64_t n, int64_t d, int64_t lda, const char* what) {
+  MIHS_ARG(A != nullptr, "%s: null matrix", what);
+  MIHS_ARG(d >= 1 && d <= kMaxD, "%s: d=%lld outside [1, %d]", what, (long long)d, kMaxD);
+  MIHS_ARG(n >= 1 && n < (1LL << 31), "%s: n=%lld outside [1, 2^31)", what, (long long)n);
+  MIHS_ARG(lda >= d && lda % 4 == 0, "%s: lda=%lld must be >= d and a multiple of 4", what,
+           (long long)lda);
+  MIHS_ARG(aligned16(A), "%s: matrix pointer must be 16-byte aligned", what);
+  return MIHS_OK;
+}
+
+}  // namespace
+}  // namespace mihs
+
+using namespace mihs;
+
+struct mihs_sketch_s {
+  int device;
+  int64_t n, d, m, dp;
+  int family;
+  uint64_t seed;
+  int P;              // split-K partials of the A-pass
+  float* SA;          // m × dp
+  float* partials;    // P × dp
+  float* g;           // dp
+  float* x_prev;      // dp
+  SolveCtl* ctl;
+  SolveCtl* ctl_host; // pinned
+  // Device-side outer loop: a CUDA graph holding one conditional WHILE node
+  // whose body is (A-pass, partial-sum reduce, AAb + heavy ball); the AAb
+  // kernel clears the condition when the stop test fires.  Rebuilt when the
+  // solve's pointers or scalars change.
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
+  struct Key {
+    const float* A; int64_t lda; const float* b; float* x;
+    float lam, alpha, beta, eps; int max_passes;
+    bool operator==(const Key& o) const {
+      return A == o.A && lda == o.lda && b == o.b && x == o.x && lam == o.lam &&
+             alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
+    }
+  } key = {};
+};
+
+namespace {
+
+void drop_graph(mihs_sketch_s* sk) {
+  if (sk->exec) cudaGraphExecDestroy(sk->exec);
+  if (sk->graph) cudaGraphDestroy(sk->graph);
+  sk->exec = nullptr;
+  sk->graph = nullptr;
+}
+
+// Captures the loop body into a conditional WHILE node.  Returns MIHS_OK or
+// an error (the caller then falls back to host-driven iterations).
+int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto) {
+  drop_graph(sk);
+  if (!sk->cap) MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&sk->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  MIHS_CUDA_TRY(cudaGraphCreate(&g, 0));
+  sk->graph = g;
+  cudaGraphConditionalHandle h;
+  MIHS_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MIHS_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  aab_prepare((int)sk->m, (int)sk->d);
+  MIHS_CUDA_TRY(cudaStreamBeginCaptureToGraph(sk->cap, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+  AabLaunch a = proto;
+  a.cond = (unsigned long long)h;
+  int rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, key.x, sk->partials, sk->ctl, sk->cap);
+  if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, key.x, key.lam, sk->g, sk->ctl, sk->cap);
+  if (!rc) rc = launch_aab(a, sk->cap);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(sk->cap, &out);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    set_error("graph capture: %s", cudaGetErrorString(e));
+    return MIHS_ERR_CUDA;
+  }
+  MIHS_CUDA_TRY(cudaGraphInstantiate(&sk->exec, g, 0));
+  sk->key = key;
+  return MIHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mihs_strerror(int code) {
+  switch (code) {
+    case MIHS_OK: return "ok";
+    case MIHS_NOT_CONVERGED: return "not converged within max_outer";
+    case MIHS_ERR_INVALID_ARG: return "invalid argument";
+    case MIHS_ERR_CUDA: return "CUDA error";
+    case MIHS_ERR_OOM: return "out of device memory";
+    case MIHS_ERR_TIMEOUT: return "device wait timed out";
+    case MIHS_ERR_NUMERIC: return "non-finite value encountered";
+    case MIHS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+const char* mihs_last_error(void) { return g_err; }
+
+uint64_t mihs_launch_count(void) { return g_launches.load(); }
+
+mihs_opts mihs_default_opts(void) {
+  mihs_opts o;
+  o.tol = 1e-6;
+  o.max_outer = 100;
+  o.eps_sub = 0.1;
+  o.max_inner = 0;
+  o.sd = 0.0;
+  o.warm_start = 0;
+  return o;
+}
+
+int mihs_sketch_apply(const float* A, int64_t n, int64_t d, int64_t lda, int family, int64_t m,
+                      uint64_t seed, float* SA, int64_t ldsa, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_sketch_apply");
+  if (rc) return rc;
+  MIHS_ARG(SA != nullptr, "mihs_sketch_apply: null SA");
+  MIHS_ARG(m >= 1 && m <= n, "mihs_sketch_apply: m=%lld outside [1, n]", (long long)m);
+  MIHS_ARG(ldsa >= d, "mihs_sketch_apply: ldsa < d");
+  MIHS_ARG(family >= MIHS_GAUSSIAN && family <= MIHS_SRHT, "mihs_sketch_apply: unknown family %d",
+           family);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  timing_begin(kTimerSketch, s);
+  switch (family) {
+    case MIHS_GAUSSIAN: rc = sketch_gaussian(A, n, d, lda, m, seed, SA, ldsa, s); break;
+    case MIHS_COUNTSKETCH: rc = sketch_countsketch(A, n, d, lda, m, seed, SA, ldsa, s); break;
+    default: rc = sketch_srht(A, n, d, lda, m, seed, SA, ldsa, s); break;
+  }
+  timing_end(kTimerSketch, s);
+  return rc;
+}
+
+int mihs_timing(int on) {
+  Timing& t = timing_state();
+  std::lock_guard<std::mutex> lk(t.mu);
+  t.on = on != 0;
+  for (int w = 0; w < kNumTimers; ++w) t.used[w] = 0;
+  return MIHS_OK;
+}
+
+int mihs_timing_read(int which, double* total_ms, int64_t* count) {
+  set_error("");
+  MIHS_ARG(which >= 0 && which < kNumTimers, "mihs_timing_read: bad timer %d", which);
+  MIHS_ARG(total_ms != nullptr && count != nullptr, "mihs_timing_read: null output");
+  Timing& t = timing_state();
+  std::lock_guard<std::mutex> lk(t.mu);
+  double tot = 0.0;
+  for (size_t i = 0; i < t.used[which]; ++i) {
+    MIHS_CUDA_TRY(cudaEventSynchronize(t.ev[which][2 * i + 1]));
+    float ms = 0.f;
+    MIHS_CUDA_TRY(cudaEventElapsedTime(&ms, t.ev[which][2 * i], t.ev[which][2 * i + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *count = (int64_t)t.used[which];
+  return MIHS_OK;
+}
+
+int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda, const float* b,
+                  const float* x, double lambda, float* g, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_gradient");
+  if (rc) return rc;
+  MIHS_ARG(b != nullptr && x != nullptr && g != nullptr, "mihs_gradient: null vector");
+  MIHS_ARG(lambda >= 0.0 && std::isfinite(lambda), "mihs_gradient: lambda must be finite, >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = apass_num_partials(n, d);
+  StreamScratch scratch;
+  rc = scratch.alloc(sizeof(float) * (size_t)P * apass_dpad(d), s);
+  if (rc) return rc;
+  float* part = static_cast<float*>(scratch.p);
+  rc = launch_apass_partial(A, n, d, lda, b, x, part, nullptr, s);
+  if (rc) return rc;
+  return launch_apass_finalize(part, P, d, x, (float)lambda, g, nullptr, s);
+}
+
+static int aab_common(const float* SA, int64_t m, int64_t d, int64_t ldsa, const float* g,
+                      double lambda, double eps_sub, int max_inner, const char* who) {
+  MIHS_ARG(SA != nullptr && g != nullptr, "%s: null pointer", who);
+  MIHS_ARG(m >= 1 && m < (1LL << 31), "%s: m=%lld out of range", who, (long long)m);
+  MIHS_ARG(d >= 1 && d <= kMaxD, "%s: d=%lld outside [1, %d]", who, (long long)d, kMaxD);
+  MIHS_ARG(ldsa >= d && ldsa % 4 == 0, "%s: ldsa must be >= d and a multiple of 4", who);
+  MIHS_ARG(aligned16(SA), "%s: SA must be 16-byte aligned", who);
+  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "%s: lambda must be > 0", who);
+  MIHS_ARG(eps_sub >= 0.0, "%s: eps_sub must be >= 0", who);
+  (void)max_inner;
+  return MIHS_OK;
+}
+
+static int cap_passes(int64_t m, int64_t d, int max_inner) {
+  const int64_t mn = m < d ? m : d;
+  return (int)(max_inner > 0 && max_inner < mn ? max_inner : mn);
+}
+
+int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa, const float* g,
+                   double lambda, double eps_sub, int max_inner, float* delta, int* passes,
+                   void* stream) {
+  set_error("");
+  int rc = aab_common(SA, m, d, ldsa, g, lambda, eps_sub, max_inner, "mihs_aab_solve");
+  if (rc) return rc;
+  MIHS_ARG(delta != nullptr, "mihs_aab_solve: null delta");
+  AabLaunch a = {};
+  a.SA = SA;
+  a.m = (int)m;
+  a.d = (int)d;
+  a.ldsa = ldsa;
+  a.g = g;
+  a.lambda = (float)lambda;
+  a.eps = (float)eps_sub;
+  a.max_passes = cap_passes(m, d, max_inner);
+  a.delta = delta;
+  a.passes = passes;
+  return launch_aab(a, static_cast<cudaStream_t>(stream));
+}
+
+int mihs_aab_heavy_ball(const float* SA, int64_t m, int64_t d, int64_t ldsa, const float* g,
+                        double lambda, double eps_sub, int max_inner, double alpha, double beta,
+                        float* x, float* x_prev, int* passes, void* stream) {
+  set_error("");
+  int rc = aab_common(SA, m, d, ldsa, g, lambda, eps_sub, max_inner, "mihs_aab_heavy_ball");
+  if (rc) return rc;
+  MIHS_ARG(x != nullptr && x_prev != nullptr, "mihs_aab_heavy_ball: null x or x_prev");
+  AabLaunch a = {};
+  a.SA = SA;
+  a.m = (int)m;
+  a.d = (int)d;
+  a.ldsa = ldsa;
+  a.g = g;
+  a.lambda = (float)lambda;
+  a.eps = (float)eps_sub;
+  a.max_passes = cap_passes(m, d, max_inner);
+  a.passes = passes;
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  a.x = x;
+  a.x_prev = x_prev;
+  return launch_aab(a, static_cast<cudaStream_t>(stream));
+}
+
+int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, int64_t m,
+                uint64_t seed, void* stream, mihs_sketch_t* out) {
+  set_error("");
+  MIHS_ARG(out != nullptr, "mihs_sketch: null out");
+  *out = nullptr;
+  int rc = check_matrix(A, n, d, lda, "mihs_sketch");
+  if (rc) return rc;
+  MIHS_ARG(m >= 1 && m <= n, "mihs_sketch: m=%lld outside [1, n]", (long long)m);
+  MIHS_ARG(family >= MIHS_GAUSSIAN && family <= MIHS_SRHT, "mihs_sketch: unknown family %d", family);
+  mihs_sketch_s* h = new (std::nothrow) mihs_sketch_s();
+  if (!h) return MIHS_ERR_OOM;
+  MIHS_CUDA_TRY(cudaGetDevice(&h->device));
+  h->n = n;
+  h->d = d;
+  h->m = m;
+  h->dp = apass_dpad(d);
+  h->family = family;
+  h->seed = seed;
+  h->P = apass_num_partials(n, d);
+  const size_t bytes = sizeof(float) * ((size_t)m * h->dp + (size_t)h->P * h->dp + 2 * h->dp) +
+                       sizeof(SolveCtl) + 256;
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    set_error("mihs_sketch: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+  }
+  h->SA = reinterpret_cast<float*>(base);
+  h->partials = h->SA + (size_t)m * h->dp;
+  h->g = h->partials + (size_t)h->P * h->dp;
+  h->x_prev = h->g + h->dp;
+  h->ctl = reinterpret_cast<SolveCtl*>(round_up(reinterpret_cast<uintptr_t>(h->x_prev + h->dp), 64));
+  e = cudaMallocHost(&h->ctl_host, sizeof(SolveCtl));
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    delete h;
+    set_error("mihs_sketch: cudaMallocHost: %s", cudaGetErrorString(e));
+    return MIHS_ERR_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->dp != d) cudaMemsetAsync(h->SA, 0, sizeof(float) * (size_t)m * h->dp, s);
+  rc = mihs_sketch_apply(A, n, d, lda, family, m, seed, h->SA, h->dp, stream);
+  if (rc) {
+    cudaStreamSynchronize(s);
+    cudaFreeHost(h->ctl_host);
+    cudaFree(base);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MIHS_OK;
+}
+
+int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr, "mihs_resketch: null handle");
+  int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_resketch");
+  if (rc) return rc;
+  sk->seed = seed;
+  return mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
+}
+
+int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m, int64_t* d, int64_t* n,
+                     int* family) {
+  MIHS_ARG(sk != nullptr, "mihs_sketch_info: null handle");
+  if (SA) *SA = sk->SA;
+  if (m) *m = sk->m;
+  if (d) *d = sk->d;
+  if (n) *n = sk->n;
+  if (family) *family = sk->family;
+  return MIHS_OK;
+}
+
+int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr && dst != nullptr, "mihs_sketch_copy: null argument");
+  MIHS_ARG(ldd >= sk->d, "mihs_sketch_copy: ldd < d");
+  MIHS_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(float) * (size_t)ldd, sk->SA, sizeof(float) * (size_t)sk->dp,
+                                  sizeof(float) * (size_t)sk->d, (size_t)sk->m, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream)));
+  return MIHS_OK;
+}
+
+int mihs_sketch_destroy(mihs_sketch_t sk) {
+  if (sk == nullptr) return MIHS_OK;
+  cudaDeviceSynchronize();
+  drop_graph(sk);
+  if (sk->cap) cudaStreamDestroy(sk->cap);
+  cudaFreeHost(sk->ctl_host);
+  cudaFree(sk->SA);
+  delete sk;
+  return MIHS_OK;
+}
+
+int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
+               const mihs_opts* opts, float* x, mihs_info* info, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr && opts != nullptr, "mihs_solve: null handle or opts");
+  int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve");
+  if (rc) return rc;
+  MIHS_ARG(b != nullptr && x != nullptr, "mihs_solve: null b or x");
+  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve: lambda must be > 0");
+  MIHS_ARG(opts->sd > 0.0 && opts->sd < (double)sk->m,
+           "mihs_solve: sd=%g must lie in (0, m=%lld)", opts->sd, (long long)sk->m);
+  MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
+  MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve: eps_sub must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = sk->n, d = sk->d;
+  // Corollary 3: β = sd/m, α = (1 − β)².
+  const double beta = opts->sd / (double)sk->m;
+  const double alpha = (1.0 - beta) * (1.0 - beta);
+
+  ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol);
+  MIHS_CHECK_LAUNCH();
+  count_launch();
+  if (opts->warm_start) {
+    // ‖Aᵀb‖ = ‖g(0)‖ for the relative residual.
+    rc = launch_apass_partial(A, n, d, lda, b, nullptr, sk->partials, nullptr, s);
+    if (rc) return rc;
+    rc = launch_apass_finalize(sk->partials, sk->P, d, nullptr, 0.f, sk->g, nullptr, s);
+    if (rc) return rc;
+    ctl_set_gnorm0_kernel<<<1, 256, 0, s>>>(sk->ctl, sk->g, (int)d);
+    MIHS_CHECK_LAUNCH();
+    count_launch();
+  } else {
+    MIHS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)d, s));
+  }
+  MIHS_CUDA_TRY(cudaMemcpyAsync(sk->x_prev, x, sizeof(float) * (size_t)d, cudaMemcpyDeviceToDevice, s));
+
+  AabLaunch a = {};
+  a.SA = sk->SA;
+  a.m = (int)sk->m;
+  a.d = (int)d;
+  a.ldsa = sk->dp;
+  a.g = sk->g;
+  a.lambda = (float)lambda;
+  a.eps = (float)opts->eps_sub;
+  a.max_passes = cap_passes(sk->m, d, opts->max_inner);
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  a.x = x;
+  a.x_prev = sk->x_prev;
+  a.ctl = sk->ctl;
+  // Algorithm 1: up to max_outer momentum steps, each after a gradient.
+  const mihs_sketch_s::Key key = {A, lda, b, x, (float)lambda, a.alpha, a.beta, a.eps, a.max_passes};
+  bool graph_ran = false;
+  if (!timing_on() && !sk->graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
+    if (!(sk->exec && sk->key == key)) {
+      if (build_graph(sk, key, a) != MIHS_OK) {
+        drop_graph(sk);
+        sk->graph_failed = true;  // keep the message; use host-driven steps from now on
+        cudaGetLastError();
+      }
+    }
+    if (sk->exec) {
+      MIHS_CUDA_TRY(cudaGraphLaunch(sk->exec, s));
+      graph_ran = true;
+    }
+  }
+  if (!graph_ran) {
+    // Host-driven steps; the kernels return at once after the stop test has
+    // fired (ctl->done).  With per-kernel timing on, the flag is read back
+    // after every step so that only working launches are timed.
+    for (int it = 0; it <= opts->max_outer; ++it) {
+      rc = launch_apass_partial(A, n, d, lda, b, x, sk->partials, sk->ctl, s);
+      if (rc) return rc;
+      rc = launch_apass_finalize(sk->partials, sk->P, d, x, (float)lambda, sk->g, sk->ctl, s);
+      if (rc) return rc;
+      rc = launch_aab(a, s);
+      if (rc) return rc;
+      if (timing_on()) {
+        MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ctl_host, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+        MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (sk->ctl_host->done) break;
+      }
+    }
+  }
+  if (info == nullptr) return MIHS_OK;
+  MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ctl_host, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+  MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+  const SolveCtl& c = *sk->ctl_host;
+  info->outer_iters = c.outer;
+  info->inner_iters_total = c.inner_total;
+  info->rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
+  info->status = c.done ? c.status : MIHS_NOT_CONVERGED;
+  if (graph_ran) count_launch(3ull * (uint64_t)(c.outer + 1));
+  return info->status;
+}
+
+}  // extern "C"

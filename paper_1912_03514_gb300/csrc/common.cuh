@@ -1,0 +1,108 @@
+// Shared device helpers and host plumbing of libmihs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+
+#include "../../include/mihs.h"
+
+namespace mihs {
+
+// ---------------------------------------------------------------- host side
+// Last error message of this host thread (mihs_last_error()).
+void set_error(const char* fmt, ...);
+// Counts kernel launches for mihs_launch_count().
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int num_sms();                // SM count of the current device (cached per device)
+
+#define MIHS_CUDA_TRY(expr)                                                        \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      ::mihs::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,               \
+                        cudaGetErrorString(_e));                                   \
+      return _e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;       \
+    }                                                                              \
+  } while (0)
+
+#define MIHS_CHECK_LAUNCH()                                                        \
+  do {                                                                             \
+    cudaError_t _e = cudaGetLastError();                                           \
+    if (_e != cudaSuccess) {                                                       \
+      ::mihs::set_error("%s:%d: kernel launch: %s", __FILE__, __LINE__,           \
+                        cudaGetErrorString(_e));                                   \
+      return MIHS_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+#define MIHS_ARG(cond, ...)                                                        \
+  do {                                                                             \
+    if (!(cond)) {                                                                 \
+      ::mihs::set_error(__VA_ARGS__);                                              \
+      return MIHS_ERR_INVALID_ARG;                                                 \
+    }                                                                              \
+  } while (0)
+
+constexpr int kMaxD = 2048;
+
+inline int64_t round_up(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
+
+// Control block of one solve, in device memory (written by the kernels).
+struct SolveCtl {
+  int done;          // 1 once the solve has stopped: later kernels return at once
+  int outer;         // momentum steps taken
+  int inner_total;   // AAb passes summed
+  int status;        // MIHS_OK / MIHS_NOT_CONVERGED / MIHS_ERR_NUMERIC
+  int max_outer;
+  int gnorm0_known;  // ‖Aᵀb‖ already in gnorm0
+  float tol;         // stop when ‖g‖ ≤ tol·‖Aᵀb‖
+  float gnorm0;      // ‖Aᵀb‖
+  float gnorm;       // ‖g‖ of the current x
+  float pad[3];
+};
+
+// ------------------------------------------------------------- device side
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (c0,c1,c2,c3) → (hi(M1·c2)⊕c1⊕k0, lo(M1·c2), hi(M0·c0)⊕c3⊕k1, lo(M0·c0)),
+// key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Box–Muller on 24-bit uniforms: u1 = (⌊a/2⁸⌋+1)·2⁻²⁴ ∈ (0,1] and
+// u2 = ⌊b/2⁸⌋·2⁻²⁴ ∈ [0,1) are exact in fp32; r = √(−2 ln u1),
+// (z0, z1) = (r cos 2πu2, r sin 2πu2).
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
+  const float u2 = (float)(b >> 8) * 0x1p-24f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+enum : uint32_t { kTagGaussian = 0, kTagCountSketch = 1, kTagSrhtSigns = 2, kTagSrhtRows = 3 };
+
+}  // namespace mihs

@@ -1,0 +1,80 @@
+// Host-side launchers shared between the translation units of libmihs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mihs {
+
+// ---- gradient A-pass (apass.cu) -------------------------------------------
+// Number of split-K partial d-vectors the A-pass writes for an n×d problem.
+int apass_num_partials(int64_t n, int64_t d);
+// Row pitch (floats) of the partial buffer.
+inline int64_t apass_dpad(int64_t d) { return round_up(d, 4); }
+// partials[p][j] = Σ_{rows of block p} A[i][j]·(b[i] − A[i]·x).  x may be
+// NULL (taken as 0).  Skips all work when ctl != NULL and ctl->done.
+int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda,
+                         const float* b, const float* x, float* partials,
+                         const SolveCtl* ctl, cudaStream_t s);
+// g[j] = Σ_p partials[p][j] − λ·x[j] in a fixed order.
+int launch_apass_finalize(const float* partials, int P, int64_t d,
+                          const float* x, float lambda, float* g,
+                          const SolveCtl* ctl, cudaStream_t s);
+
+// ---- AAb_Solver (aab.cu) --------------------------------------------------
+struct AabLaunch {
+  const float* SA;
+  int m, d;
+  int64_t ldsa;
+  const float* g;
+  float lambda, eps;
+  int max_passes;      // already capped at min(m, d)
+  float* delta;        // written when non-NULL
+  int* passes;         // device, optional
+  // heavy ball (when x != NULL): x⁺ = x + αΔ + β(x − x⁻), x⁻ ← x
+  float alpha, beta;
+  float* x;
+  float* x_prev;
+  SolveCtl* ctl;       // solve mode (stop test, counters); may be NULL
+  unsigned long long cond;  // graph conditional handle to clear when the solve stops (0: none)
+};
+int launch_aab(const AabLaunch& a, cudaStream_t s);
+// Picks and caches the cluster shape for (m, d) (call outside stream capture).
+void aab_prepare(int m, int d);
+
+// ---- sketches (sketch_*.cu) ------------------------------------------------
+int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
+                    uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
+                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
+                uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+
+// ---- per-kernel event timing (api.cu) -------------------------------------
+enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kNumTimers = 3 };
+bool timing_on();
+void timing_begin(int which, cudaStream_t s);
+void timing_end(int which, cudaStream_t s);
+
+// Stream-ordered scratch that frees itself on the same stream.
+struct StreamScratch {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~StreamScratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  int alloc(size_t bytes, cudaStream_t stream) {
+    s = stream;
+    cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+    }
+    return MIHS_OK;
+  }
+};
+
+}  // namespace mihs

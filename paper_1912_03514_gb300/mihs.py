@@ -1,0 +1,297 @@
+"""Python binding of libmihs (ctypes).  Argument marshalling only: every step
+of the solver runs in the library's CUDA kernels.  The functions carry the
+names of the C entry points in include/mihs.h without the ``mihs_`` prefix.
+
+Tensors must be CUDA fp32 with unit column stride; row pitches are taken from
+``stride(0)``.  Work is enqueued on ``torch.cuda.current_stream()`` unless a
+stream is given.  There is no CPU fallback: without the built library every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
+FAMILIES = {"gaussian": GAUSSIAN, "countsketch": COUNTSKETCH, "srht": SRHT}
+OK, NOT_CONVERGED = 0, 1
+
+
+class MihsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(msg)
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("eps_sub", ctypes.c_double), ("max_inner", ctypes.c_int),
+                ("sd", ctypes.c_double), ("warm_start", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters_total", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+_i64, _u64, _vp, _dbl, _int = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmihs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmihs.so is not built ({path}); run "
+                           "`python -m paper_1912_03514_gb300._build` or __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    sig = {
+        "mihs_strerror": (ctypes.c_char_p, [_int]),
+        "mihs_last_error": (ctypes.c_char_p, []),
+        "mihs_launch_count": (_u64, []),
+        "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
+        "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
+        "mihs_aab_solve": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
+        "mihs_aab_heavy_ball": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _dbl, _dbl,
+                                       _vp, _vp, _vp, _vp]),
+        "mihs_sketch": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, ctypes.POINTER(_vp)]),
+        "mihs_sketch_info": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+        "mihs_resketch": (_int, [_vp, _vp, _i64, _u64, _vp]),
+        "mihs_sketch_copy": (_int, [_vp, _vp, _i64, _vp]),
+        "mihs_sketch_destroy": (_int, [_vp]),
+        "mihs_default_opts": (_Opts, []),
+        "mihs_timing": (_int, [_int]),
+        "mihs_timing_read": (_int, [_int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+        "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
+                              ctypes.POINTER(_Info), _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow_not_converged: bool = False) -> int:
+    if rc == 0 or (allow_not_converged and rc == NOT_CONVERGED):
+        return rc
+    L = lib()
+    raise MihsError(rc, f"{L.mihs_strerror(rc).decode()}: {L.mihs_last_error().decode()}")
+
+
+def _stream(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _mat(A: torch.Tensor, name: str):
+    if not (A.is_cuda and A.dtype == torch.float32 and A.dim() == 2 and A.stride(1) == 1):
+        raise ValueError(f"{name} must be a CUDA fp32 matrix with unit column stride")
+    return A.data_ptr(), A.shape[0], A.shape[1], A.stride(0)
+
+
+def _vec(v: torch.Tensor, n: int, name: str):
+    if not (v.is_cuda and v.dtype == torch.float32 and v.dim() == 1 and v.numel() == n
+            and v.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA fp32 vector of length {n}")
+    return v.data_ptr()
+
+
+def family_id(family) -> int:
+    return FAMILIES[family] if isinstance(family, str) else int(family)
+
+
+def launch_count() -> int:
+    return int(lib().mihs_launch_count())
+
+
+TIMER_APASS, TIMER_AAB, TIMER_SKETCH = 0, 1, 2
+
+
+def timing(on: bool) -> None:
+    """Start (clearing old records) or stop per-kernel event timing."""
+    _check(lib().mihs_timing(int(bool(on))))
+
+
+def timing_read(which: int):
+    """(total milliseconds, launches) recorded for one timer."""
+    ms, cnt = _dbl(), _i64()
+    _check(lib().mihs_timing_read(int(which), ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def sketch_apply(A: torch.Tensor, family, m: int, seed: int, SA: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """SA = S·A (the sketch step of Algorithm 1) into a new or given m×d tensor."""
+    pa, n, d, lda = _mat(A, "A")
+    if SA is None:
+        SA = torch.empty(m, d, dtype=torch.float32, device=A.device)
+    ps, mm, dd, ldsa = _mat(SA, "SA")
+    if (mm, dd) != (m, d):
+        raise ValueError("SA has the wrong shape")
+    _check(lib().mihs_sketch_apply(pa, n, d, lda, family_id(family), m, seed & (2**64 - 1),
+                                   ps, ldsa, _stream(stream)))
+    return SA
+
+
+def gradient(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
+             g: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """g = Aᵀ(b − Ax) − λx."""
+    pa, n, d, lda = _mat(A, "A")
+    if g is None:
+        g = torch.empty(d, dtype=torch.float32, device=A.device)
+    _check(lib().mihs_gradient(pa, n, d, lda, _vec(b, n, "b"), _vec(x, d, "x"), float(lam),
+                               _vec(g, d, "g"), _stream(stream)))
+    return g
+
+
+def aab_solve(SA: torch.Tensor, g: torch.Tensor, lam: float, eps_sub: float = 0.1,
+              max_inner: int = 0, delta: torch.Tensor | None = None,
+              passes: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Δ ≈ (SAᵀSA + λI)⁻¹ g by AAb_Solver (Algorithm 5)."""
+    ps, m, d, ldsa = _mat(SA, "SA")
+    if delta is None:
+        delta = torch.empty(d, dtype=torch.float32, device=SA.device)
+    pp = 0
+    if passes is not None:
+        assert passes.is_cuda and passes.dtype == torch.int32 and passes.numel() >= 1
+        pp = passes.data_ptr()
+    _check(lib().mihs_aab_solve(ps, m, d, ldsa, _vec(g, d, "g"), float(lam), float(eps_sub),
+                                int(max_inner), _vec(delta, d, "delta"), pp or None,
+                                _stream(stream)))
+    return delta
+
+
+def aab_heavy_ball(SA: torch.Tensor, g: torch.Tensor, lam: float, eps_sub: float, max_inner: int,
+                   alpha: float, beta: float, x: torch.Tensor, x_prev: torch.Tensor,
+                   passes: torch.Tensor | None = None, stream=None) -> None:
+    """AAb_Solver then x⁺ = x + αΔ + β(x − x⁻), x⁻ ← x (in place)."""
+    ps, m, d, ldsa = _mat(SA, "SA")
+    pp = passes.data_ptr() if passes is not None else None
+    _check(lib().mihs_aab_heavy_ball(ps, m, d, ldsa, _vec(g, d, "g"), float(lam), float(eps_sub),
+                                     int(max_inner), float(alpha), float(beta),
+                                     _vec(x, d, "x"), _vec(x_prev, d, "x_prev"), pp,
+                                     _stream(stream)))
+
+
+@dataclass
+class SolveInfo:
+    outer_iters: int
+    inner_iters_total: int
+    rel_resid: float
+    status: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+class Sketch:
+    """A handle holding SA = S·A (mihs_sketch) for repeated solves."""
+
+    def __init__(self, A: torch.Tensor, family, m: int, seed: int, stream=None):
+        pa, n, d, lda = _mat(A, "A")
+        h = ctypes.c_void_p()
+        _check(lib().mihs_sketch(pa, n, d, lda, family_id(family), int(m), seed & (2**64 - 1),
+                                 _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n, self.d, self.m = n, d, int(m)
+        self.family = family_id(family)
+        self.device = A.device
+
+    def resketch(self, A: torch.Tensor, seed: int, stream=None) -> None:
+        """Recompute SA for a new A of the same shape (reuses the handle's memory)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        _check(lib().mihs_resketch(self._h, pa, lda, seed & (2**64 - 1), _stream(stream)))
+
+    def sa(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.m, self.d, dtype=torch.float32, device=self.device)
+        _check(lib().mihs_sketch_copy(self._h, out.data_ptr(), self.d, _stream(stream)))
+        return out
+
+    def solve(self, A: torch.Tensor, b: torch.Tensor, lam: float, sd: float, tol: float = 1e-6,
+              max_outer: int = 100, eps_sub: float = 0.1, max_inner: int = 0,
+              x: torch.Tensor | None = None, warm_start: bool = False, want_info: bool = True,
+              stream=None):
+        """Algorithm 1 with this sketch.  Returns (x, SolveInfo or None)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        if x is None:
+            x = torch.empty(d, dtype=torch.float32, device=A.device)
+        o = lib().mihs_default_opts()
+        o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+        o.max_inner, o.sd, o.warm_start = int(max_inner), float(sd), int(bool(warm_start))
+        info = _Info()
+        rc = lib().mihs_solve(self._h, pa, lda, _vec(b, n, "b"), float(lam), ctypes.byref(o),
+                              _vec(x, d, "x"), ctypes.byref(info) if want_info else None,
+                              _stream(stream))
+        _check(rc, allow_not_converged=True)
+        if not want_info:
+            return x, None
+        return x, SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mihs_sketch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+_HANDLES: dict = {}
+
+
+def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: float, seed: int = 0,
+          out: torch.Tensor | None = None, **kw):
+    """Sketch A then run Algorithm 1: the one-call form.
+
+    A and b may live on the GPU or on the host (ideally pinned).  Host inputs
+    are copied to the current CUDA device and x is copied back (into `out`
+    when given), which makes this the end-to-end form of the solver.  One
+    sketch handle per (device, n, d, m, family) is kept and reused, so
+    repeated calls allocate nothing new.  Returns (x, SolveInfo or None).
+    """
+    host = not A.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if host:
+        A = A.to(dev, non_blocking=True)
+        b = b.to(dev, non_blocking=True)
+    key = (A.device.index, A.shape[0], A.shape[1], int(m), family_id(family))
+    sk = _HANDLES.get(key)
+    if sk is None:
+        sk = _HANDLES[key] = Sketch(A, family, m, seed)
+    else:
+        sk.resketch(A, seed)
+    x, info = sk.solve(A, b, lam, sd, **kw)
+    if host:
+        if out is None:
+            out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        out.copy_(x, non_blocking=True)
+        return out, info
+    return x, info

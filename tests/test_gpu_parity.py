@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Each step of Algorithm 1 is compared element by element with the oracle on
+the same seeded inputs: the gradient (bound from fp32 error analysis, plus a
+bit-exact integer case), AAb_Solver and the fused heavy-ball step (against the
+oracle's fp64 run, with the fp32 rounding amplification measured by the
+oracle's own fp32 mode as the yardstick), and the three sketch families
+(componentwise bounds).  Sizes span several tiles/blocks and ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mihs_oracle as o
+from paper_1912_03514_gb300 import mihs
+from paper_1912_03514_gb300 import workloads as W
+
+from tests._tol import U32, apass_depths, gamma, gradient_bound
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+# ----------------------------------------------------------------- gradient
+GRAD_CASES = [  # n, d, lda
+    (1000, 256, 256), (4096, 1024, 1024), (777, 100, 104), (3001, 129, 132),
+    (5000, 2048, 2048), (33, 1, 4), (20000, 640, 644), (1, 7, 8), (50, 1536, 1536),
+]
+
+
+@pytest.mark.parametrize("n,d,lda", GRAD_CASES)
+def test_gradient_matches_oracle(n, d, lda):
+    A = W.padded_matrix(n, d, lda, seed=n + d)
+    b = W.randn((n,), seed=11 + n)
+    x = W.randn((d,), seed=12 + d, scale=0.3)
+    lam = 0.37
+    Ad, bd, xd = A.to(DEV), b.to(DEV), x.to(DEV)
+    Av = Ad.as_strided((n, d), (lda, 1))
+    g = mihs.gradient(Av, bd, xd, lam)
+    g2 = mihs.gradient(Av, bd, xd, lam)
+    torch.cuda.synchronize()
+    An = A[:, :d].numpy()
+    ref = o.gradient(An, b.numpy(), x.numpy(), lam)
+    dr, da = apass_depths(n, d, _sms())
+    bound = gradient_bound(An, b.numpy(), x.numpy(), lam, dr, da)
+    err = np.abs(_np(g) - ref)
+    assert np.all(np.isfinite(_np(g))), "padding (NaN) leaked into the result"
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound)}"
+    assert torch.equal(g, g2), "gradient is not deterministic"
+
+
+def test_gradient_integer_data_is_exact():
+    """Integer data small enough that every fp32 operation is exact: any
+    dropped row, column, sign or transposition shows up as a mismatch."""
+    n, d = 4096, 256
+    A = W.randint_matrix((n, d), 5, -2, 2)
+    x = W.randint_matrix((d,), 6, -2, 2)
+    b = W.randint_matrix((n,), 7, -40, 40)
+    lam = 3.0
+    g = mihs.gradient(A.to(DEV), b.to(DEV), x.to(DEV), lam).cpu().numpy()
+    ref = o.gradient(A.numpy(), b.numpy(), x.numpy(), lam)
+    assert np.array_equal(g.astype(np.float64), ref)
+
+
+def test_gradient_zero_rows_beyond_n_and_lambda_zero():
+    n, d = 130, 33
+    A = W.padded_matrix(n, d, 36, seed=3)
+    b = W.randn((n,), seed=4)
+    x = torch.zeros(d)
+    g = mihs.gradient(A.to(DEV).as_strided((n, d), (36, 1)), b.to(DEV), x.to(DEV), 0.0)
+    ref = A[:, :d].double().t() @ b.double()
+    assert torch.allclose(g.cpu().double(), ref, rtol=1e-5, atol=1e-5)
+
+
+# ------------------------------------------------------------- AAb_Solver
+AAB_CASES = [  # m, d, lam
+    (40, 30, 0.3), (256, 256, 0.0103), (588, 1024, 1e-4), (1000, 64, 1e-2), (7, 5, 0.5),
+    (100, 1, 0.2), (3, 2048, 1.0), (2048, 2048, 0.5), (1500, 300, 1e-3),
+]
+
+
+def _sa_case(m, d, seed):
+    SA = W.randn((m, d), seed, scale=1.0 / math.sqrt(m))
+    g = W.randn((d,), seed + 1)
+    return SA, g
+
+
+def _fp32_amplification(SA, g, lam, k):
+    """‖Δ₃₂ − Δ₆₄‖/‖Δ₆₄‖ of the oracle run in fp32 vs fp64 for k passes."""
+    x64, _ = o.aab_solve(SA, g, lam, 0.0, max_iter=k)
+    x32, _ = o.aab_solve(SA.astype(np.float32), g.astype(np.float32), lam, 0.0, max_iter=k,
+                         dtype=np.float32)
+    return o.rel_error(x32, x64), x64
+
+
+@pytest.mark.parametrize("m,d,lam", AAB_CASES)
+@pytest.mark.parametrize("k", [1, 4, 25])
+def test_aab_fixed_passes_matches_oracle(m, d, lam, k):
+    SA, g = _sa_case(m, d, 100 * m + d)
+    SAn, gn = SA.numpy().astype(np.float64), g.numpy().astype(np.float64)
+    amp, ref = _fp32_amplification(SAn, gn, lam, k)
+    passes = torch.zeros(1, dtype=torch.int32, device=DEV)
+    delta = mihs.aab_solve(SA.to(DEV), g.to(DEV), lam, eps_sub=0.0, max_inner=k, passes=passes)
+    torch.cuda.synchronize()
+    kk = min(k, m, d)
+    assert int(passes.item()) == kk
+    err = o.rel_error(_np(delta), ref)
+    assert err <= 20 * max(amp, 4 * U32 * math.sqrt(d)), (err, amp)
+
+
+@pytest.mark.parametrize("m,d,lam", [(588, 1024, 1e-4), (256, 256, 0.0103), (1500, 300, 1e-3)])
+@pytest.mark.parametrize("eps", [0.5, 0.1, 1e-3])
+def test_aab_forcing_term(m, d, lam, eps):
+    """Stops at the first pass with t < eps (t certifies the previous iterate),
+    like the oracle, and the returned Δ meets the forcing term."""
+    SA, g = _sa_case(m, d, 7 * m + d)
+    SAn, gn = SA.numpy().astype(np.float64), g.numpy().astype(np.float64)
+    _, k_ref, ts = o.aab_solve(SAn, gn, lam, eps, history=True)
+    passes = torch.zeros(1, dtype=torch.int32, device=DEV)
+    delta = mihs.aab_solve(SA.to(DEV), g.to(DEV), lam, eps_sub=eps, passes=passes)
+    kg = int(passes.item())
+    near = any(abs(t - eps) < 1e-3 * eps for t in ts[max(0, k_ref - 2):k_ref + 1])
+    assert kg == k_ref or (near and abs(kg - k_ref) <= 1)
+    H = SAn.T @ SAn + lam * np.eye(d)
+    res = np.linalg.norm(H @ _np(delta) - gn) / np.linalg.norm(gn)
+    assert res < eps * (1 + 1e-3)
+
+
+def test_aab_zero_rhs():
+    SA, _ = _sa_case(50, 40, 1)
+    passes = torch.full((1,), -1, dtype=torch.int32, device=DEV)
+    delta = mihs.aab_solve(SA.to(DEV), torch.zeros(40, device=DEV), 0.1, passes=passes)
+    assert int(passes.item()) == 0 and not torch.any(delta)
+
+
+@pytest.mark.parametrize("m,d", [(588, 1024), (64, 48)])
+def test_aab_heavy_ball_matches_oracle(m, d):
+    lam, k, sd = 1e-3, 6, 0.3 * min(m, d)
+    SA, g = _sa_case(m, d, 3 * m)
+    x = W.randn((d,), 91)
+    xp = W.randn((d,), 92)
+    alpha, beta = o.momentum_params(sd, m)
+    amp, delta_ref = _fp32_amplification(SA.numpy().astype(np.float64), g.numpy().astype(np.float64), lam, k)
+    xr, xpr = o.heavy_ball(x.numpy().astype(np.float64), xp.numpy().astype(np.float64), delta_ref,
+                           alpha, beta)
+    xd, xpd = x.to(DEV), xp.to(DEV)
+    mihs.aab_heavy_ball(SA.to(DEV), g.to(DEV), lam, 0.0, k, alpha, beta, xd, xpd)
+    assert torch.equal(xpd.cpu(), x)                  # x⁻ ← x exactly
+    tol = 20 * max(amp, 1e-6) * np.linalg.norm(alpha * delta_ref) + 8 * U32 * np.linalg.norm(np.abs(xr) + 2 * np.abs(x.numpy()))
+    assert np.linalg.norm(_np(xd) - xr) <= tol
+
+
+# ----------------------------------------------------------------- sketches
+def _sketch_bound(family, A, m, seed, n):
+    """Componentwise bound on |SA_gpu − SA| for each family's kernel."""
+    absA = np.abs(A)
+    if family == o.COUNTSKETCH:
+        h, _ = o.countsketch_hash(n, m, seed)
+        S = np.zeros((m, n))
+        S[h, np.arange(n)] = 1.0
+        cnt = np.bincount(h, minlength=m).max()
+        return gamma(cnt + 1) * (S @ absA)
+    if family == o.SRHT:
+        L = max(0, math.ceil(math.log2(n)))
+        LB = min(L, 10)
+        nblk = 2 ** (L - LB)
+        return gamma(LB + nblk + _sms() + 4) * (np.ones((m, 1)) * absA.sum(0, keepdims=True)) / math.sqrt(m)
+    S = np.abs(o.gaussian_sketch_matrix(m, n, seed))
+    ks = 16 + n  # per-split sequential depth ≤ n, plus the split-K sum
+    return (gamma(ks) + 16 * U32) * (S @ absA) + 1e-30
+
+
+SKETCH_CASES = [(4096, 256, 256), (3000, 130, 64), (1000, 33, 17), (8192, 1024, 100), (777, 2048, 31)]
+
+
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+@pytest.mark.parametrize("n,d,m", SKETCH_CASES)
+def test_sketch_matches_oracle(family, n, d, m):
+    lda = (d + 3) // 4 * 4
+    A = W.padded_matrix(n, d, lda, seed=n * 3 + d)
+    seed = 0xDEADBEEF12345 + family
+    Ad = A.to(DEV).as_strided((n, d), (lda, 1))
+    SA = mihs.sketch_apply(Ad, family, m, seed)
+    SA2 = mihs.sketch_apply(Ad, family, m, seed)
+    torch.cuda.synchronize()
+    An = A[:, :d].numpy().astype(np.float64)
+    ref = o.sketch_apply(family, An, m, seed)
+    bound = _sketch_bound(family, An, m, seed, n)
+    err = np.abs(_np(SA) - ref)
+    assert np.all(np.isfinite(_np(SA)))
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound)}"
+    assert torch.equal(SA, SA2), "sketch is not deterministic"
+
+
+def test_countsketch_integer_exact():
+    n, d, m = 20000, 96, 50
+    A = W.randint_matrix((n, d), 9, -100, 100)
+    SA = mihs.sketch_apply(A.to(DEV), o.COUNTSKETCH, m, 77).cpu().numpy().astype(np.float64)
+    assert np.array_equal(SA, o.sketch_apply(o.COUNTSKETCH, A.numpy(), m, 77))
+
+
+def test_srht_integer_exact():
+    n, d, m = 5000, 40, 64          # ±1 sums of integers, scaled by 1/√m = 1/8 exactly
+    A = W.randint_matrix((n, d), 10, -50, 50)
+    SA = mihs.sketch_apply(A.to(DEV), o.SRHT, m, 78).cpu().numpy().astype(np.float64)
+    assert np.array_equal(SA, o.sketch_apply(o.SRHT, A.numpy(), m, 78))
+
+
+# ------------------------------------------------------------ end to end
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_solve_small_problem_matches_exact(family):
+    """4096×256, κ(A)=1e4, sd=64, m=256: stop at relative residual 1e-6 and
+    land within 1e-5 of the fp64 solution."""
+    p = W.problem_small()
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam)
+    with mihs.Sketch(A, family, p.m, seed=2024) as sk:
+        x, info = sk.solve(A, b, p.lam, p.sd, tol=1e-6, max_outer=200)
+    assert info.converged and info.rel_resid <= 1e-6
+    assert info.outer_iters < 60
+    assert o.rel_error(_np(x), xs) <= 1e-5
+    # the certificate ‖x − x*‖ ≤ ‖g(x)‖/λ agrees
+    assert o.certify(p.A.numpy(), p.b.numpy(), _np(x), p.lam) >= np.linalg.norm(_np(x) - xs) * (1 - 1e-6)
+
+
+def test_solve_is_deterministic_and_warm_start():
+    p = W.problem_scaled(20000, 300, seed=3)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    with mihs.Sketch(A, "countsketch", p.m, seed=5) as sk:
+        x1, i1 = sk.solve(A, b, p.lam, p.sd, tol=1e-7, max_outer=300)
+        x2, i2 = sk.solve(A, b, p.lam, p.sd, tol=1e-7, max_outer=300)
+        assert torch.equal(x1, x2) and i1.outer_iters == i2.outer_iters
+        x3 = x1.clone()
+        x3, i3 = sk.solve(A, b, p.lam, p.sd, tol=1e-7, max_outer=300, x=x3, warm_start=True)
+        assert i3.converged and i3.outer_iters <= 2
+        x4, i4 = sk.solve(A, b, p.lam, p.sd, tol=1e-7, max_outer=0)
+        assert i4.status == mihs.NOT_CONVERGED and i4.outer_iters == 0
+        assert not torch.any(x4) and abs(i4.rel_resid - 1.0) < 1e-6
+
+
+def test_solve_reports_non_finite():
+    p = W.problem_scaled(4096, 64, seed=4)
+    A, b = p.A.to(DEV), p.b.clone()
+    b[17] = float("nan")
+    with mihs.Sketch(A, "gaussian", p.m, seed=1) as sk:
+        with pytest.raises(mihs.MihsError) as ei:
+            sk.solve(A, b.to(DEV), p.lam, p.sd)
+    assert ei.value.code == -5
+
+
+def test_invalid_arguments_are_rejected():
+    A = torch.zeros(64, 8, device=DEV)
+    with pytest.raises(mihs.MihsError):
+        mihs.sketch_apply(A, "gaussian", 65, 0)                  # m > n
+    with pytest.raises(mihs.MihsError):
+        mihs.aab_solve(torch.zeros(8, 8, device=DEV), torch.zeros(8, device=DEV), 0.0)  # λ = 0
+    big = torch.zeros(4, 2052, device=DEV)
+    with pytest.raises(mihs.MihsError):
+        mihs.gradient(big, torch.zeros(4, device=DEV), torch.zeros(2052, device=DEV), 1.0)
+    mis = torch.zeros(64 * 8 + 1, device=DEV)[1:].view(64, 8)   # 4-byte offset: misaligned
+    with pytest.raises(mihs.MihsError):
+        mihs.gradient(mis, torch.zeros(64, device=DEV), torch.zeros(8, device=DEV), 1.0)
+    with mihs.Sketch(A + 1, "countsketch", 16, 0) as sk:
+        with pytest.raises(mihs.MihsError):
+            sk.solve(A, torch.zeros(64, device=DEV), 1.0, sd=16.0)  # sd ≥ m
