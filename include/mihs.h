@@ -105,6 +105,8 @@ int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda,
  * estimate t < eps_sub or after `max_inner` loop passes (≤ 0: min(m, d)).
  *   SA m×d (ld ldsa), g (d) inputs; delta (d) output.
  *   passes: optional DEVICE int* receiving the number of loop passes.
+ * Any ldsa ≥ d is accepted when SA fits in the cluster's shared memory
+ * (m·d ≲ 800K); larger SA must have 16-byte aligned rows (ldsa % 4 == 0).
  * Runs as one thread-block cluster; allocates nothing.
  * Errors: INVALID_ARG (λ ≤ 0, eps_sub < 0, sizes), CUDA. */
 int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa,

@@ -53,6 +53,7 @@ struct AabParams {
   int rpc_pad;         // rpc rounded up to 4
   int cols_per;        // column slice per block (multiple of 4)
   int sa_in_smem;
+  int sa_vec;          // SA rows may be read as float4 (ldsa % 4 == 0, 16-byte aligned)
 };
 
 // Deterministic block-wide sum; every thread returns the same value.
@@ -68,9 +69,10 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return t;
 }
 
-__device__ __forceinline__ float4 load4_masked(const float* row, int j, int d) {
+__device__ __forceinline__ float4 load4_masked(const float* row, int j, int d, bool vec = true) {
   // j is a multiple of 4 and j < dp; columns ≥ d read as zero.
-  if (j + 4 <= d) return *reinterpret_cast<const float4*>(row + j);
+  if (vec && j + 4 <= d) return *reinterpret_cast<const float4*>(row + j);
+  if (j + 4 <= d) return make_float4(row[j], row[j + 1], row[j + 2], row[j + 3]);
   float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
   if (j < d) t.x = row[j];
   if (j + 1 < d) t.y = row[j + 1];
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     for (int idx = tid; idx < nr * q; idx += kThreads) {
       const int i = idx / q, j = 4 * (idx - i * q);
       *reinterpret_cast<float4*>(sa + (size_t)i * dp + j) =
-          load4_masked(P.SA + (long long)(r0 + i) * P.ldsa, j, d);
+          load4_masked(P.SA + (long long)(r0 + i) * P.ldsa, j, d, P.sa_vec != 0);
     }
     SAc = sa;
     ldc = dp;
@@ -428,6 +430,12 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   P.rpc_pad = (int)round_up(P.rpc, 4);
   P.cols_per = (int)round_up((P.dp + cp.cl - 1) / cp.cl, 4);
   P.sa_in_smem = cp.in_smem;
+  P.sa_vec = (a.ldsa % 4 == 0 && (reinterpret_cast<uintptr_t>(a.SA) & 15u) == 0) ? 1 : 0;
+  if (!P.sa_in_smem && !P.sa_vec) {
+    set_error("aab: SA of %d×%d does not fit in shared memory; its rows must then be 16-byte "
+              "aligned (ldsa %% 4 == 0)", a.m, a.d);
+    return MIHS_ERR_INVALID_ARG;
+  }
 
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

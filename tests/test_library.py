@@ -54,8 +54,7 @@ def test_host_side_argument_checks(L):
     assert L.mihs_sketch_apply(FAKE, 10, 4, 4, 0, 11, 0, FAKE, 4, None) == EINVAL  # m > n
     assert L.mihs_aab_solve(FAKE, 8, 4, 4, FAKE, 0.0, 0.1, 0, FAKE, None, None) == EINVAL
     assert L.mihs_aab_solve(FAKE, 8, 4, 4, FAKE, 1.0, -0.1, 0, FAKE, None, None) == EINVAL
-    assert L.mihs_aab_solve(ctypes.c_void_p((1 << 20) + 4), 8, 4, 4, FAKE, 1.0, 0.1, 0, FAKE,
-                            None, None) == EINVAL  # misaligned SA
+    assert L.mihs_aab_solve(FAKE, 8, 4, 3, FAKE, 1.0, 0.1, 0, FAKE, None, None) == EINVAL  # ldsa < d
     o = L.mihs_default_opts()
     assert L.mihs_solve(None, FAKE, 4, FAKE, 1.0, ctypes.byref(o), FAKE, None, None) == EINVAL
     assert b"lambda" in L.mihs_last_error() or b"null" in L.mihs_last_error()
