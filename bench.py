@@ -38,7 +38,7 @@ METRIC = "ridge solves/s at stated rel. error"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mihs", "reference"], default="mihs")
     ap.add_argument("--families", default=",".join(FAMILIES))
@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--profile-op", choices=["apass", "aab", "gaussian", "countsketch", "srht"],
+                    help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
 
 
@@ -94,7 +96,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -190,6 +192,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, ws, rank, families)
+    if args.profile_op:
+        return run_profile_op(args, local)
 
     from paper_1912_03514_gb300 import mihs
 
@@ -229,6 +233,7 @@ def main():
     # ---------------- timed region (device-resident inputs)
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(gpu_uuid())
+    time.sleep(1.0)  # let the sampler start before the timed region
     barrier(ws)
     torch.cuda.synchronize()
     t_host0 = time.perf_counter()
@@ -349,6 +354,41 @@ def main():
         print(json.dumps(out), flush=True)
     for sk in sketches.values():
         sk.close()
+
+
+def run_profile_op(args, local):
+    """W + K launches of one operation on the workload, timed with CUDA events."""
+    import torch
+
+    from paper_1912_03514_gb300 import mihs
+    from paper_1912_03514_gb300 import workloads as W
+    dev = torch.device("cuda", local)
+    p = W.problem_bandwidth(device=str(dev), seed=1001, n=args.n, d=args.d)
+    A, b = p.A, p.b
+    x = W.randn((p.d,), seed=5, scale=0.01).to(dev)
+    g = torch.empty(p.d, device=dev)
+    op = args.profile_op
+    if op == "aab":
+        SA = mihs.sketch_apply(A, "countsketch", p.m, 3)
+        g = mihs.gradient(A, b, torch.zeros_like(x), p.lam)
+        delta = torch.empty_like(g)
+        fn = lambda: mihs.aab_solve(SA, g, p.lam, 0.1, delta=delta)
+    elif op == "apass":
+        fn = lambda: mihs.gradient(A, b, x, p.lam, g=g)
+    else:
+        SA = torch.empty(p.m, p.d, device=dev)
+        fn = lambda: mihs.sketch_apply(A, op, p.m, 3, SA=SA)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_op": op, "n": p.n, "d": p.d, "m": p.m,
+                      "ms_per_call": round(e0.elapsed_time(e1) / args.steps, 4)}), flush=True)
 
 
 def run_reference(args, ws, rank, families):
