@@ -99,6 +99,28 @@ int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda,
                   const float* b, const float* x, double lambda, float* g,
                   void* stream);
 
+/* The gradient of mihs_gradient (same arguments, same result) without any
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc/cudaMallocAsync at the moment they
+ * need a gradient — e.g. code running inside a stream capture whose mode
+ * forbids allocation, inside an allocator or memory-pool callback that must
+ * not re-enter the allocator, or under a device-memory budget fixed up front.
+ * Its split-K scratch is a fixed 1.25 MiB array in the library's own device
+ * memory, reserved on every GPU that loads the library and held until exit.
+ *   - The first call on each device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Limit: (partial rows = min(#SMs, ⌈n/rows per block step⌉)) × d rounded
+ *     up to 4 must fit in 160 × 2048 floats; larger cases return
+ *     MIHS_ERR_UNSUPPORTED with a message (only GPUs with more than 160 SMs
+ *     can reach it, since d ≤ 2048).
+ *   - Every call shares the array.  Calls whose kernels overlap on the GPU
+ *     (different streams or host threads) race on it; serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int mihs_gradient_noalloc(const float* A, int64_t n, int64_t d, int64_t lda,
+                          const float* b, const float* x, double lambda,
+                          float* g, void* stream);
+
 /* AAb_Solver (Algorithm 5, Section 3.6): approximately solve
  *     (SAᵀSA + λI) Δ = g
  * by upper bidiagonalisation of SA, stopping when the relative residual

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
         "mihs_launch_count": (_u64, []),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
+        "mihs_gradient_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_aab_solve": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
         "mihs_aab_heavy_ball": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _dbl, _dbl,
                                        _vp, _vp, _vp, _vp]),
@@ -155,6 +156,17 @@ def gradient(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
         g = torch.empty(d, dtype=torch.float32, device=A.device)
     _check(lib().mihs_gradient(pa, n, d, lda, _vec(b, n, "b"), _vec(x, d, "x"), float(lam),
                                _vec(g, d, "g"), _stream(stream)))
+    return g
+
+
+def gradient_noalloc(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
+                     g: torch.Tensor, stream=None) -> torch.Tensor:
+    """g = Aᵀ(b − Ax) − λx through the entry point that allocates nothing (its
+    scratch is a fixed array in the library; `g` must be given).  Calls that
+    overlap on the GPU race on that array."""
+    pa, n, d, lda = _mat(A, "A")
+    _check(lib().mihs_gradient_noalloc(pa, n, d, lda, _vec(b, n, "b"), _vec(x, d, "x"), float(lam),
+                                       _vec(g, d, "g"), _stream(stream)))
     return g
 
 
