@@ -64,6 +64,13 @@ const char* mihs_last_error(void);
 /* Number of kernels this library has launched in this process so far. */
 uint64_t mihs_launch_count(void);
 
+/* Device-side failure report: every wait inside the library's kernels is
+ * bounded (2 s); a wait that runs out makes its kernel stop early and record
+ * MIHS_ERR_TIMEOUT here (and in the status of the solve it belongs to).
+ * Writes the recorded code (0 if none) to *code and clears it; synchronises
+ * the current device. */
+int mihs_device_status(int* code);
+
 /* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
  * the records and starts recording CUDA events on the launching stream around
  * every gradient A-pass kernel (timer 0), AAb_Solver kernel (timer 1) and
@@ -220,6 +227,12 @@ mihs_opts mihs_default_opts(void);
 int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
                double lambda, const mihs_opts* opts, float* x, mihs_info* info,
                void* stream);
+
+/* Trace of the last solve on this handle: the relative residual
+ * ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step (i = 0, 1, …, at most 1024 entries)
+ * into the HOST array host_out[0..cap), the number written in *count.
+ * Synchronises the device. */
+int mihs_solve_history(mihs_sketch_t sk, float* host_out, int cap, int* count);
 
 #ifdef __cplusplus
 }

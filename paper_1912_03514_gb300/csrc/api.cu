@@ -132,6 +132,7 @@ struct mihs_sketch_s {
   float* partials;    // P × dp
   float* g;           // dp
   float* x_prev;      // dp
+  float* hist;        // kHistCap: ‖g‖ per gradient step of the last solve
   SolveCtl* ctl;
   SolveCtl* ctl_host; // pinned
   // Device-side outer loop: a CUDA graph holding one conditional WHILE node
@@ -220,6 +221,18 @@ const char* mihs_strerror(int code) {
 const char* mihs_last_error(void) { return g_err; }
 
 uint64_t mihs_launch_count(void) { return g_launches.load(); }
+
+int mihs_device_status(int* code) {
+  set_error("");
+  MIHS_ARG(code != nullptr, "mihs_device_status: null code");
+  int a = 0, g = 0;
+  int rc = apass_device_error(&a);
+  if (rc) return rc;
+  rc = gauss_tc_device_error(&g);
+  if (rc) return rc;
+  *code = a ? a : g;
+  return MIHS_OK;
+}
 
 mihs_opts mihs_default_opts(void) {
   mihs_opts o;
@@ -378,7 +391,7 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, i
   h->family = family;
   h->seed = seed;
   h->P = apass_num_partials(n, d);
-  const size_t bytes = sizeof(float) * ((size_t)m * h->dp + (size_t)h->P * h->dp + 2 * h->dp) +
+  const size_t bytes = sizeof(float) * ((size_t)m * h->dp + (size_t)h->P * h->dp + 2 * h->dp + kHistCap) +
                        sizeof(SolveCtl) + 256;
   char* base = nullptr;
   cudaError_t e = cudaMalloc(&base, bytes);
@@ -391,7 +404,8 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, i
   h->partials = h->SA + (size_t)m * h->dp;
   h->g = h->partials + (size_t)h->P * h->dp;
   h->x_prev = h->g + h->dp;
-  h->ctl = reinterpret_cast<SolveCtl*>(round_up(reinterpret_cast<uintptr_t>(h->x_prev + h->dp), 64));
+  h->hist = h->x_prev + h->dp;
+  h->ctl = reinterpret_cast<SolveCtl*>(round_up(reinterpret_cast<uintptr_t>(h->hist + kHistCap), 64));
   e = cudaMallocHost(&h->ctl_host, sizeof(SolveCtl));
   if (e != cudaSuccess) {
     cudaFree(base);
@@ -430,6 +444,22 @@ int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m, int64_t* d,
   if (d) *d = sk->d;
   if (n) *n = sk->n;
   if (family) *family = sk->family;
+  return MIHS_OK;
+}
+
+int mihs_solve_history(mihs_sketch_t sk, float* host_out, int cap, int* count) {
+  set_error("");
+  MIHS_ARG(sk != nullptr && host_out != nullptr && count != nullptr && cap >= 0,
+           "mihs_solve_history: bad argument");
+  MIHS_CUDA_TRY(cudaDeviceSynchronize());
+  SolveCtl c;
+  MIHS_CUDA_TRY(cudaMemcpy(&c, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost));
+  int k = c.outer + 1;
+  if (k > kHistCap) k = kHistCap;
+  if (k > cap) k = cap;
+  if (k > 0) MIHS_CUDA_TRY(cudaMemcpy(host_out, sk->hist, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < k; ++i) host_out[i] = c.gnorm0 > 0.f ? host_out[i] / c.gnorm0 : 0.f;
+  *count = k;
   return MIHS_OK;
 }
 
@@ -503,6 +533,7 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, do
   a.x = x;
   a.x_prev = sk->x_prev;
   a.ctl = sk->ctl;
+  a.hist = sk->hist;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
   const mihs_sketch_s::Key key = {A, lda, b, x, (float)lambda, a.alpha, a.beta, a.eps, a.max_passes};
   bool graph_ran = false;

@@ -15,9 +15,13 @@ int apass_num_partials(int64_t n, int64_t d);
 inline int64_t apass_dpad(int64_t d) { return round_up(d, 4); }
 // partials[p][j] = Σ_{rows of block p} A[i][j]·(b[i] − A[i]·x).  x may be
 // NULL (taken as 0).  Skips all work when ctl != NULL and ctl->done.
+// A bounded wait that runs out sets ctl->status = MIHS_ERR_TIMEOUT and
+// ctl->done (when ctl != NULL) and the library-wide device error word.
 int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda,
                          const float* b, const float* x, float* partials,
-                         const SolveCtl* ctl, cudaStream_t s);
+                         SolveCtl* ctl, cudaStream_t s);
+// Reads and clears the library-wide device error word (synchronises).
+int apass_device_error(int* code);
 // g[j] = Σ_p partials[p][j] − λ·x[j] in a fixed order.
 int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const float* x, float lambda, float* g,
@@ -38,15 +42,23 @@ struct AabLaunch {
   float* x;
   float* x_prev;
   SolveCtl* ctl;       // solve mode (stop test, counters); may be NULL
+  float* hist;         // solve mode: ‖g‖ of every gradient step (kHistCap entries); may be NULL
   unsigned long long cond;  // graph conditional handle to clear when the solve stops (0: none)
 };
 int launch_aab(const AabLaunch& a, cudaStream_t s);
 // Picks and caches the cluster shape for (m, d) (call outside stream capture).
 void aab_prepare(int m, int d);
 
+constexpr int kHistCap = 1024;
+
 // ---- sketches (sketch_*.cu) ------------------------------------------------
 int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                     uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+// tcgen05 version of the Gaussian sketch (sketch_gaussian_tc.cu).
+bool gaussian_tc_available();
+int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
+                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+int gauss_tc_device_error(int* code);
 int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                        uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,

@@ -3,9 +3,11 @@
 // S is never stored: the tile of S a block needs is regenerated from the
 // Philox4x32-10 counter (⌊j/4⌋, i, 0, 0) and a Box–Muller transform right
 // before it is used, so the only HBM traffic is one read of A (split-K over
-// the n rows) plus the small m×d partial sums.  This is the portable SIMT
-// version (fp32 FMA, 64×128 output tile, k-step 16).
+// the n rows) plus the small m×d partial sums.  This file holds the fp32 SIMT
+// version (64×128 output tile, k-step 16), used when the tensor-core version
+// (sketch_gaussian_tc.cu) is unavailable or MIHS_GAUSSIAN_SIMT is set.
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -112,6 +114,9 @@ __global__ void gauss_reduce_kernel(const float* __restrict__ part, int KS, int 
 
 int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
                     float* SA, int64_t ldsa, cudaStream_t s) {
+  // Tensor-core path by default; MIHS_GAUSSIAN_SIMT selects this fp32 SIMT path.
+  static const bool force_simt = std::getenv("MIHS_GAUSSIAN_SIMT") != nullptr;
+  if (!force_simt && gaussian_tc_available()) return sketch_gaussian_tc(A, n, d, lda, m, seed, SA, ldsa, s);
   const int tn = (int)((d + TN - 1) / TN), tm = (int)((m + TM - 1) / TM);
   const int64_t ksteps = (n + TK - 1) / TK;
   int64_t KS = (2LL * num_sms() + (int64_t)tn * tm - 1) / ((int64_t)tn * tm);

@@ -1,0 +1,417 @@
+// Gaussian sketch on the 5th-generation tensor cores (tcgen05, TMEM, TMA):
+//     SA = S·A,  S_ij ~ N(0, 1/m)  (Lemma 3, case iv).
+//
+// GEMM orientation: D[M = 128 sketch rows][N = 256 columns of A] accumulates
+// over K = rows of A.  The tf32 MMA reads both operands K-major, while A is
+// stored with its columns contiguous, so per K-block of 32 rows:
+//   * a TMA lane loads the 32×256 tile of A (fp32) into a staging ring;
+//   * four transposer warps rewrite it K-major (one 128-byte row per column
+//     of A, 16-byte chunks XOR-swizzled by row mod 8 — the canonical 128-byte
+//     swizzle layout), rounding to tf32;
+//   * sixteen generator warps write the 128×32 tile of S (Philox4x32-10 counter
+//     (⌊k/4⌋, i, 0, 0), Box–Muller, rounded to tf32) in the same layout — S
+//     never leaves shared memory;
+//   * one thread issues four tcgen05.mma.kind::tf32 (K = 8 each) into a
+//     128×256 fp32 accumulator in tensor memory and commits the operand stage
+//     back to the producers.
+// Rings: 3 operand stages (48 KB) and 2 staging stages (32 KB).  The K range is
+// split across blocks (split-K); each block's accumulator goes to a partial
+// buffer that a small kernel sums in a fixed order and scales by 1/√m.
+// Every mbarrier wait is bounded; a wait that runs out records
+// MIHS_ERR_TIMEOUT, the block still frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "internal.h"
+
+namespace mihs {
+
+namespace {
+
+constexpr int TM = 128;          // sketch rows per tile (MMA M)
+constexpr int TN = 256;          // columns of A per tile (MMA N)
+constexpr int TK = 32;           // rows of A per stage (4 MMAs of K = 8)
+constexpr int kStages = 3;       // operand ring
+constexpr int kStg = 2;          // staging ring (TMA → transposers)
+constexpr int kGenWarps = 16;    // S generators (warps 2–17); warps 2–5 then run the epilogue
+constexpr int kTrWarps = 4;      // A transposers (warps 18–21)
+constexpr int kThreads = (2 + kGenWarps + kTrWarps) * 32;  // warp 0: MMA, warp 1: TMA
+constexpr uint32_t kSBytes = TM * TK * 4;       // 16 KB
+constexpr uint32_t kABytes = TK * TN * 4;       // 32 KB
+constexpr uint32_t kStageBytes = kSBytes + kABytes;
+constexpr size_t kSmemBytes =
+    (size_t)kStages * kStageBytes + (size_t)kStg * kABytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t kTmemCols = 256;
+
+__device__ int g_gauss_tc_error = 0;
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // tcgen05 shared-memory matrix descriptor: start >> 4, leading/stride byte
+  // offsets >> 4, descriptor version 1 (bit 46), 128-byte swizzle (mode 2).
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
+                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Box–Muller with CUDA's fast intrinsics (its results are rounded to tf32,
+// 2⁻¹¹ relative, so the intrinsics' ~2⁻²¹ error is invisible): the same
+// u1 = (⌊a/2⁸⌋+1)·2⁻²⁴, u2 = ⌊b/2⁸⌋·2⁻²⁴ as box_muller(); the angle is taken
+// as 2π(u2 − ½) ∈ [−π, π), where the intrinsics are accurate, and the
+// half-turn is undone by negating both outputs.
+__device__ __forceinline__ float2 box_muller_fast(uint32_t a, uint32_t b) {
+  const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
+  const float u2 = (float)(b >> 8) * 0x1p-24f;
+  const float t = -2.0f * __logf(u1);
+  const float r = t > 0.f ? t * rsqrtf(t) : 0.f;
+  float sn, cs;
+  __sincosf(6.283185307179586f * (u2 - 0.5f), &sn, &cs);
+  return make_float2(-r * cs, -r * sn);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float f) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+// 32 lanes × 32 consecutive columns of the accumulator → 32 registers.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GaussTcArgs {
+  int n, d, m;
+  int rows_per_split;   // multiple of TK
+  uint32_t k0, k1;      // Philox key
+  float* part;          // [gridDim.z][m][dp]
+  int dp;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte alignment for the 128-byte swizzle atoms.
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* stg = base + (size_t)kStages * kStageBytes;           // staging ring
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)kStg * kABytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* stg_full = empty + kStages;
+  uint64_t* stg_empty = stg_full + kStg;
+  uint64_t* accum = stg_empty + kStg;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * TM;             // first sketch row
+  const int c0 = blockIdx.x * TN;             // first column of A
+  const int kb0 = blockIdx.z * a.rows_per_split;
+  const int kb1 = min(a.n, kb0 + a.rows_per_split);
+  const int nkb = kb1 > kb0 ? (kb1 - kb0 + TK - 1) / TK : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], kGenWarps + kTrWarps);  // one arrival per producer warp
+      mbar_init(&empty[s], 1);                    // MMA commit
+    }
+    for (int s = 0; s < kStg; ++s) {
+      mbar_init(&stg_full[s], 1);                 // TMA expect_tx arrival
+      mbar_init(&stg_empty[s], kTrWarps);
+    }
+    mbar_init(accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        if (!mbar_wait(&full[s], ph, kWaitLimitNs)) {
+          atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sS = smem_u32(base + (size_t)s * kStageBytes);
+        const uint32_t sA = sS + kSBytes;
+#pragma unroll
+        for (int kk = 0; kk < TK / 8; ++kk) {
+          // Both operands K-major: 8-row atoms of 1024 B; K advances 32 bytes.
+          const uint64_t ad = smem_desc_sw128(sS + kk * 32, 16, 1024);
+          const uint64_t bd = smem_desc_sw128(sA + kk * 32, 16, 1024);
+          mma_tf32(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);  // fires when every MMA issued above has completed
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ TMA loads of A
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kStg;
+        const uint32_t ph = (uint32_t)(kb / kStg) & 1u;
+        if (kb >= kStg && !mbar_wait(&stg_empty[s], ph ^ 1u, kWaitLimitNs)) {
+          atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
+        mbar_arrive_expect_tx(&stg_full[s], kABytes);
+        tma_load_2d(stg + (size_t)s * kABytes, &tmap_a, c0, kb0 + kb * TK, &stg_full[s]);
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 2 + kGenWarps) {
+    // ------------------------------------------------ A transposers: staging → K-major
+    const int tt = threadIdx.x - (2 + kGenWarps) * 32;  // 0..127: columns tt, tt + 128
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      const int q = kb % kStg;
+      if (!mbar_wait(&stg_full[q], (uint32_t)(kb / kStg) & 1u, kWaitLimitNs) ||
+          (kb >= kStages && !mbar_wait(&empty[s], ((uint32_t)(kb / kStages) & 1u) ^ 1u, kWaitLimitNs))) {
+        atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+        break;
+      }
+      const float* src = reinterpret_cast<const float*>(stg + (size_t)q * kABytes);  // [32 rows][256 cols]
+      unsigned char* dstA = base + (size_t)s * kStageBytes + kSBytes;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = tt + 128 * h;
+        unsigned char* row = dstA + (c >> 3) * 1024 + (c & 7) * 128;
+#pragma unroll
+        for (int ch = 0; ch < TK / 4; ++ch) {
+          uint4 v;
+          v.x = to_tf32(src[(4 * ch + 0) * TN + c]);
+          v.y = to_tf32(src[(4 * ch + 1) * TN + c]);
+          v.z = to_tf32(src[(4 * ch + 2) * TN + c]);
+          v.w = to_tf32(src[(4 * ch + 3) * TN + c]);
+          *reinterpret_cast<uint4*>(row + ((ch ^ (c & 7)) << 4)) = v;
+        }
+      }
+      fence_async_shared();  // generic-proxy writes → visible to the tensor core
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&stg_empty[q]);
+        mbar_arrive(&full[s]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ S generators
+    // Thread g: tile row g mod 128, 16-byte chunks 2h and 2h + 1 with h = g div 128
+    // (two Philox calls per stage; the generation is ALU-bound, so many warps).
+    const int g = threadIdx.x - 64;
+    const int gt = g & (TM - 1);
+    const int h = g >> 7;
+    const int gi = i0 + gt;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+      if (kb >= kStages && !mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs)) {
+        atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+        break;
+      }
+      unsigned char* sS = base + (size_t)s * kStageBytes;
+      unsigned char* row = sS + (gt >> 3) * 1024 + (gt & 7) * 128;
+      const int kbase = kb0 + kb * TK;
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * h + cc;
+        const int j0 = kbase + 4 * c;
+        uint4 out = make_uint4(0u, 0u, 0u, 0u);
+        if (gi < a.m && j0 < kb1) {
+          const uint4 w = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), (uint32_t)gi, kTagGaussian, 0u), a.k0, a.k1);
+          const float2 za = box_muller_fast(w.x, w.y);
+          const float2 zb = box_muller_fast(w.z, w.w);
+          out = make_uint4(to_tf32(za.x), j0 + 1 < kb1 ? to_tf32(za.y) : 0u,
+                           j0 + 2 < kb1 ? to_tf32(zb.x) : 0u, j0 + 3 < kb1 ? to_tf32(zb.y) : 0u);
+        }
+        *reinterpret_cast<uint4*>(row + ((c ^ (gt & 7)) << 4)) = out;
+      }
+      fence_async_shared();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+    }
+    if (warp >= 6) goto done;  // warps 2–5 (one per TMEM lane quarter) run the epilogue
+    {
+    // -------------------------------------------------------------- epilogue
+    const bool ok = mbar_wait(accum, 0u, kWaitLimitNs);
+    if (!ok) atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+    tc_fence_after();
+    const int qw = warp & 3;                 // TMEM lanes 32·qw … 32·qw + 31
+    const int row_local = 32 * qw + lane;
+    const int grow = i0 + row_local;
+    float* dst = a.part + ((size_t)blockIdx.z * a.m + (size_t)(grow < a.m ? grow : 0)) * a.dp;
+    for (int cc = 0; cc < TN; cc += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)cc, v);
+      if (grow < a.m) {
+        const int col = c0 + cc;
+        const bool have = ok && nkb > 0;
+        if (col + 32 <= a.d) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(dst + col + 4 * q) =
+                have ? make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          for (int q = 0; q < 32; ++q)
+            if (col + q < a.d) dst[col + q] = have ? v[q] : 0.f;
+        }
+      }
+    }
+    }
+  }
+done:
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// SA[i][c] = scale · Σ_z part[z][i][c] (fixed order).
+__global__ void gauss_tc_reduce_kernel(const float* __restrict__ part, int KS, int m, int d, int dp,
+                                       float scale, float* __restrict__ SA, long long ldsa) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * d) return;
+  const int i = (int)(idx / d), c = (int)(idx - (long long)i * d);
+  float s = 0.f;
+  for (int z = 0; z < KS; ++z) s += part[((size_t)z * m + i) * dp + c];
+  SA[(long long)i * ldsa + c] = s * scale;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+bool gaussian_tc_available() { return encode_fn() != nullptr; }
+
+int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
+                       int64_t ldsa, cudaStream_t s) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) {
+    set_error("gaussian sketch: cuTensorMapEncodeTiled unavailable");
+    return MIHS_ERR_UNSUPPORTED;
+  }
+  CUtensorMap tmap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)n};
+  const cuuint64_t gstride[1] = {(cuuint64_t)lda * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)TN, (cuuint32_t)TK};
+  const cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("gaussian sketch: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MIHS_ERR_UNSUPPORTED;
+  }
+  const int tn = (int)((d + TN - 1) / TN), tm = (int)((m + TM - 1) / TM);
+  const int64_t kblocks = (n + TK - 1) / TK;
+  int64_t KS = num_sms() / (int64_t)(tn * tm);
+  if (KS < 1) KS = 1;
+  if (KS > kblocks) KS = kblocks;
+  const int rows_per_split = (int)(((n + KS - 1) / KS + TK - 1) / TK * TK);
+  KS = (n + rows_per_split - 1) / rows_per_split;
+  const int dp = (int)round_up(d, 4);
+  StreamScratch scratch;
+  int rc = scratch.alloc(sizeof(float) * (size_t)KS * m * dp, s);
+  if (rc) return rc;
+  GaussTcArgs args;
+  args.n = (int)n;
+  args.d = (int)d;
+  args.m = (int)m;
+  args.rows_per_split = rows_per_split;
+  args.k0 = (uint32_t)seed;
+  args.k1 = (uint32_t)(seed >> 32);
+  args.part = static_cast<float*>(scratch.p);
+  args.dp = dp;
+  MIHS_CUDA_TRY(cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  gauss_tc_kernel<<<dim3(tn, tm, (unsigned)KS), kThreads, kSmemBytes, s>>>(tmap, args);
+  MIHS_CHECK_LAUNCH();
+  const long long tot = (long long)m * d;
+  gauss_tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      args.part, (int)KS, (int)m, (int)d, dp, (float)(1.0 / std::sqrt((double)m)), SA, ldsa);
+  MIHS_CHECK_LAUNCH();
+  count_launch(2);
+  return MIHS_OK;
+}
+
+int gauss_tc_device_error(int* code) {
+  int v = 0, zero = 0;
+  MIHS_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_gauss_tc_error, sizeof(int)));
+  if (v != 0) MIHS_CUDA_TRY(cudaMemcpyToSymbol(g_gauss_tc_error, &zero, sizeof(int)));
+  *code = v;
+  return MIHS_OK;
+}
+
+}  // namespace mihs

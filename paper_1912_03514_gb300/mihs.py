@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         "mihs_strerror": (ctypes.c_char_p, [_int]),
         "mihs_last_error": (ctypes.c_char_p, []),
         "mihs_launch_count": (_u64, []),
+        "mihs_device_status": (_int, [ctypes.POINTER(_int)]),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_gradient_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
@@ -71,6 +72,7 @@ def lib() -> ctypes.CDLL:
         "mihs_sketch_info": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
         "mihs_resketch": (_int, [_vp, _vp, _i64, _u64, _vp]),
         "mihs_sketch_copy": (_int, [_vp, _vp, _i64, _vp]),
+        "mihs_solve_history": (_int, [_vp, ctypes.POINTER(ctypes.c_float), _int, ctypes.POINTER(_int)]),
         "mihs_sketch_destroy": (_int, [_vp]),
         "mihs_default_opts": (_Opts, []),
         "mihs_timing": (_int, [_int]),
@@ -113,6 +115,13 @@ def _vec(v: torch.Tensor, n: int, name: str):
 
 def family_id(family) -> int:
     return FAMILIES[family] if isinstance(family, str) else int(family)
+
+
+def device_status() -> int:
+    """Reads and clears the library's device-side failure code (0 if none)."""
+    c = _int()
+    _check(lib().mihs_device_status(ctypes.byref(c)))
+    return c.value
 
 
 def launch_count() -> int:
@@ -257,6 +266,13 @@ class Sketch:
         if not want_info:
             return x, None
         return x, SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status)
+
+    def history(self):
+        """Relative residual ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step of the last solve."""
+        buf = (ctypes.c_float * 1024)()
+        cnt = _int()
+        _check(lib().mihs_solve_history(self._h, buf, 1024, ctypes.byref(cnt)))
+        return [float(buf[i]) for i in range(cnt.value)]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -183,7 +183,9 @@ def _sketch_bound(family, A, m, seed, n):
         return gamma(LB + nblk + _sms() + 4) * (np.ones((m, 1)) * absA.sum(0, keepdims=True)) / math.sqrt(m)
     S = np.abs(o.gaussian_sketch_matrix(m, n, seed))
     ks = 16 + n  # per-split sequential depth ≤ n, plus the split-K sum
-    return (gamma(ks) + 16 * U32) * (S @ absA) + 1e-30
+    # tensor-core path: A enters as tf32 (≤ 2⁻¹⁰ relative), S is rounded to tf32
+    # (≤ 2⁻¹¹); Box–Muller's fp32 transcendental error ≤ 16u
+    return (gamma(ks) + 2.0 ** -10 + 2.0 ** -11 + 16 * U32) * (S @ absA) + 1e-30
 
 
 SKETCH_CASES = [(4096, 256, 256), (3000, 130, 64), (1000, 33, 17), (8192, 1024, 100), (777, 2048, 31)]
@@ -237,6 +239,18 @@ def test_solve_small_problem_matches_exact(family):
     assert o.rel_error(_np(x), xs) <= 1e-5
     # the certificate ‖x − x*‖ ≤ ‖g(x)‖/λ agrees
     assert o.certify(p.A.numpy(), p.b.numpy(), _np(x), p.lam) >= np.linalg.norm(_np(x) - xs) * (1 - 1e-6)
+
+
+def test_solve_history_matches_info():
+    p = W.problem_scaled(20000, 300, seed=8)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    with mihs.Sketch(A, "srht", p.m, seed=9) as sk:
+        _, info = sk.solve(A, b, p.lam, p.sd, tol=1e-6, max_outer=100)
+        h = sk.history()
+    assert len(h) == info.outer_iters + 1
+    assert h[0] == pytest.approx(1.0, rel=1e-6)          # x¹ = 0: ‖g(0)‖ = ‖Aᵀb‖
+    assert h[-1] == pytest.approx(info.rel_resid, rel=1e-5) and h[-1] <= 1e-6
+    assert all(v > 1e-6 for v in h[:-1])
 
 
 def test_solve_is_deterministic_and_warm_start():
