@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="run the per-family solves of a step one after another on one stream")
     ap.add_argument("--profile-op", choices=["apass", "aab", "aab-late", "gaussian", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
@@ -206,12 +208,26 @@ def main():
     xs = {f: torch.empty(d, dtype=torch.float32, device=dev) for f in families}
     kw = dict(tol=args.tol, max_outer=args.max_outer, eps_sub=0.1)
 
+    main_stream = torch.cuda.current_stream()
+    streams = {f: (main_stream if args.sequential else torch.cuda.Stream()) for f in families}
+
     def step(want_info=False):
+        # The solves of one step are independent problems: each runs on its
+        # own stream (so one solve's latency-bound inner solver overlaps
+        # another's bandwidth-bound gradient pass), joined back to the main
+        # stream at the end of the step.
         infos = {}
+        ev = torch.cuda.Event()
+        ev.record(main_stream)
         for f in families:
-            sk = sketches[f]
-            sk.resketch(A, seed)
-            _, infos[f] = sk.solve(A, b, p.lam, p.sd, x=xs[f], want_info=want_info, **kw)
+            s = streams[f]
+            s.wait_event(ev)
+            with torch.cuda.stream(s):
+                sk = sketches[f]
+                sk.resketch(A, seed)
+                _, infos[f] = sk.solve(A, b, p.lam, p.sd, x=xs[f], want_info=want_info, **kw)
+        for f in families:
+            main_stream.wait_stream(streams[f])
         return infos
 
     # Warm-up; the last warm-up step reports iteration counts.
@@ -298,9 +314,15 @@ def main():
         outs = {f: torch.empty(d, dtype=torch.float32, pin_memory=True) for f in families}
 
         def e2e_step():
+            ev = torch.cuda.Event()
+            ev.record(main_stream)
             for f in families:
-                mihs.solve(A_pin, b_pin, p.lam, f, m, p.sd, seed=seed, out=outs[f],
-                           want_info=False, **kw)
+                streams[f].wait_event(ev)
+                with torch.cuda.stream(streams[f]):
+                    mihs.solve(A_pin, b_pin, p.lam, f, m, p.sd, seed=seed, out=outs[f],
+                               want_info=False, **kw)
+            for f in families:
+                main_stream.wait_stream(streams[f])
 
         for _ in range(max(args.warmup, 1)):
             e2e_step()
@@ -339,6 +361,7 @@ def main():
                        "n": n, "d": d, "m": m, "lambda": p.lam, "sd": round(p.sd, 3), "tol": args.tol,
                        "stop": "‖Aᵀ(b−Ax)−λx‖ ≤ tol·‖Aᵀb‖", "eps_sub": 0.1,
                        "families": families, "l2": "inputs larger than L2 (A = %.2f GB)" % (4 * n * d / 1e9),
+                       "streams": "sequential" if args.sequential else "one CUDA stream per family (independent solves run concurrently)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "gpu_launches": launches_per_step * args.steps,
             "per_family_ms": per_family,

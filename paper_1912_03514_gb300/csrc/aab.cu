@@ -32,9 +32,9 @@ namespace mihs {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemBudget = 210 * 1024;
 
 struct AabParams {
   const float* SA;
@@ -83,76 +83,8 @@ __device__ __forceinline__ float4 load4_masked(const float* row, int j, int d, b
   return t;
 }
 
-// out[i] = SAc[i,:]·v for the block's rows.  Warp w takes rows w, w+16, …,
-// four at a time, so each chunk of v read from smem feeds four rows.
-__device__ __forceinline__ void rows_dot4(const float* SAc, long long ldc, int nr, int d, int dp,
-                                          const float* v, float* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = warp; i0 < nr; i0 += 4 * kWarps) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    const float* rows[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) rows[q] = SAc + (long long)min(i0 + q * kWarps, nr - 1) * ldc;
-#pragma unroll 2
-    for (int j = 4 * lane; j < dp; j += 128) {
-      const float4 b = *reinterpret_cast<const float4*>(v + j);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 a = load4_masked(rows[q], j, d);
-        s[q] = fmaf(a.x, b.x, s[q]);
-        s[q] = fmaf(a.y, b.y, s[q]);
-        s[q] = fmaf(a.z, b.z, s[q]);
-        s[q] = fmaf(a.w, b.w, s[q]);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (i0 + q * kWarps < nr) out[i0 + q * kWarps] = s[q];
-    }
-  }
-}
-
-// u_h[j] = Σ_{i in half h} SAc[i][j]·w[i]: threads [256h, 256h+256) take row
-// half h, one float4 column group each (the two halves are summed later, in
-// a fixed order, by the reduce-scatter).
-__device__ __forceinline__ void cols_dot_halves(const float* SAc, long long ldc, int nr, int d,
-                                                int dp, const float* w, float* u0, float* u1) {
-  const int h = threadIdx.x >> 8, t = threadIdx.x & 255;
-  const int half = (nr + 1) >> 1;
-  const int ib = h * half, ie = min(nr, ib + half);
-  float* u = h ? u1 : u0;
-  for (int j = 4 * t; j < dp; j += 1024) {
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-    int i = ib;
-#pragma unroll 2
-    for (; i + 2 <= ie; i += 2) {
-      const float4 r0 = load4_masked(SAc + (long long)i * ldc, j, d);
-      const float4 r1 = load4_masked(SAc + (long long)(i + 1) * ldc, j, d);
-      const float w0 = w[i], w1 = w[i + 1];
-      a0.x = fmaf(r0.x, w0, a0.x); a0.y = fmaf(r0.y, w0, a0.y);
-      a0.z = fmaf(r0.z, w0, a0.z); a0.w = fmaf(r0.w, w0, a0.w);
-      a1.x = fmaf(r1.x, w1, a1.x); a1.y = fmaf(r1.y, w1, a1.y);
-      a1.z = fmaf(r1.z, w1, a1.z); a1.w = fmaf(r1.w, w1, a1.w);
-    }
-    if (i < ie) {
-      const float4 r0 = load4_masked(SAc + (long long)i * ldc, j, d);
-      const float w0 = w[i];
-      a0.x = fmaf(r0.x, w0, a0.x); a0.y = fmaf(r0.y, w0, a0.y);
-      a0.z = fmaf(r0.z, w0, a0.z); a0.w = fmaf(r0.w, w0, a0.w);
-    }
-    *reinterpret_cast<float4*>(u + j) = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
-  }
-}
-
-// Σ over the cluster of one scalar slot: lane r of every warp loads rank r's
-// value, then a fixed butterfly sums them (identical in every thread and
-// every block).
+// Σ over the cluster of one scalar slot: lane r loads rank r's value, then a
+// fixed butterfly sums them (identical wherever it is computed).
 template <int CL>
 __device__ __forceinline__ float cluster_scalar_sum(const float* my_rank_scal, int slot) {
   const int lane = threadIdx.x & 31;
@@ -160,24 +92,75 @@ __device__ __forceinline__ float cluster_scalar_sum(const float* my_rank_scal, i
   return warp_sum(v);
 }
 
-template <int CL>
+// Fused sweep over the block's rows of SA (each row read once per pass):
+//   w_i = SA_i·v − θ·p_i            (warp all-reduce of the row dot)
+//   u  += SA_iᵀ·w_i                 (lane ℓ accumulates columns 4ℓ + 128c)
+//   ρ²_part += w_i²
+// Warp `warp` takes rows warp, warp + 8, …; v and u live in registers (CH
+// float4 per lane), the per-warp u partials are written to `wpart`.
+template <int CH>
+__device__ __forceinline__ float fused_sweep(const float* SAc, long long ldc, int nr, int d,
+                                             const float* v, const float* p, float theta,
+                                             float* w, float* wpart, int dp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 vr[CH], ur[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int j = 4 * lane + 128 * c;
+    vr[c] = j < dp ? *reinterpret_cast<const float4*>(v + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    ur[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float rsq = 0.f;
+  for (int i = warp; i < nr; i += kWarps) {
+    const float* row = SAc + (long long)i * ldc;
+    float4 a[CH];
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j = 4 * lane + 128 * c;
+      a[c] = j < dp ? load4_masked(row, j, d) : make_float4(0.f, 0.f, 0.f, 0.f);
+      s0 = fmaf(a[c].x, vr[c].x, s0);
+      s1 = fmaf(a[c].y, vr[c].y, s1);
+      s0 = fmaf(a[c].z, vr[c].z, s0);
+      s1 = fmaf(a[c].w, vr[c].w, s1);
+    }
+    const float wi = warp_sum(s0 + s1) - theta * p[i];
+    rsq = fmaf(wi, wi, rsq);
+    if (lane == 0) w[i] = wi;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      ur[c].x = fmaf(a[c].x, wi, ur[c].x);
+      ur[c].y = fmaf(a[c].y, wi, ur[c].y);
+      ur[c].z = fmaf(a[c].z, wi, ur[c].z);
+      ur[c].w = fmaf(a[c].w, wi, ur[c].w);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int j = 4 * lane + 128 * c;
+    if (j < dp) *reinterpret_cast<float4*>(wpart + (size_t)warp * dp + j) = ur[c];
+  }
+  return rsq;  // this warp's share of ρ² (same in all lanes)
+}
+
+template <int CL, int CH>
 __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParams P) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int d = P.d, dp = P.dp;
 
   extern __shared__ float4 smem4[];
   float* v = reinterpret_cast<float*>(smem4);  // replicated d-vectors
   float* dv = v + dp;
   float* xs = dv + dp;
-  float* up0 = xs + dp;     // this block's partial SAᵀw, row half 0 (read remotely)
-  float* up1 = up0 + dp;    // row half 1 (read remotely)
-  float* zsl = up1 + dp;    // this block's slice of θv (read remotely)
-  float* p = zsl + dp;      // own rows
+  float* up = xs + dp;      // this block's SAᵀw (read remotely)
+  float* zsl = up + dp;     // this block's slice of θv (read remotely)
+  float* wpart = zsl + dp;  // kWarps × dp per-warp partials of SAᵀw
+  float* p = wpart + (size_t)kWarps * dp;  // own rows
   float* w = p + P.rpc_pad;
   float* red = w + P.rpc_pad;  // kWarps floats
-  float* scal = red + kWarps;  // [0] θ² partial, [1] ρ² partial (read remotely)
+  float* scal = red + kWarps;  // [0] θ² partial, [1] ρ² partial (read remotely), [2] broadcast
   uint64_t* stage_bar = reinterpret_cast<uint64_t*>(scal + 6);  // 8-byte aligned slot
   float* sa = scal + 8;        // SA rows (when kept in smem)
 
@@ -220,13 +203,11 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     SAc = sa;
     ldc = dp;
   } else if (P.sa_in_smem) {
-    const int q = dp / 4;
     for (int i = 0; i < nr; ++i) {
       const float* src = P.SA + (long long)(r0 + i) * P.ldsa;
       for (int j = 4 * tid; j < dp; j += 4 * kThreads)
         *reinterpret_cast<float4*>(sa + (size_t)i * dp + j) = load4_masked(src, j, d, P.sa_vec != 0);
     }
-    (void)q;
     SAc = sa;
     ldc = dp;
   } else {
@@ -243,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     xs[j] = 0.f;
     dv[j] = 0.f;
   }
+  for (int i = tid; i < P.rpc_pad; i += kThreads) p[i] = 0.f;
   const float theta1 = sqrtf(block_sum(gsq, red));
   if (staged_async) {
     // Every thread waits for the rows (also on the early-exit paths below, so
@@ -279,18 +261,30 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const float inv_theta1 = 1.0f / theta1;
     for (int j = tid; j < dp; j += kThreads) v[j] *= inv_theta1;
     __syncthreads();
-    // ρ p = SA v.  The normalisation by ρ is deferred: the block also forms
-    // SAᵀw for the next product before the cluster learns ρ, so one barrier
-    // publishes both the ρ² partials and the SAᵀw partials.
-    rows_dot4(SAc, ldc, nr, d, dp, v, w);
+    // One sweep: w = SA v (p = 0 here), ρ² partial and u = SAᵀw (ρ p = w, the
+    // normalisation by ρ deferred so that one barrier publishes both).
+    float rsq_w = fused_sweep<CH>(SAc, ldc, nr, d, v, p, 0.f, w, wpart, dp);
+    if (lane == 0) red[warp] = rsq_w;
     __syncthreads();
-    float part = 0.f;
-    for (int i = tid; i < nr; i += kThreads) part = fmaf(w[i], w[i], part);
-    part = block_sum(part, red);
-    if (tid == 0) scal[1] = part;
-    cols_dot_halves(SAc, ldc, nr, d, dp, w, up0, up1);
+    for (int j = tid; j < dp; j += kThreads) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) t += wpart[(size_t)q * dp + j];
+      up[j] = t;
+    }
+    if (tid == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) t += red[q];
+      scal[1] = t;
+    }
     cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-    float rho = sqrtf(cluster_scalar_sum<CL>(lane_scal, 1));
+    if (warp == 0) {
+      const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
+      if (lane == 0) scal[2] = r2;
+    }
+    __syncthreads();
+    float rho = sqrtf(scal[2]);
 
     const float lam = P.lambda;
     float rhobar = sqrtf(rho * rho + lam);
@@ -315,15 +309,12 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
       const float inv_rho = 1.0f / rho;
       float zpart = 0.f;
       for (int j = c0 + tid; j < c1; j += kThreads) {
-        float u0[CL], u1[CL];
+        float u[CL];
 #pragma unroll
-        for (int r = 0; r < CL; ++r) {
-          u0[r] = cluster.map_shared_rank(up0, r)[j];
-          u1[r] = cluster.map_shared_rank(up1, r)[j];
-        }
+        for (int r = 0; r < CL; ++r) u[r] = cluster.map_shared_rank(up, r)[j];
         float us = 0.f;
 #pragma unroll
-        for (int r = 0; r < CL; ++r) us += u0[r] + u1[r];
+        for (int r = 0; r < CL; ++r) us += u[r];
         const float z = j < d ? us * inv_rho - rho * v[j] : 0.f;
         zsl[j] = z;
         zpart = fmaf(z, z, zpart);
@@ -331,26 +322,41 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
       zpart = block_sum(zpart, red);
       if (tid == 0) scal[0] = zpart;
       cluster.sync();  // (B) slices of θv and θ² partials visible
-      const float theta = sqrtf(cluster_scalar_sum<CL>(lane_scal, 0));
+      if (warp == 0) {
+        const float t2 = cluster_scalar_sum<CL>(lane_scal, 0);
+        if (lane == 0) scal[2] = t2;
+      }
+      __syncthreads();
+      const float theta = sqrtf(scal[2]);
       if (!(theta > 0.f)) break;  // invariant subspace: same decision everywhere
       const float inv_theta = 1.0f / theta;
       for (int j = tid; j < dp; j += kThreads)
         v[j] = cluster.map_shared_rank(zsl, j >> P.cols_log2)[j] * inv_theta;
       __syncthreads();
-      // ρ p := SA v − θ p (kept unnormalised in w until ρ is known)
-      rows_dot4(SAc, ldc, nr, d, dp, v, w);
+      // ρ p := SA v − θ p (kept unnormalised in w until ρ is known), its ρ²
+      // partial and SAᵀw, in one sweep.
+      rsq_w = fused_sweep<CH>(SAc, ldc, nr, d, v, p, theta, w, wpart, dp);
+      if (lane == 0) red[warp] = rsq_w;
       __syncthreads();
-      part = 0.f;
-      for (int i = tid; i < nr; i += kThreads) {
-        const float wi = w[i] - theta * p[i];
-        w[i] = wi;
-        part = fmaf(wi, wi, part);
+      for (int j = tid; j < dp; j += kThreads) {
+        float tt = 0.f;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) tt += wpart[(size_t)q * dp + j];
+        up[j] = tt;
       }
-      part = block_sum(part, red);  // also orders the w updates before the next product
-      if (tid == 0) scal[1] = part;
-      cols_dot_halves(SAc, ldc, nr, d, dp, w, up0, up1);
+      if (tid == 0) {
+        float tt = 0.f;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) tt += red[q];
+        scal[1] = tt;
+      }
       cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-      rho = sqrtf(cluster_scalar_sum<CL>(lane_scal, 1));
+      if (warp == 0) {
+        const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
+        if (lane == 0) scal[2] = r2;
+      }
+      __syncthreads();
+      rho = sqrtf(scal[2]);
       // Eldén's rotation of √λ into the bidiagonal, then the φ recursion and
       // the forward-substitution update (Section 3.6).
       const float lambar = sqrtf(lam + (s * theta) * (s * theta));
@@ -405,13 +411,23 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
 
 using AabKernelFn = void (*)(const AabParams);
 
-AabKernelFn kernel_for(int cl) {
+template <int CL>
+AabKernelFn kernel_for_ch(int ch) {
+  if (ch <= 2) return aab_cluster_kernel<CL, 2>;
+  if (ch <= 4) return aab_cluster_kernel<CL, 4>;
+  if (ch <= 8) return aab_cluster_kernel<CL, 8>;
+  return aab_cluster_kernel<CL, 16>;
+}
+
+// Kernel for a cluster size and a padded width dp (CH float4 per lane).
+AabKernelFn kernel_for(int cl, int dp) {
+  const int ch = (dp + 127) / 128;
   switch (cl) {
-    case 1: return aab_cluster_kernel<1>;
-    case 2: return aab_cluster_kernel<2>;
-    case 4: return aab_cluster_kernel<4>;
-    case 8: return aab_cluster_kernel<8>;
-    default: return aab_cluster_kernel<16>;
+    case 1: return kernel_for_ch<1>(ch);
+    case 2: return kernel_for_ch<2>(ch);
+    case 4: return kernel_for_ch<4>(ch);
+    case 8: return kernel_for_ch<8>(ch);
+    default: return kernel_for_ch<16>(ch);
   }
 }
 
@@ -424,12 +440,12 @@ struct ClusterPlan {
 size_t smem_bytes(int m, int dp, int cl, bool in_smem) {
   const int rpc = (m + cl - 1) / cl;
   const int rpc_pad = (int)round_up(rpc, 4);
-  size_t base = (size_t)(6 * dp + 2 * rpc_pad + kWarps + 8) * sizeof(float);
+  size_t base = (size_t)((5 + kWarps) * dp + 2 * rpc_pad + kWarps + 8) * sizeof(float);
   if (in_smem) base += (size_t)rpc * dp * sizeof(float);
   return base;
 }
 
-bool cluster_fits(int cl, size_t smem) {
+bool cluster_fits(int cl, int dp, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -442,7 +458,7 @@ bool cluster_fits(int cl, size_t smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel_for(cl), &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel_for(cl, dp), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -452,11 +468,12 @@ bool cluster_fits(int cl, size_t smem) {
 ClusterPlan plan_cluster_uncached(int m, int dp) {
   static bool attr_set = false;
   if (!attr_set) {
-    for (int cl : {1, 2, 4, 8, 16}) {
-      cudaFuncSetAttribute((void*)kernel_for(cl), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      cudaFuncSetAttribute((void*)kernel_for(cl), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSmemBudget + 16 * 1024);
-    }
+    for (int cl : {1, 2, 4, 8, 16})
+      for (int w : {256, 512, 1024, 2048}) {
+        cudaFuncSetAttribute((void*)kernel_for(cl, w), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute((void*)kernel_for(cl, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBudget + 16 * 1024);
+      }
     attr_set = true;
   }
   int forced = 0;
@@ -467,7 +484,7 @@ ClusterPlan plan_cluster_uncached(int m, int dp) {
     if (forced > 0 && cl != forced) continue;
     if (cl > m && cl > 1) break;
     const size_t sm = smem_bytes(m, dp, cl, true);
-    if (sm <= kSmemBudget && cluster_fits(cl, sm)) return {cl, 1, sm};
+    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm)) return {cl, 1, sm};
   }
   // Otherwise the largest launchable cluster reading SA from global memory (L2).
   for (int i = 4; i >= 0; --i) {
@@ -475,7 +492,7 @@ ClusterPlan plan_cluster_uncached(int m, int dp) {
     if (forced > 0 && cl != forced) continue;
     if (cl > m && cl > 1) continue;
     const size_t sm = smem_bytes(m, dp, cl, false);
-    if (sm <= kSmemBudget && cluster_fits(cl, sm)) return {cl, 0, sm};
+    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm)) return {cl, 0, sm};
   }
   return {0, 0, 0};
 }
@@ -550,7 +567,7 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   timing_begin(kTimerAab, s);
-  MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel_for(cp.cl), P));
+  MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel_for(cp.cl, P.dp), P));
   timing_end(kTimerAab, s);
   count_launch();
   return MIHS_OK;
