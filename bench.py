@@ -32,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FAMILIES = ["gaussian", "countsketch", "srht"]
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one A-pass
+# launch from the ncu capture summarised in
+# profiles/apass_partial_kernel_ridge-65536x1024.md (65536×1024).  Traffic is
+# one read of A plus O(d) vectors, so it scales with the rows processed.
+APASS_NCU = {"n": 65536, "d": 1024, "bytes": 268.741120e6 + 3.547392e6}
 METRIC = "ridge solves/s at stated rel. error"
 
 
@@ -286,7 +292,9 @@ def main():
     roofline = {"bound": "hbm", "kernel": "apass_partial_kernel (gradient g = Aᵀ(b−Ax) − λx)",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": f"{peak_src} hbm_gbs",
-                "traffic": None, "bytes_per_launch": bytes_per_pass,
+                "traffic": (round(APASS_NCU["bytes"] * n / APASS_NCU["n"]) if d == APASS_NCU["d"] else None),
+                "traffic_source": "ncu capture at 65536 rows, scaled by rows",
+                "bytes_per_launch": bytes_per_pass,
                 "avg_launch_us": round(apass_avg_s * 1e6, 2), "launches_timed": apass_n}
 
     # ---------------- accuracy vs the oracle's exact solution
