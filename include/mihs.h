@@ -151,6 +151,16 @@ int mihs_aab_heavy_ball(const float* SA, int64_t m, int64_t d, int64_t ldsa,
                         int max_inner, double alpha, double beta,
                         float* x, float* x_prev, int* passes, void* stream);
 
+/* Statistical dimension estimate (Algorithm 4, inexact Hutchinson):
+ *     sd ≈ d − (λ/T)·Σ_ℓ ⟨v^ℓ, z^ℓ⟩,   z^ℓ = AAb_Solver(SA, v^ℓ, λ, eps_tr),
+ * with Rademacher probes v^ℓ_j = ±1 from Philox counter (j, ℓ, 4, 0) keyed by
+ * `seed`.  The paper uses T = 2 or 3 and eps_tr = 0.5.  Synchronises the
+ * stream and writes the estimate to the HOST double *sd_out.  Allocates
+ * stream-ordered scratch (2d floats).  Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa,
+                     double lambda, int T, double eps_tr, uint64_t seed,
+                     double* sd_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * The solver (Algorithm 1, M-IHS for n ≥ d).
  * ---------------------------------------------------------------------- */
@@ -191,8 +201,10 @@ typedef struct {
   int max_outer;    /* N of Algorithm 1: at most this many momentum steps   */
   double eps_sub;   /* forcing term ε_sub of AAb_Solver (0.1 in the paper)  */
   int max_inner;    /* cap on AAb_Solver passes per step (≤ 0: min(m, d))   */
-  double sd;        /* statistical dimension estimate, 0 < sd < m; gives
-                       β = sd/m and α = (1 − β)² (Corollary 3)             */
+  double sd;        /* statistical dimension estimate, sd < m; gives
+                       β = sd/m and α = (1 − β)² (Corollary 3).  sd ≤ 0:
+                       estimated from SA by Algorithm 4 (T = 2, eps 0.5,
+                       capped at 0.95·m); the call then synchronises      */
   int warm_start;   /* 0: x is ignored and the iteration starts at 0;
                        1: x holds x¹ (costs one extra pass over A for ‖Aᵀb‖) */
 } mihs_opts;
@@ -227,6 +239,28 @@ mihs_opts mihs_default_opts(void);
 int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
                double lambda, const mihs_opts* opts, float* x, mihs_info* info,
                void* stream);
+
+/* Algorithm 1 with compensated refinement: the same iteration with the
+ * iterate x in fp64 and the gradient g = Aᵀ(b − Ax) − λx computed by a
+ * compensated pass over A (double-float sums: TwoProduct/TwoSum in fp32
+ * pairs, fp64 partial sums), while SA, AAb_Solver and its stop test stay
+ * fp32 (the sketch only preconditions; the fixed point of the iteration is
+ * where the gradient vanishes).  For targets below the fp32 floor
+ * (relative error ~1e-6 and beyond).  x is a DEVICE double array (x¹ on
+ * entry if warm_start).  The first refined solve on a handle allocates its
+ * workspace (double-float partials, fp64 previous iterate) with cudaMalloc.
+ * Same arguments, semantics and errors as mihs_solve otherwise. */
+int mihs_solve_refined(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
+                       double lambda, const mihs_opts* opts, double* x,
+                       mihs_info* info, void* stream);
+
+/* The compensated gradient of mihs_solve_refined on its own:
+ * g = Aᵀ(b − Ax) − λx with x and g DEVICE double arrays (d), A and b fp32.
+ * Allocates stream-ordered scratch for the double-float partials.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda,
+                          const float* b, const double* x, double lambda,
+                          double* g, void* stream);
 
 /* Trace of the last solve on this handle: the relative residual
  * ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step (i = 0, 1, …, at most 1024 entries)

@@ -25,6 +25,7 @@ Contents and the passage each follows:
   momentum_params ...... β = sd/m, α = (1−β)² (Corollary 3, Algorithm 1).
   theorem1_params ...... β*, α*, rate of Theorem 1.
   mihs ................. Algorithm 1 (M-IHS for n ≥ d).
+  hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
   heavy_ball ........... x⁺ = x + αΔ + β(x − x⁻) (Eq. mihs1).
   characteristic_rate .. roots of u² − (1+β−αμ)u + β (proof of Theorem 1).
 
@@ -59,6 +60,7 @@ TAG_GAUSSIAN = 0
 TAG_COUNTSKETCH = 1
 TAG_SRHT_SIGNS = 2
 TAG_SRHT_ROWS = 3
+TAG_HUTCHINSON = 4
 
 GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
 FAMILY_NAMES = {GAUSSIAN: "gaussian", COUNTSKETCH: "countsketch", SRHT: "srht"}
@@ -223,10 +225,13 @@ def gradient(A, b, x, lam):
     return A.T @ r - lam * x
 
 
-def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16):
+def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16, extended: bool = False):
     """x* = (AᵀA + λI)⁻¹Aᵀb: fp64 Gram matrix (row blocks summed in order),
     Cholesky, two triangular solves, then `refine` steps of iterative
-    refinement x += H⁻¹(Aᵀ(b−Ax) − λx)."""
+    refinement x += H⁻¹(Aᵀ(b−Ax) − λx).  With `extended`, the refinement
+    residual is formed in numpy's extended precision (np.longdouble: 64-bit
+    significand on x86-64, IEEE quad on aarch64), which makes the result
+    accurate to ~κ(H)·u_ext instead of ~κ(H)·u₆₄."""
     n, d = np.shape(A)
     H = np.zeros((d, d))
     Atb = np.zeros(d)
@@ -243,8 +248,20 @@ def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16):
 
     x = hsolve(Atb)
     for _ in range(refine):
-        x = x + hsolve(gradient_blocked(A, b, x, lam, row_block))
+        r = gradient_extended(A, b, x, lam, row_block) if extended else gradient_blocked(A, b, x, lam, row_block)
+        x = x + hsolve(np.asarray(r, dtype=np.float64))
     return x
+
+
+def gradient_extended(A, b, x, lam, row_block: int = 1 << 14):
+    """g = Aᵀ(b − Ax) − λx in np.longdouble (row blocks summed in order)."""
+    n = np.shape(A)[0]
+    xe = np.asarray(x, dtype=np.longdouble)
+    g = -np.longdouble(lam) * xe
+    for r0 in range(0, n, row_block):
+        Ab = np.asarray(A[r0:r0 + row_block], dtype=np.longdouble)
+        g += Ab.T @ (np.asarray(b[r0:r0 + row_block], dtype=np.longdouble) - Ab @ xe)
+    return g
 
 
 def gradient_blocked(A, b, x, lam, row_block: int = 1 << 16):
@@ -482,3 +499,27 @@ def mihs_solve(A, b, lam, family, m, sd, seed, N=200, tol=1e-6, eps_sub=0.1,
     SA = sketch_apply(family, A, m, seed)
     return mihs(A, b, lam, SA, sd, N, eps_sub=eps_sub, tol=tol,
                 max_inner=max_inner, dtype=dtype)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4: inexact Hutchinson trace estimator of the statistical dimension
+# ---------------------------------------------------------------------------
+def rademacher_probe(d: int, ell: int, seed: int) -> np.ndarray:
+    """Probe v^ℓ ∈ {−1, +1}^d: entry j from Philox counter (j, ℓ,
+    TAG_HUTCHINSON, 0), +1 when w0 is even."""
+    k0, k1 = seed_key(seed)
+    w0, _, _, _ = philox4x32_10(np.arange(d, dtype=np.uint64), np.uint64(ell), TAG_HUTCHINSON, 0, k0, k1)
+    return np.where((w0 & np.uint64(1)) == 0, 1.0, -1.0)
+
+
+def hutchinson_sd(SA, lam, T, eps_tr, seed, max_iter=None, dtype=np.float64):
+    """sd ≈ d − (λ/T)·Σ_ℓ ⟨v^ℓ, z^ℓ⟩ with z^ℓ = AAb_Solver(SA, v^ℓ, λ, ε_tr):
+    tr(A(AᵀA+λI)⁻¹Aᵀ) = d − λ·tr((AᵀA+λI)⁻¹) with SA standing in for A."""
+    SA = np.asarray(SA, dtype=np.float64)
+    d = SA.shape[1]
+    tau = 0.0
+    for ell in range(T):
+        v = rademacher_probe(d, ell, seed)
+        z, _ = aab_solve(SA, v, lam, eps_tr, max_iter=max_iter, dtype=dtype)
+        tau += lam * float(np.dot(v, np.asarray(z, dtype=np.float64)))
+    return d - tau / T

@@ -48,6 +48,9 @@ struct AabParams {
   float alpha, beta;
   float* x;
   float* x_prev;
+  double* x64;
+  double* x_prev64;
+  double alpha64, beta64;
   SolveCtl* ctl;
   float* hist;
   unsigned long long cond;
@@ -392,6 +395,11 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
         P.x[j] = xj + P.alpha * dj + P.beta * (xj - xp);
         P.x_prev[j] = xj;
       }
+      if (P.x64 != nullptr) {
+        const double xj = P.x64[j], xp = P.x_prev64[j];
+        P.x64[j] = xj + P.alpha64 * (double)dj + P.beta64 * (xj - xp);
+        P.x_prev64[j] = xj;
+      }
     }
   }
   if (rank == 0 && tid == 0) {
@@ -530,6 +538,10 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   P.beta = a.beta;
   P.x = a.x;
   P.x_prev = a.x_prev;
+  P.x64 = a.x64;
+  P.x_prev64 = a.x_prev64;
+  P.alpha64 = a.alpha64;
+  P.beta64 = a.beta64;
   P.ctl = a.ctl;
   P.cond = a.cond;
   P.hist = a.hist;

@@ -1,0 +1,342 @@
+// Compensated gradient for the refinement solve:  g = Aᵀ(b − Ax) − λx with
+// x in fp64 and the sums carried in double-float (an unevaluated pair of
+// fp32 numbers hi + lo):
+//   * products by TwoProduct (p = a·x_hi, e = fma(a, x_hi, −p) exactly, plus
+//     a·x_lo), sums by TwoSum (Knuth; Ogita, Rump & Oishi, "Accurate sum and
+//     dot product", SIAM J. Sci. Comput. 2005), so the row residual and the
+//     column sums keep about twice the fp32 precision;
+//   * the split-K partials are pairs, summed in fp64 by the finalize kernel,
+//     which also subtracts λx in fp64.
+// The stream of A is the same as the plain A-pass (bulk-copy ring, one read
+// of A); the extra fp32 arithmetic (~10 operations per element and phase)
+// hides under the memory time.  This is the accuracy-critical step of M-IHS:
+// the iteration's fixed point is where this gradient vanishes, while the
+// sketch and AAb_Solver only precondition.
+#include "internal.h"
+
+namespace mihs {
+
+namespace {
+
+// Consumer warps per block: 8, or 7 for rows wider than 1024 so that the
+// block has 256 threads and each may hold 255 registers (the double-float
+// column accumulators need 8 registers per float4 column group).
+template <int CH>
+struct DdCfg {
+  static constexpr int NC = CH > 8 ? 7 : 8;
+  static constexpr int kThreads = (NC + 1) * 32;
+};
+constexpr size_t kRingBudget = 150 * 1024;
+
+__device__ int g_apass_dd_error = 0;
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// (s.hi + s.lo) += v (+ ve): compensated accumulation of a value with its error.
+__device__ __forceinline__ void df_add(DF& s, float v, float ve) {
+  float t, e;
+  two_sum(s.hi, v, t, e);
+  s.hi = t;
+  s.lo += e + ve;
+}
+
+// a·(x_hi + x_lo) as (p, e) with p + e exact up to a·x_lo's rounding.
+__device__ __forceinline__ void df_prod(float a, float xh, float xl, float& p, float& e) {
+  p = a * xh;
+  e = fmaf(a, xh, -p);
+  e = fmaf(a, xl, e);
+}
+
+__device__ __forceinline__ DF df_shfl_xor_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    float t, e;
+    two_sum(v.hi, oh, t, e);
+    v.hi = t;
+    v.lo = v.lo + ol + e;
+  }
+  return v;
+}
+
+template <int CH>
+__global__ void __launch_bounds__(DdCfg<CH>::kThreads, 1)
+apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const float* __restrict__ b,
+                const double* __restrict__ x, float2* __restrict__ partials, int dpad, int rows_per_cta,
+                int stages, SolveCtl* __restrict__ ctl) {
+  constexpr int NC = DdCfg<CH>::NC, R = NC;
+  constexpr int kThreads = DdCfg<CH>::kThreads;
+  if (ctl != nullptr && ctl->done) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
+  uint64_t* empty = full + stages;
+  float* xh = reinterpret_cast<float*>(empty + stages);  // CH·128 each
+  float* xl = xh + CH * 128;
+  __shared__ int issued;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min((long long)n, r0 + rows_per_cta);
+  const int nst = r1 > r0 ? (int)((r1 - r0 + R - 1) / R) : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NC);
+    }
+    issued = 0;
+    fence_mbar_init();
+  }
+  for (int j = threadIdx.x; j < CH * 128; j += kThreads) {
+    const double xv = (x != nullptr && j < d) ? x[j] : 0.0;
+    const float h = (float)xv;
+    xh[j] = h;
+    xl[j] = (float)(xv - (double)h);
+  }
+  __syncthreads();
+
+  if (warp == NC) {  // producer
+    if (lane == 0) {
+      const uint32_t row_bytes = (uint32_t)dpad * 4u;
+      const bool contiguous = lda == (long long)dpad;
+      for (int it = 0; it < nst; ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        if (it >= stages && !mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs)) {
+          atomicExch(&g_apass_dd_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
+        const long long row0 = r0 + (long long)it * R;
+        const int rows = (int)min((long long)R, r1 - row0);
+        float* dst = ring + (size_t)s * R * dpad;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)rows * row_bytes);
+        if (contiguous) {
+          bulk_copy_g2s(dst, A + row0 * lda, (uint32_t)rows * row_bytes, &full[s]);
+        } else {
+          for (int r = 0; r < rows; ++r)
+            bulk_copy_g2s(dst + (size_t)r * dpad, A + (row0 + r) * lda, row_bytes, &full[s]);
+        }
+        *(volatile int*)&issued = it + 1;
+      }
+    }
+    return;
+  }
+
+  DF acc[CH][4];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[c][q] = DF{0.f, 0.f};
+  int consumed = 0;
+  for (int it = 0; it < nst; ++it) {
+    const int s = it % stages;
+    const uint32_t ph = (uint32_t)(it / stages) & 1u;
+    const long long row = r0 + (long long)it * R + warp;
+    const float bi = row < r1 ? __ldg(b + row) : 0.f;
+    if (!mbar_wait(&full[s], ph, kWaitLimitNs)) {
+      atomicExch(&g_apass_dd_error, MIHS_ERR_TIMEOUT);
+      break;
+    }
+    if (row < r1) {  // uniform across the warp
+      const float4* row4 = reinterpret_cast<const float4*>(ring + ((size_t)s * R + warp) * dpad);
+      // Column group c of the row; the ragged last float4 is masked because the
+      // copied padding may hold anything.  Read twice (dot, then accumulate)
+      // instead of being kept in registers.
+      auto chunk = [&](int c) {
+        const int col = 4 * lane + 128 * c;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col < d) {
+          t = row4[lane + 32 * c];
+          if (col + 4 > d) {
+            if (col + 1 >= d) t.y = 0.f;
+            if (col + 2 >= d) t.z = 0.f;
+            t.w = 0.f;
+          }
+        }
+        return t;
+      };
+      DF sum = {0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int col = 4 * lane + 128 * c;
+        const float4 t = chunk(c);
+        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
+        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
+        float p, e;
+        df_prod(t.x, h4.x, l4.x, p, e);
+        df_add(sum, p, e);
+        df_prod(t.y, h4.y, l4.y, p, e);
+        df_add(sum, p, e);
+        df_prod(t.z, h4.z, l4.z, p, e);
+        df_add(sum, p, e);
+        df_prod(t.w, h4.w, l4.w, p, e);
+        df_add(sum, p, e);
+      }
+      sum = df_shfl_xor_sum(sum);
+      // r = b − (sum.hi + sum.lo), renormalised to a double-float pair
+      float rh, re;
+      two_sum(bi, -sum.hi, rh, re);
+      float r_hi, r_lo;
+      two_sum(rh, re - sum.lo, r_hi, r_lo);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const float4 t = chunk(c);
+        float p, e;
+        df_prod(t.x, r_hi, r_lo, p, e);
+        df_add(acc[c][0], p, e);
+        df_prod(t.y, r_hi, r_lo, p, e);
+        df_add(acc[c][1], p, e);
+        df_prod(t.z, r_hi, r_lo, p, e);
+        df_add(acc[c][2], p, e);
+        df_prod(t.w, r_hi, r_lo, p, e);
+        df_add(acc[c][3], p, e);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    consumed = it + 1;
+  }
+  if (consumed < nst && warp == 0 && lane == 0) {
+    // Aborted: let the copies already issued land before the block exits.
+    const int iss = *(volatile int*)&issued;
+    for (int it = consumed; it < iss; ++it)
+      if (!mbar_wait(&full[it % stages], (uint32_t)(it / stages) & 1u, kWaitLimitNs)) break;
+    if (ctl != nullptr) {
+      ctl->status = MIHS_ERR_TIMEOUT;
+      ctl->done = 1;
+    }
+  }
+  named_sync(1, NC * 32);  // every consumer is done with the ring
+  // Per-warp pairs into the ring memory, then a fixed-order fp64 sum per column.
+  float2* wpart = reinterpret_cast<float2*>(ring);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = 4 * lane + 128 * c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (col + q < dpad) wpart[(size_t)warp * dpad + col + q] = make_float2(acc[c][q].hi, acc[c][q].lo);
+  }
+  named_sync(1, NC * 32);
+  float2* out = partials + (size_t)blockIdx.x * dpad;
+  for (int j = threadIdx.x; j < dpad; j += NC * 32) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NC; ++w) {
+      const float2 v = wpart[(size_t)w * dpad + j];
+      t += (double)v.x + (double)v.y;
+    }
+    const float hi = (float)t;
+    out[j] = make_float2(hi, (float)(t - (double)hi));
+  }
+}
+
+// g[j] = Σ_p (hi + lo) − λ·x[j] in fp64 (fixed order); also an fp32 copy.
+__global__ void __launch_bounds__(256)
+apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int dpad,
+                         const double* __restrict__ x, double lambda, double* __restrict__ g64,
+                         float* __restrict__ g32, const SolveCtl* __restrict__ ctl) {
+  if (ctl != nullptr && ctl->done) return;
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (j < d)
+    for (int p = grp; p < P; p += 8) {
+      const float2 v = partials[(size_t)p * dpad + j];
+      s += (double)v.x + (double)v.y;
+    }
+  red[grp][lane] = s;
+  __syncthreads();
+  if (grp == 0 && j < d) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    if (x != nullptr) t -= lambda * x[j];
+    if (g64 != nullptr) g64[j] = t;
+    if (g32 != nullptr) g32[j] = (float)t;
+  }
+}
+
+struct DdKernel {
+  const void* fn;
+  int chunks;
+  int nc;  // consumer warps = rows per stage
+};
+
+template <int CH>
+DdKernel make_dd() {
+  return DdKernel{reinterpret_cast<const void*>(&apass_dd_kernel<CH>), CH, DdCfg<CH>::NC};
+}
+
+DdKernel pick_dd(int64_t d) {
+  const int ch = (int)((d + 127) / 128);
+  if (ch <= 1) return make_dd<1>();
+  if (ch <= 2) return make_dd<2>();
+  if (ch <= 4) return make_dd<4>();
+  if (ch <= 8) return make_dd<8>();
+  if (ch <= 12) return make_dd<12>();
+  return make_dd<16>();
+}
+
+}  // namespace
+
+int apass_dd_num_partials(int64_t n, int64_t d) {
+  const int nc = pick_dd(d).nc;
+  const int64_t by_rows = (n + nc - 1) / nc;
+  int64_t P = num_sms();
+  if (P > by_rows) P = by_rows;
+  return (int)(P < 1 ? 1 : P);
+}
+
+int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
+                    float2* partials, SolveCtl* ctl, cudaStream_t s) {
+  const DdKernel k = pick_dd(d);
+  const int P = apass_dd_num_partials(n, d);
+  const int64_t dpad = apass_dpad(d);
+  const int R = k.nc;
+  const int rows_per_cta = (int)round_up((n + P - 1) / P, R);
+  const size_t stage_bytes = (size_t)R * dpad * sizeof(float);
+  int stages = (int)(kRingBudget / stage_bytes);
+  stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
+  // The ring must also hold the NC × dpad float2 warp pairs at the end.
+  while ((size_t)stages * stage_bytes < (size_t)k.nc * dpad * sizeof(float2)) ++stages;
+  const size_t smem = (size_t)stages * stage_bytes + 2 * sizeof(uint64_t) * stages +
+                      2 * (size_t)k.chunks * 128 * sizeof(float);
+  MIHS_CUDA_TRY(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int n32 = (int)n, d32 = (int)d, dp32 = (int)dpad;
+  long long lda64 = lda;
+  void* args[] = {(void*)&A, &n32, &d32, &lda64, (void*)&b, (void*)&x,
+                  (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl};
+  timing_begin(kTimerApass, s);
+  MIHS_CUDA_TRY(cudaLaunchKernel(k.fn, dim3(P), dim3((k.nc + 1) * 32), args, smem, s));
+  timing_end(kTimerApass, s);
+  count_launch();
+  return MIHS_OK;
+}
+
+int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s) {
+  apass_dd_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)apass_dpad(d), x,
+                                                                     lambda, g64, g32, ctl);
+  MIHS_CHECK_LAUNCH();
+  count_launch();
+  return MIHS_OK;
+}
+
+int apass_dd_device_error(int* code) {
+  int v = 0, zero = 0;
+  MIHS_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_apass_dd_error, sizeof(int)));
+  if (v != 0) MIHS_CUDA_TRY(cudaMemcpyToSymbol(g_apass_dd_error, &zero, sizeof(int)));
+  *code = v;
+  return MIHS_OK;
+}
+
+}  // namespace mihs

@@ -133,6 +133,15 @@ struct mihs_sketch_s {
   float* g;           // dp
   float* x_prev;      // dp
   float* hist;        // kHistCap: ‖g‖ per gradient step of the last solve
+  // Refinement workspace (allocated on first refined solve): double-float
+  // partials of the compensated A-pass and the fp64 previous iterate.
+  float2* dd_partials = nullptr;
+  double* x_prev64 = nullptr;
+  int P_dd = 0;
+  cudaGraphExec_t exec_dd = nullptr;
+  cudaGraph_t graph_dd = nullptr;
+  bool graph_dd_failed = false;
+  double last_sd = 0; // sd estimated by the last solve that was given sd ≤ 0
   SolveCtl* ctl;
   SolveCtl* ctl_host; // pinned
   // Device-side outer loop: a CUDA graph holding one conditional WHILE node
@@ -144,13 +153,13 @@ struct mihs_sketch_s {
   cudaGraphExec_t exec = nullptr;
   bool graph_failed = false;
   struct Key {
-    const float* A; int64_t lda; const float* b; float* x;
-    float lam, alpha, beta, eps; int max_passes;
+    const float* A; int64_t lda; const float* b; void* x;
+    double lam, alpha, beta; float eps; int max_passes;
     bool operator==(const Key& o) const {
       return A == o.A && lda == o.lda && b == o.b && x == o.x && lam == o.lam &&
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
-  } key = {};
+  } key = {}, key_dd = {};
 };
 
 namespace {
@@ -162,14 +171,43 @@ void drop_graph(mihs_sketch_s* sk) {
   sk->graph = nullptr;
 }
 
+void drop_graph_dd(mihs_sketch_s* sk) {
+  if (sk->exec_dd) cudaGraphExecDestroy(sk->exec_dd);
+  if (sk->graph_dd) cudaGraphDestroy(sk->graph_dd);
+  sk->exec_dd = nullptr;
+  sk->graph_dd = nullptr;
+}
+
+// One outer step of Algorithm 1 (gradient, partial-sum reduce, AAb_Solver +
+// heavy ball), plain fp32 or compensated (refinement).
+int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& a, bool refined,
+                cudaStream_t s) {
+  int rc;
+  if (refined) {
+    rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const double*>(key.x),
+                         sk->dd_partials, sk->ctl, s);
+    if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, static_cast<const double*>(key.x),
+                                           key.lam, nullptr, sk->g, sk->ctl, s);
+  } else {
+    rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const float*>(key.x),
+                              sk->partials, sk->ctl, s);
+    if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, static_cast<const float*>(key.x),
+                                        (float)key.lam, sk->g, sk->ctl, s);
+  }
+  if (!rc) rc = launch_aab(a, s);
+  return rc;
+}
+
 // Captures the loop body into a conditional WHILE node.  Returns MIHS_OK or
 // an error (the caller then falls back to host-driven iterations).
-int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto) {
-  drop_graph(sk);
+int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto, bool refined) {
+  cudaGraph_t& graph = refined ? sk->graph_dd : sk->graph;
+  cudaGraphExec_t& exec = refined ? sk->exec_dd : sk->exec;
+  if (refined) drop_graph_dd(sk); else drop_graph(sk);
   if (!sk->cap) MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&sk->cap, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   MIHS_CUDA_TRY(cudaGraphCreate(&g, 0));
-  sk->graph = g;
+  graph = g;
   cudaGraphConditionalHandle h;
   MIHS_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np = {};
@@ -185,9 +223,7 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
                                               cudaStreamCaptureModeThreadLocal));
   AabLaunch a = proto;
   a.cond = (unsigned long long)h;
-  int rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, key.x, sk->partials, sk->ctl, sk->cap);
-  if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, key.x, key.lam, sk->g, sk->ctl, sk->cap);
-  if (!rc) rc = launch_aab(a, sk->cap);
+  int rc = launch_step(sk, key, a, refined, sk->cap);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(sk->cap, &out);
   if (rc) return rc;
@@ -195,8 +231,8 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
     set_error("graph capture: %s", cudaGetErrorString(e));
     return MIHS_ERR_CUDA;
   }
-  MIHS_CUDA_TRY(cudaGraphInstantiate(&sk->exec, g, 0));
-  sk->key = key;
+  MIHS_CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
+  if (refined) sk->key_dd = key; else sk->key = key;
   return MIHS_OK;
 }
 
@@ -225,12 +261,14 @@ uint64_t mihs_launch_count(void) { return g_launches.load(); }
 int mihs_device_status(int* code) {
   set_error("");
   MIHS_ARG(code != nullptr, "mihs_device_status: null code");
-  int a = 0, g = 0;
+  int a = 0, g = 0, dd = 0;
   int rc = apass_device_error(&a);
   if (rc) return rc;
   rc = gauss_tc_device_error(&g);
   if (rc) return rc;
-  *code = a ? a : g;
+  rc = apass_dd_device_error(&dd);
+  if (rc) return rc;
+  *code = a ? a : (g ? g : dd);
   return MIHS_OK;
 }
 
@@ -372,6 +410,16 @@ int mihs_aab_heavy_ball(const float* SA, int64_t m, int64_t d, int64_t ldsa, con
   return launch_aab(a, static_cast<cudaStream_t>(stream));
 }
 
+int mihs_estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lambda, int T,
+                     double eps_tr, uint64_t seed, double* sd_out, void* stream) {
+  set_error("");
+  int rc = aab_common(SA, m, d, ldsa, SA, lambda, eps_tr, 0, "mihs_estimate_sd");
+  if (rc) return rc;
+  MIHS_ARG(T >= 1 && T <= 1024, "mihs_estimate_sd: T=%d outside [1, 1024]", T);
+  MIHS_ARG(sd_out != nullptr, "mihs_estimate_sd: null sd_out");
+  return estimate_sd(SA, m, d, ldsa, lambda, T, eps_tr, seed, sd_out, static_cast<cudaStream_t>(stream));
+}
+
 int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, int64_t m,
                 uint64_t seed, void* stream, mihs_sketch_t* out) {
   set_error("");
@@ -477,30 +525,56 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk == nullptr) return MIHS_OK;
   cudaDeviceSynchronize();
   drop_graph(sk);
+  drop_graph_dd(sk);
   if (sk->cap) cudaStreamDestroy(sk->cap);
+  if (sk->dd_partials) cudaFree(sk->dd_partials);
   cudaFreeHost(sk->ctl_host);
   cudaFree(sk->SA);
   delete sk;
   return MIHS_OK;
 }
 
-int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
-               const mihs_opts* opts, float* x, mihs_info* info, void* stream) {
+static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
+                      const mihs_opts* opts, void* xv, bool refined, mihs_info* info, void* stream) {
   set_error("");
   MIHS_ARG(sk != nullptr && opts != nullptr, "mihs_solve: null handle or opts");
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve");
   if (rc) return rc;
-  MIHS_ARG(b != nullptr && x != nullptr, "mihs_solve: null b or x");
+  MIHS_ARG(b != nullptr && xv != nullptr, "mihs_solve: null b or x");
   MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve: lambda must be > 0");
-  MIHS_ARG(opts->sd > 0.0 && opts->sd < (double)sk->m,
-           "mihs_solve: sd=%g must lie in (0, m=%lld)", opts->sd, (long long)sk->m);
+  MIHS_ARG(opts->sd < (double)sk->m, "mihs_solve: sd=%g must be < m=%lld", opts->sd, (long long)sk->m);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
   MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve: eps_sub must be >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = sk->n, d = sk->d;
+  if (refined && sk->dd_partials == nullptr) {
+    sk->P_dd = apass_dd_num_partials(n, d);
+    char* p = nullptr;
+    const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + sizeof(double) * (size_t)sk->dp;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      set_error("mihs_solve_refined: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+    }
+    sk->dd_partials = reinterpret_cast<float2*>(p);
+    sk->x_prev64 = reinterpret_cast<double*>(p + sizeof(float2) * (size_t)sk->P_dd * sk->dp);
+  }
+  // sd ≤ 0: estimate it from SA (Algorithm 4 with the paper's T = 2,
+  // ε_tr = 0.5); an over-estimate only slows the rate (Remark after
+  // Corollary 3), so the estimate is capped below m.
+  double sd = opts->sd;
+  if (!(sd > 0.0)) {
+    rc = estimate_sd(sk->SA, sk->m, sk->d, sk->dp, lambda, 2, 0.5, sk->seed ^ 0x4855544348ull, &sd, s);
+    if (rc) return rc;
+    const double cap = 0.95 * (double)sk->m;
+    if (!(sd > 0.0)) sd = 1.0;
+    if (sd > cap) sd = cap;
+    sk->last_sd = sd;
+  }
   // Corollary 3: β = sd/m, α = (1 − β)².
-  const double beta = opts->sd / (double)sk->m;
+  const double beta = sd / (double)sk->m;
   const double alpha = (1.0 - beta) * (1.0 - beta);
+  const size_t xbytes = (refined ? sizeof(double) : sizeof(float)) * (size_t)d;
 
   ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol);
   MIHS_CHECK_LAUNCH();
@@ -515,9 +589,10 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, do
     MIHS_CHECK_LAUNCH();
     count_launch();
   } else {
-    MIHS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)d, s));
+    MIHS_CUDA_TRY(cudaMemsetAsync(xv, 0, xbytes, s));
   }
-  MIHS_CUDA_TRY(cudaMemcpyAsync(sk->x_prev, x, sizeof(float) * (size_t)d, cudaMemcpyDeviceToDevice, s));
+  MIHS_CUDA_TRY(cudaMemcpyAsync(refined ? (void*)sk->x_prev64 : (void*)sk->x_prev, xv, xbytes,
+                                cudaMemcpyDeviceToDevice, s));
 
   AabLaunch a = {};
   a.SA = sk->SA;
@@ -528,25 +603,35 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, do
   a.lambda = (float)lambda;
   a.eps = (float)opts->eps_sub;
   a.max_passes = cap_passes(sk->m, d, opts->max_inner);
-  a.alpha = (float)alpha;
-  a.beta = (float)beta;
-  a.x = x;
-  a.x_prev = sk->x_prev;
+  if (refined) {
+    a.x64 = static_cast<double*>(xv);
+    a.x_prev64 = sk->x_prev64;
+    a.alpha64 = alpha;
+    a.beta64 = beta;
+  } else {
+    a.alpha = (float)alpha;
+    a.beta = (float)beta;
+    a.x = static_cast<float*>(xv);
+    a.x_prev = sk->x_prev;
+  }
   a.ctl = sk->ctl;
   a.hist = sk->hist;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
-  const mihs_sketch_s::Key key = {A, lda, b, x, (float)lambda, a.alpha, a.beta, a.eps, a.max_passes};
+  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes};
   bool graph_ran = false;
-  if (!timing_on() && !sk->graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
-    if (!(sk->exec && sk->key == key)) {
-      if (build_graph(sk, key, a) != MIHS_OK) {
-        drop_graph(sk);
-        sk->graph_failed = true;  // keep the message; use host-driven steps from now on
+  bool& failed = refined ? sk->graph_dd_failed : sk->graph_failed;
+  cudaGraphExec_t& exec = refined ? sk->exec_dd : sk->exec;
+  const mihs_sketch_s::Key& cached = refined ? sk->key_dd : sk->key;
+  if (!timing_on() && !failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
+    if (!(exec && cached == key)) {
+      if (build_graph(sk, key, a, refined) != MIHS_OK) {
+        if (refined) drop_graph_dd(sk); else drop_graph(sk);
+        failed = true;  // keep the message; use host-driven steps from now on
         cudaGetLastError();
       }
     }
-    if (sk->exec) {
-      MIHS_CUDA_TRY(cudaGraphLaunch(sk->exec, s));
+    if (exec) {
+      MIHS_CUDA_TRY(cudaGraphLaunch(exec, s));
       graph_ran = true;
     }
   }
@@ -555,11 +640,7 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, do
     // fired (ctl->done).  With per-kernel timing on, the flag is read back
     // after every step so that only working launches are timed.
     for (int it = 0; it <= opts->max_outer; ++it) {
-      rc = launch_apass_partial(A, n, d, lda, b, x, sk->partials, sk->ctl, s);
-      if (rc) return rc;
-      rc = launch_apass_finalize(sk->partials, sk->P, d, x, (float)lambda, sk->g, sk->ctl, s);
-      if (rc) return rc;
-      rc = launch_aab(a, s);
+      rc = launch_step(sk, key, a, refined, s);
       if (rc) return rc;
       if (timing_on()) {
         MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ctl_host, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
@@ -578,6 +659,34 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, do
   info->status = c.done ? c.status : MIHS_NOT_CONVERGED;
   if (graph_ran) count_launch(3ull * (uint64_t)(c.outer + 1));
   return info->status;
+}
+
+int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
+               const mihs_opts* opts, float* x, mihs_info* info, void* stream) {
+  return solve_impl(sk, A, lda, b, lambda, opts, x, false, info, stream);
+}
+
+int mihs_solve_refined(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
+                       const mihs_opts* opts, double* x, mihs_info* info, void* stream) {
+  return solve_impl(sk, A, lda, b, lambda, opts, x, true, info, stream);
+}
+
+int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda, const float* b,
+                          const double* x, double lambda, double* g, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_gradient_refined");
+  if (rc) return rc;
+  MIHS_ARG(b != nullptr && x != nullptr && g != nullptr, "mihs_gradient_refined: null vector");
+  MIHS_ARG(lambda >= 0.0 && std::isfinite(lambda), "mihs_gradient_refined: lambda must be finite, >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = apass_dd_num_partials(n, d);
+  StreamScratch scratch;
+  rc = scratch.alloc(sizeof(float2) * (size_t)P * apass_dpad(d), s);
+  if (rc) return rc;
+  float2* part = static_cast<float2*>(scratch.p);
+  rc = launch_apass_dd(A, n, d, lda, b, x, part, nullptr, s);
+  if (rc) return rc;
+  return launch_apass_dd_finalize(part, P, d, x, lambda, g, nullptr, nullptr, s);
 }
 
 }  // extern "C"

@@ -103,7 +103,7 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   return make_float2(r * c, r * s);
 }
 
-enum : uint32_t { kTagGaussian = 0, kTagCountSketch = 1, kTagSrhtSigns = 2, kTagSrhtRows = 3 };
+enum : uint32_t { kTagGaussian = 0, kTagCountSketch = 1, kTagSrhtSigns = 2, kTagSrhtRows = 3, kTagHutchinson = 4 };
 
 }  // namespace mihs
 

@@ -27,6 +27,16 @@ int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const float* x, float lambda, float* g,
                           const SolveCtl* ctl, cudaStream_t s);
 
+// ---- compensated gradient (apass_dd.cu) -------------------------------------
+// Same pass with x in fp64 and double-float sums; partials are (hi, lo) pairs.
+int apass_dd_num_partials(int64_t n, int64_t d);
+int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
+                    float2* partials, SolveCtl* ctl, cudaStream_t s);
+// g64[j] = Σ_p (hi + lo) − λ·x[j] in fp64; g32 (optional) its fp32 rounding.
+int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s);
+int apass_dd_device_error(int* code);
+
 // ---- AAb_Solver (aab.cu) --------------------------------------------------
 struct AabLaunch {
   const float* SA;
@@ -41,6 +51,9 @@ struct AabLaunch {
   float alpha, beta;
   float* x;
   float* x_prev;
+  double* x64;         // refinement mode: fp64 iterate (heavy ball in fp64)
+  double* x_prev64;
+  double alpha64, beta64;
   SolveCtl* ctl;       // solve mode (stop test, counters); may be NULL
   float* hist;         // solve mode: ‖g‖ of every gradient step (kHistCap entries); may be NULL
   unsigned long long cond;  // graph conditional handle to clear when the solve stops (0: none)
@@ -63,6 +76,11 @@ int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_
                        uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                 uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+
+// ---- statistical dimension (hutchinson.cu) ----------------------------------
+// Algorithm 4; synchronises `s` and writes the estimate to *sd_out (host).
+int estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lambda, int T, double eps_tr,
+                uint64_t seed, double* sd_out, cudaStream_t s);
 
 // ---- per-kernel event timing (api.cu) -------------------------------------
 enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kNumTimers = 3 };

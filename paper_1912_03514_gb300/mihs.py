@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         "mihs_aab_solve": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
         "mihs_aab_heavy_ball": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _dbl, _dbl,
                                        _vp, _vp, _vp, _vp]),
+        "mihs_estimate_sd": (_int, [_vp, _i64, _i64, _i64, _dbl, _int, _dbl, _u64, ctypes.POINTER(_dbl), _vp]),
         "mihs_sketch": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, ctypes.POINTER(_vp)]),
         "mihs_sketch_info": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
         "mihs_resketch": (_int, [_vp, _vp, _i64, _u64, _vp]),
@@ -77,6 +78,9 @@ def lib() -> ctypes.CDLL:
         "mihs_default_opts": (_Opts, []),
         "mihs_timing": (_int, [_int]),
         "mihs_timing_read": (_int, [_int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+        "mihs_solve_refined": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
+                                      ctypes.POINTER(_Info), _vp]),
+        "mihs_gradient_refined": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
                               ctypes.POINTER(_Info), _vp]),
     }
@@ -168,6 +172,19 @@ def gradient(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
     return g
 
 
+def gradient_refined(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
+                     g: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Compensated g = Aᵀ(b − Ax) − λx with fp64 x and g (A, b fp32)."""
+    pa, n, d, lda = _mat(A, "A")
+    if not (x.is_cuda and x.dtype == torch.float64 and x.numel() == d and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA fp64 vector of length d")
+    if g is None:
+        g = torch.empty(d, dtype=torch.float64, device=A.device)
+    _check(lib().mihs_gradient_refined(pa, n, d, lda, _vec(b, n, "b"), x.data_ptr(), float(lam),
+                                       g.data_ptr(), _stream(stream)))
+    return g
+
+
 def gradient_noalloc(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, lam: float,
                      g: torch.Tensor, stream=None) -> torch.Tensor:
     """g = Aᵀ(b − Ax) − λx through the entry point that allocates nothing (its
@@ -194,6 +211,16 @@ def aab_solve(SA: torch.Tensor, g: torch.Tensor, lam: float, eps_sub: float = 0.
                                 int(max_inner), _vec(delta, d, "delta"), pp or None,
                                 _stream(stream)))
     return delta
+
+
+def estimate_sd(SA: torch.Tensor, lam: float, T: int = 2, eps_tr: float = 0.5, seed: int = 0,
+                stream=None) -> float:
+    """Statistical dimension from SA by Algorithm 4 (Hutchinson)."""
+    ps, m, d, ldsa = _mat(SA, "SA")
+    out = _dbl()
+    _check(lib().mihs_estimate_sd(ps, m, d, ldsa, float(lam), int(T), float(eps_tr), seed & (2**64 - 1),
+                                  ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def aab_heavy_ball(SA: torch.Tensor, g: torch.Tensor, lam: float, eps_sub: float, max_inner: int,
@@ -262,6 +289,30 @@ class Sketch:
         rc = lib().mihs_solve(self._h, pa, lda, _vec(b, n, "b"), float(lam), ctypes.byref(o),
                               _vec(x, d, "x"), ctypes.byref(info) if want_info else None,
                               _stream(stream))
+        _check(rc, allow_not_converged=True)
+        if not want_info:
+            return x, None
+        return x, SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status)
+
+    def solve_refined(self, A: torch.Tensor, b: torch.Tensor, lam: float, sd: float, tol: float = 1e-12,
+                      max_outer: int = 200, eps_sub: float = 0.1, max_inner: int = 0,
+                      x: torch.Tensor | None = None, warm_start: bool = False, want_info: bool = True,
+                      stream=None):
+        """Algorithm 1 with compensated refinement (fp64 x).  Returns (x, SolveInfo)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        if x is None:
+            x = torch.empty(d, dtype=torch.float64, device=A.device)
+        if not (x.is_cuda and x.dtype == torch.float64 and x.numel() == d and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA fp64 vector of length d")
+        o = lib().mihs_default_opts()
+        o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+        o.max_inner, o.sd, o.warm_start = int(max_inner), float(sd), int(bool(warm_start))
+        info = _Info()
+        rc = lib().mihs_solve_refined(self._h, pa, lda, _vec(b, n, "b"), float(lam), ctypes.byref(o),
+                                      x.data_ptr(), ctypes.byref(info) if want_info else None,
+                                      _stream(stream))
         _check(rc, allow_not_converged=True)
         if not want_info:
             return x, None

@@ -32,3 +32,14 @@ def apass_depths(n: int, d: int, num_sms: int = 152):
     rows_per_cta = math.ceil(n / min(num_sms, n))
     depth_acc = math.ceil(rows_per_cta / 8) + 16 + math.ceil(num_sms / 8) + 8 + 1
     return depth_r, depth_acc
+
+
+def gradient_bound_refined(A, b, x, lam, depth_r: int, depth_acc: int):
+    """Componentwise bound on |ĝ − g| for the compensated (double-float)
+    gradient: each double-float sum of k terms errs by ≲ 2k·u² relative to the
+    sum of magnitudes (TwoSum/TwoProduct, Ogita–Rump–Oishi 2005), plus the
+    fp64 reductions and λx (≲ 4·u₆₄)."""
+    Aa = np.abs(np.asarray(A, np.float64))
+    M = Aa.T @ (np.abs(np.asarray(b, np.float64)) + Aa @ np.abs(np.asarray(x, np.float64)))
+    u64 = 2.0 ** -53
+    return (4 * (depth_r + depth_acc) * U32 * U32 + 16 * u64) * M + 4 * u64 * lam * np.abs(np.asarray(x, np.float64))

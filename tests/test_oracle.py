@@ -372,3 +372,67 @@ def test_nominal_sd_close_to_actual():
     p = W.problem_small()
     sd = o.stat_dim_of(p.A.numpy(), p.lam)
     assert abs(sd - 64.0) < 2.0 and abs(p.sd - 64.0) < 1e-9
+
+
+# ---------------------------------------------------------------- Algorithm 4
+def test_hutchinson_probe_is_rademacher():
+    v = o.rademacher_probe(20000, 3, 5)
+    assert set(np.unique(v)) == {-1.0, 1.0}
+    assert abs(v.mean()) < 5 / math.sqrt(v.size)
+    assert not np.array_equal(v, o.rademacher_probe(20000, 4, 5))
+
+
+def test_hutchinson_is_unbiased_for_the_sketched_trace():
+    """With exact inner solves, the mean over many probes approaches
+    d − λ·tr((SAᵀSA+λI)⁻¹), the statistical dimension of SA itself."""
+    rng = np.random.default_rng(2)
+    m, d, lam = 60, 40, 0.05
+    SA = rng.standard_normal((m, d)) * np.logspace(0, -2, d)[None, :]
+    exact = o.stat_dim_of(SA, lam)
+    T = 3000
+    est = o.hutchinson_sd(SA, lam, T, 0.0, seed=9)
+    # per-probe variance of vᵀMv for Rademacher v is 2·Σ_{i≠j} M_ij²
+    M = lam * np.linalg.inv(SA.T @ SA + lam * np.eye(d))
+    var = 2 * (np.sum(M ** 2) - np.sum(np.diag(M) ** 2))
+    assert abs(est - exact) < 5 * math.sqrt(var / T) + 1e-9
+
+
+def test_hutchinson_inexact_overestimates_little():
+    """ε_tr = 0.5 and T = 2 (the paper's setting) land within a few percent
+    of the exact statistical dimension on a sketched problem."""
+    p = W.problem_small()
+    A = p.A.numpy().astype(np.float64)
+    SA = o.sketch_apply(o.GAUSSIAN, A, p.m, 3)
+    exact = o.stat_dim_of(A, p.lam)
+    est = o.hutchinson_sd(SA, p.lam, 2, 0.5, seed=4)
+    assert 0.7 * exact < est < 1.5 * exact
+
+
+# ------------------------------------------------------ extended precision
+def test_extended_gradient_agrees_and_is_more_accurate():
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((300, 20)).astype(np.float32).astype(np.float64)
+    b = rng.standard_normal(300)
+    x = rng.standard_normal(20)
+    ge = o.gradient_extended(A, b, x, 0.3)
+    g = o.gradient(A, b, x, 0.3)
+    assert np.allclose(np.asarray(ge, dtype=np.float64), g, rtol=1e-12, atol=1e-12)
+    # exact rational check on integer data: every operation is exact
+    Ai = rng.integers(-5, 6, (50, 7)).astype(np.float64)
+    bi = rng.integers(-5, 6, 50).astype(np.float64)
+    xi = rng.integers(-5, 6, 7).astype(np.float64)
+    ref = [sum(Ai[i, j] * (bi[i] - sum(Ai[i, k] * xi[k] for k in range(7))) for i in range(50)) - 2 * xi[j]
+           for j in range(7)]
+    assert np.array_equal(np.asarray(o.gradient_extended(Ai, bi, xi, 2.0), dtype=np.float64), np.array(ref))
+
+
+def test_exact_solve_extended_on_ill_conditioned_problem():
+    """κ(H) ≈ 1e6: the extended-precision refinement drives the certified
+    error (‖g‖/λ against ‖x*‖) to ~1e-12, the fp64 one only to ~κ·u₆₄."""
+    p = W.make_problem(4096, 64, W.profile_exponential(64, 8.0), 1e-6, 40.0, seed=3)
+    A = p.A.numpy().astype(np.float64)
+    b = p.b.numpy().astype(np.float64)
+    x = o.exact_solve(A, b, p.lam, refine=3, extended=True)
+    g = np.asarray(o.gradient_extended(A, b, x, p.lam), dtype=np.float64)
+    assert np.linalg.norm(g) / p.lam <= 1e-11 * np.linalg.norm(x)
+    assert o.rel_error(o.svd_solve(A, b, p.lam), x) < 1e-8
