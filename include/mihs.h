@@ -73,8 +73,8 @@ int mihs_device_status(int* code);
 
 /* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
  * the records and starts recording CUDA events on the launching stream around
- * every gradient A-pass kernel (timer 0), AAb_Solver kernel (timer 1) and
- * sketch call (timer 2); while it is on, mihs_solve runs its steps as host-
+ * every gradient A-pass kernel (timer 0), AAb_Solver kernel (timer 1),
+ * sketch call (timer 2) and compensated A-pass kernel (timer 3); while it is on, mihs_solve runs its steps as host-
  * driven launches and reads the stop flag back after each step, so only
  * launches that did work are recorded.  mihs_timing(0) stops recording.
  * mihs_timing_read synchronises on the recorded events and returns the summed
@@ -241,7 +241,8 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
                void* stream);
 
 /* Algorithm 1 with compensated refinement: the same iteration with the
- * iterate x in fp64 and the gradient g = Aᵀ(b − Ax) − λx computed by a
+ * iterate x in fp64.  Steps use the plain fp32 gradient until the relative
+ * residual is below 1e-6, then the gradient g = Aᵀ(b − Ax) − λx computed by a
  * compensated pass over A (double-float sums: TwoProduct/TwoSum in fp32
  * pairs, fp64 partial sums), while SA, AAb_Solver and its stop test stay
  * fp32 (the sketch only preconditions; the fixed point of the iteration is

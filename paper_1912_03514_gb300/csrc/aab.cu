@@ -50,6 +50,7 @@ struct AabParams {
   float* x_prev;
   double* x64;
   double* x_prev64;
+  float* x32_shadow;
   double alpha64, beta64;
   SolveCtl* ctl;
   float* hist;
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
 
   // Solve-mode control block: read everything before the first barrier; only
   // rank 0 writes it, after the last barrier.
-  int done = 0, outer = 0, max_outer = 0, g0known = 0;
-  float tol = 0.f, gnorm0 = 0.f;
+  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1;
+  float tol = 0.f, gnorm0 = 0.f, switch_tol = 0.f;
   if (P.ctl != nullptr) {
     done = P.ctl->done;
     outer = P.ctl->outer;
@@ -178,6 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     g0known = P.ctl->gnorm0_known;
     tol = P.ctl->tol;
     gnorm0 = P.ctl->gnorm0;
+    phase = P.ctl->phase;
+    switch_tol = P.ctl->switch_tol;
   }
   cluster.sync();  // every block is running before any DSMEM access
   if (done) {
@@ -244,6 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const bool bad = !(theta1 <= 3.0e38f);
     const bool conv = tol > 0.f && theta1 <= tol * g0;
     const bool capped = outer >= max_outer;
+    // Refinement solves: from here on the compensated gradient (next step).
+    if (phase == 0 && theta1 <= switch_tol * g0 && rank == 0 && tid == 0) P.ctl->phase = 1;
     if (bad || conv || capped) {
       if (rank == 0 && tid == 0) {
         P.ctl->gnorm = theta1;
@@ -397,8 +402,10 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
       }
       if (P.x64 != nullptr) {
         const double xj = P.x64[j], xp = P.x_prev64[j];
-        P.x64[j] = xj + P.alpha64 * (double)dj + P.beta64 * (xj - xp);
+        const double xn = xj + P.alpha64 * (double)dj + P.beta64 * (xj - xp);
+        P.x64[j] = xn;
         P.x_prev64[j] = xj;
+        if (P.x32_shadow != nullptr) P.x32_shadow[j] = (float)xn;
       }
     }
   }
@@ -540,6 +547,7 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   P.x_prev = a.x_prev;
   P.x64 = a.x64;
   P.x_prev64 = a.x_prev64;
+  P.x32_shadow = a.x32_shadow;
   P.alpha64 = a.alpha64;
   P.beta64 = a.beta64;
   P.ctl = a.ctl;

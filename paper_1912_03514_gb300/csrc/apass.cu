@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
                      const float* __restrict__ b, const float* __restrict__ x,
                      float* __restrict__ partials, int dpad, int rows_per_cta, int stages,
-                     SolveCtl* __restrict__ ctl) {
+                     SolveCtl* __restrict__ ctl, int gate) {
   constexpr int NC = kConsumerWarps, R = NC * RW;
   constexpr bool XS = CH > 8;  // wide rows: keep x in smem instead of registers
-  if (ctl != nullptr && ctl->done) return;  // same value for every block
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;  // uniform
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
@@ -188,8 +188,8 @@ apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
 __global__ void __launch_bounds__(256)
 apass_finalize_kernel(const float* __restrict__ partials, int P, int d, int dpad,
                       const float* __restrict__ x, float lambda, float* __restrict__ g,
-                      const SolveCtl* __restrict__ ctl) {
-  if (ctl != nullptr && ctl->done) return;
+                      const SolveCtl* __restrict__ ctl, int gate) {
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
   __shared__ float red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -239,7 +239,7 @@ int apass_num_partials(int64_t n, int64_t d) {
 }
 
 int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda, const float* b,
-                         const float* x, float* partials, SolveCtl* ctl, cudaStream_t s) {
+                         const float* x, float* partials, SolveCtl* ctl, cudaStream_t s, int gate) {
   const ApassKernel k = pick(d);
   const int P = apass_num_partials(n, d);
   const int64_t dpad = apass_dpad(d);
@@ -254,7 +254,7 @@ int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda, cons
   int n32 = (int)n, d32 = (int)d, dp32 = (int)dpad;
   long long lda64 = lda;
   void* args[] = {(void*)&A, &n32, &d32, &lda64, (void*)&b, (void*)&x,
-                  (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl};
+                  (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl, &gate};
   timing_begin(kTimerApass, s);
   MIHS_CUDA_TRY(cudaLaunchKernel(k.fn, dim3(P), dim3(kThreads), args, smem, s));
   timing_end(kTimerApass, s);
@@ -271,10 +271,10 @@ int apass_device_error(int* code) {
 }
 
 int launch_apass_finalize(const float* partials, int P, int64_t d, const float* x,
-                          float lambda, float* g, const SolveCtl* ctl, cudaStream_t s) {
+                          float lambda, float* g, const SolveCtl* ctl, cudaStream_t s, int gate) {
   const int64_t dpad = apass_dpad(d);
   apass_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)dpad,
-                                                                   x, lambda, g, ctl);
+                                                                   x, lambda, g, ctl, gate);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

@@ -72,10 +72,10 @@ template <int CH>
 __global__ void __launch_bounds__(DdCfg<CH>::kThreads, 1)
 apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const float* __restrict__ b,
                 const double* __restrict__ x, float2* __restrict__ partials, int dpad, int rows_per_cta,
-                int stages, SolveCtl* __restrict__ ctl) {
+                int stages, SolveCtl* __restrict__ ctl, int gate) {
   constexpr int NC = DdCfg<CH>::NC, R = NC;
   constexpr int kThreads = DdCfg<CH>::kThreads;
-  if (ctl != nullptr && ctl->done) return;
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;  // uniform
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
@@ -242,8 +242,8 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
 __global__ void __launch_bounds__(256)
 apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int dpad,
                          const double* __restrict__ x, double lambda, double* __restrict__ g64,
-                         float* __restrict__ g32, const SolveCtl* __restrict__ ctl) {
-  if (ctl != nullptr && ctl->done) return;
+                         float* __restrict__ g32, const SolveCtl* __restrict__ ctl, int gate) {
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -297,7 +297,7 @@ int apass_dd_num_partials(int64_t n, int64_t d) {
 }
 
 int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
-                    float2* partials, SolveCtl* ctl, cudaStream_t s) {
+                    float2* partials, SolveCtl* ctl, cudaStream_t s, int gate) {
   const DdKernel k = pick_dd(d);
   const int P = apass_dd_num_partials(n, d);
   const int64_t dpad = apass_dpad(d);
@@ -314,18 +314,18 @@ int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const flo
   int n32 = (int)n, d32 = (int)d, dp32 = (int)dpad;
   long long lda64 = lda;
   void* args[] = {(void*)&A, &n32, &d32, &lda64, (void*)&b, (void*)&x,
-                  (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl};
-  timing_begin(kTimerApass, s);
+                  (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl, &gate};
+  timing_begin(kTimerApassDd, s);
   MIHS_CUDA_TRY(cudaLaunchKernel(k.fn, dim3(P), dim3((k.nc + 1) * 32), args, smem, s));
-  timing_end(kTimerApass, s);
+  timing_end(kTimerApassDd, s);
   count_launch();
   return MIHS_OK;
 }
 
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
-                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s) {
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate) {
   apass_dd_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)apass_dpad(d), x,
-                                                                     lambda, g64, g32, ctl);
+                                                                     lambda, g64, g32, ctl, gate);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

@@ -45,7 +45,7 @@ struct Timing {
   std::mutex mu;
   bool on = false;
   std::vector<cudaEvent_t> ev[kNumTimers];  // (start, stop) pairs
-  size_t used[kNumTimers] = {0, 0, 0};
+  size_t used[kNumTimers] = {};
 };
 Timing& timing_state() {
   static Timing* t = new Timing();  // never destroyed: events outlive static teardown
@@ -81,12 +81,19 @@ void timing_end(int which, cudaStream_t s) {
 
 namespace {
 
-__global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol) {
+__global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int phase, float switch_tol) {
   SolveCtl c = {};
   c.max_outer = max_outer;
   c.tol = tol;
   c.status = MIHS_OK;
+  c.phase = phase;
+  c.switch_tol = switch_tol;
   *ctl = c;
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) b[j] = (float)a[j];
 }
 
 // ‖g‖ for the warm-start reference norm ‖Aᵀb‖ (one block, fixed order).
@@ -137,6 +144,7 @@ struct mihs_sketch_s {
   // partials of the compensated A-pass and the fp64 previous iterate.
   float2* dd_partials = nullptr;
   double* x_prev64 = nullptr;
+  float* x32_shadow = nullptr;
   int P_dd = 0;
   cudaGraphExec_t exec_dd = nullptr;
   cudaGraph_t graph_dd = nullptr;
@@ -180,14 +188,24 @@ void drop_graph_dd(mihs_sketch_s* sk) {
 
 // One outer step of Algorithm 1 (gradient, partial-sum reduce, AAb_Solver +
 // heavy ball), plain fp32 or compensated (refinement).
+// In a refinement solve both gradient variants are launched, each gated on
+// ctl->phase (plain fp32 while it is 0, compensated once it is 1), unless
+// `phase` names the one the host knows to be current.
 int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& a, bool refined,
-                cudaStream_t s) {
-  int rc;
+                cudaStream_t s, int phase = -1) {
+  int rc = MIHS_OK;
   if (refined) {
-    rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const double*>(key.x),
-                         sk->dd_partials, sk->ctl, s);
-    if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, static_cast<const double*>(key.x),
-                                           key.lam, nullptr, sk->g, sk->ctl, s);
+    if (phase != 1) {
+      rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, sk->x32_shadow, sk->partials, sk->ctl, s, 0);
+      if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, sk->x32_shadow, (float)key.lam, sk->g,
+                                          sk->ctl, s, 0);
+    }
+    if (!rc && phase != 0) {
+      rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const double*>(key.x),
+                           sk->dd_partials, sk->ctl, s, 1);
+      if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, static_cast<const double*>(key.x),
+                                             key.lam, nullptr, sk->g, sk->ctl, s, 1);
+    }
   } else {
     rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const float*>(key.x),
                               sk->partials, sk->ctl, s);
@@ -550,7 +568,8 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   if (refined && sk->dd_partials == nullptr) {
     sk->P_dd = apass_dd_num_partials(n, d);
     char* p = nullptr;
-    const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + sizeof(double) * (size_t)sk->dp;
+    const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + sizeof(double) * (size_t)sk->dp +
+                         sizeof(float) * (size_t)sk->dp;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       set_error("mihs_solve_refined: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -558,6 +577,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
     }
     sk->dd_partials = reinterpret_cast<float2*>(p);
     sk->x_prev64 = reinterpret_cast<double*>(p + sizeof(float2) * (size_t)sk->P_dd * sk->dp);
+    sk->x32_shadow = reinterpret_cast<float*>(sk->x_prev64 + sk->dp);
   }
   // sd ≤ 0: estimate it from SA (Algorithm 4 with the paper's T = 2,
   // ε_tr = 0.5); an over-estimate only slows the rate (Remark after
@@ -576,7 +596,11 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   const double alpha = (1.0 - beta) * (1.0 - beta);
   const size_t xbytes = (refined ? sizeof(double) : sizeof(float)) * (size_t)d;
 
-  ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol);
+  // Refinement solves start with plain fp32 gradients and switch to the
+  // compensated pass once the relative residual is below 1e-6 (well above the
+  // fp32 floor); plain solves never switch.
+  const float switch_tol = refined ? 1e-6f : 0.f;
+  ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol, refined ? 0 : 1, switch_tol);
   MIHS_CHECK_LAUNCH();
   count_launch();
   if (opts->warm_start) {
@@ -593,6 +617,12 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   }
   MIHS_CUDA_TRY(cudaMemcpyAsync(refined ? (void*)sk->x_prev64 : (void*)sk->x_prev, xv, xbytes,
                                 cudaMemcpyDeviceToDevice, s));
+  if (refined) {
+    f64_to_f32_kernel<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(static_cast<const double*>(xv), sk->x32_shadow,
+                                                                 (int)d);
+    MIHS_CHECK_LAUNCH();
+    count_launch();
+  }
 
   AabLaunch a = {};
   a.SA = sk->SA;
@@ -606,6 +636,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   if (refined) {
     a.x64 = static_cast<double*>(xv);
     a.x_prev64 = sk->x_prev64;
+    a.x32_shadow = sk->x32_shadow;
     a.alpha64 = alpha;
     a.beta64 = beta;
   } else {
@@ -637,15 +668,18 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   }
   if (!graph_ran) {
     // Host-driven steps; the kernels return at once after the stop test has
-    // fired (ctl->done).  With per-kernel timing on, the flag is read back
-    // after every step so that only working launches are timed.
+    // fired (ctl->done).  With per-kernel timing on, the control block is
+    // read back after every step so that only working launches are timed.
+    const bool poll = timing_on();
+    int phase = poll && refined ? 0 : -1;
     for (int it = 0; it <= opts->max_outer; ++it) {
-      rc = launch_step(sk, key, a, refined, s);
+      rc = launch_step(sk, key, a, refined, s, phase);
       if (rc) return rc;
-      if (timing_on()) {
+      if (poll) {
         MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ctl_host, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
         MIHS_CUDA_TRY(cudaStreamSynchronize(s));
         if (sk->ctl_host->done) break;
+        if (refined) phase = sk->ctl_host->phase;
       }
     }
   }
@@ -657,7 +691,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   info->inner_iters_total = c.inner_total;
   info->rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
   info->status = c.done ? c.status : MIHS_NOT_CONVERGED;
-  if (graph_ran) count_launch(3ull * (uint64_t)(c.outer + 1));
+  if (graph_ran) count_launch((refined ? 5ull : 3ull) * (uint64_t)(c.outer + 1));
   return info->status;
 }
 

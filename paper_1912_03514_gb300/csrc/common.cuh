@@ -64,7 +64,9 @@ struct SolveCtl {
   float tol;         // stop when ‖g‖ ≤ tol·‖Aᵀb‖
   float gnorm0;      // ‖Aᵀb‖
   float gnorm;       // ‖g‖ of the current x
-  float pad[3];
+  int phase;         // refinement solves: 0 = plain fp32 gradient, 1 = compensated
+  float switch_tol;  // switch to phase 1 once ‖g‖ ≤ switch_tol·‖Aᵀb‖
+  float pad;
 };
 
 // ------------------------------------------------------------- device side

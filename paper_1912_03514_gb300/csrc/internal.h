@@ -17,24 +17,25 @@ inline int64_t apass_dpad(int64_t d) { return round_up(d, 4); }
 // NULL (taken as 0).  Skips all work when ctl != NULL and ctl->done.
 // A bounded wait that runs out sets ctl->status = MIHS_ERR_TIMEOUT and
 // ctl->done (when ctl != NULL) and the library-wide device error word.
+// gate ≥ 0: run only while ctl->phase == gate (refinement solves).
 int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda,
                          const float* b, const float* x, float* partials,
-                         SolveCtl* ctl, cudaStream_t s);
+                         SolveCtl* ctl, cudaStream_t s, int gate = -1);
 // Reads and clears the library-wide device error word (synchronises).
 int apass_device_error(int* code);
 // g[j] = Σ_p partials[p][j] − λ·x[j] in a fixed order.
 int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const float* x, float lambda, float* g,
-                          const SolveCtl* ctl, cudaStream_t s);
+                          const SolveCtl* ctl, cudaStream_t s, int gate = -1);
 
 // ---- compensated gradient (apass_dd.cu) -------------------------------------
 // Same pass with x in fp64 and double-float sums; partials are (hi, lo) pairs.
 int apass_dd_num_partials(int64_t n, int64_t d);
 int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
-                    float2* partials, SolveCtl* ctl, cudaStream_t s);
+                    float2* partials, SolveCtl* ctl, cudaStream_t s, int gate = -1);
 // g64[j] = Σ_p (hi + lo) − λ·x[j] in fp64; g32 (optional) its fp32 rounding.
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
-                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s);
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate = -1);
 int apass_dd_device_error(int* code);
 
 // ---- AAb_Solver (aab.cu) --------------------------------------------------
@@ -53,6 +54,7 @@ struct AabLaunch {
   float* x_prev;
   double* x64;         // refinement mode: fp64 iterate (heavy ball in fp64)
   double* x_prev64;
+  float* x32_shadow;   // refinement mode: fp32 copy of the fp64 iterate (plain phase)
   double alpha64, beta64;
   SolveCtl* ctl;       // solve mode (stop test, counters); may be NULL
   float* hist;         // solve mode: ‖g‖ of every gradient step (kHistCap entries); may be NULL
@@ -83,7 +85,7 @@ int estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lamb
                 uint64_t seed, double* sd_out, cudaStream_t s);
 
 // ---- per-kernel event timing (api.cu) -------------------------------------
-enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kNumTimers = 3 };
+enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kNumTimers = 4 };
 bool timing_on();
 void timing_begin(int which, cudaStream_t s);
 void timing_end(int which, cudaStream_t s);

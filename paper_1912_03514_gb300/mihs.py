@@ -132,7 +132,7 @@ def launch_count() -> int:
     return int(lib().mihs_launch_count())
 
 
-TIMER_APASS, TIMER_AAB, TIMER_SKETCH = 0, 1, 2
+TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD = 0, 1, 2, 3
 
 
 def timing(on: bool) -> None:

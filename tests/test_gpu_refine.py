@@ -51,6 +51,34 @@ def test_refined_solve_reaches_1e10_on_small_problem(family):
     assert o.rel_error(x.cpu().numpy(), xs) <= 1e-10
 
 
+def test_refined_solve_switches_phase_once():
+    """Refinement solves take plain fp32 gradients until the relative residual
+    is below 1e-6, then compensated ones.  The host-driven loop (per-kernel
+    timing on) launches only the current variant; the graph launches both,
+    gated on the device: the two must produce the same bytes."""
+    p = W.problem_small()
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    with mihs.Sketch(A, "gaussian", p.m, seed=12) as sk:
+        xg, ig = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12, max_outer=200)
+        mihs.timing(True)
+        try:
+            xt, it = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12, max_outer=200)
+            _, n_plain = mihs.timing_read(mihs.TIMER_APASS)
+            _, n_dd = mihs.timing_read(mihs.TIMER_APASS_DD)
+        finally:
+            mihs.timing(False)
+        hist = np.asarray(sk.history(), dtype=np.float64)
+    assert ig.converged and it.converged
+    assert torch.equal(xg, xt)
+    assert ig.outer_iters == it.outer_iters
+    assert n_plain >= 1 and n_dd >= 1
+    assert n_plain + n_dd == it.outer_iters + 1  # one gradient per step plus the final stop test
+    # the switch came at the first step whose plain residual was ≤ 1e-6·‖Aᵀb‖
+    k = n_plain - 1
+    assert hist[k] <= 1e-6 * hist[0] * (1 + 1e-6)
+    assert k == 0 or hist[k - 1] > 1e-6 * hist[0] * (1 - 1e-6)
+
+
 def test_refined_solve_ill_conditioned():
     """κ(H) ≈ 1e6 (eight decades of singular values, λ = 1e-6), the shape of
     the mixed-precision workload at a size the oracle refines quickly: the
