@@ -26,6 +26,9 @@ Contents and the passage each follows:
   theorem1_params ...... β*, α*, rate of Theorem 1.
   mihs ................. Algorithm 1 (M-IHS for n ≥ d).
   hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
+  ridge_backward ....... gradients of x*(A, b, λ) through the normal equations
+                          of Section 1 (not in the paper: the adjoint of the
+                          linear solve; parity pinned by central differences).
   heavy_ball ........... x⁺ = x + αΔ + β(x − x⁻) (Eq. mihs1).
   characteristic_rate .. roots of u² − (1+β−αμ)u + β (proof of Theorem 1).
 
@@ -288,6 +291,26 @@ def stat_dim(sigma, lam):
 
 def stat_dim_of(A, lam):
     return stat_dim(np.linalg.svd(np.asarray(A, dtype=np.float64), compute_uv=False), lam)
+
+
+def ridge_backward(A, b, lam, gbar, x=None):
+    """Gradients of L = ḡᵀx* with respect to A, b and λ, where
+    H x* = Aᵀb, H = AᵀA + λI.  Differentiating the normal equations:
+    H dx = dAᵀ(b − Ax*) − AᵀdA x* + Aᵀdb − dλ x*, so with the adjoint
+    v = H⁻¹ḡ and r = b − Ax*:
+        ∂L/∂A = r vᵀ − (Av) x*ᵀ,  ∂L/∂b = Av,  ∂L/∂λ = −x*ᵀv.
+    Returns (x, v, dA, db, dlam) in fp64; x defaults to the exact solution."""
+    A64 = np.asarray(A, dtype=np.float64)
+    b64 = np.asarray(b, dtype=np.float64)
+    H = A64.T @ A64 + lam * np.eye(A64.shape[1])
+    if x is None:
+        x = np.linalg.solve(H, A64.T @ b64)
+    x = np.asarray(x, dtype=np.float64)
+    v = np.linalg.solve(H, np.asarray(gbar, dtype=np.float64))
+    r = b64 - A64 @ x
+    Av = A64 @ v
+    dA = np.outer(r, v) - np.outer(Av, x)
+    return x, v, dA, Av, float(-(x @ v))
 
 
 def certify(A, b, x, lam):

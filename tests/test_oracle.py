@@ -436,3 +436,56 @@ def test_exact_solve_extended_on_ill_conditioned_problem():
     g = np.asarray(o.gradient_extended(A, b, x, p.lam), dtype=np.float64)
     assert np.linalg.norm(g) / p.lam <= 1e-11 * np.linalg.norm(x)
     assert o.rel_error(o.svd_solve(A, b, p.lam), x) < 1e-8
+
+
+# ------------------------------------------------------ gradients of the solve
+def _ridge_loss(A, b, lam, w):
+    """L = wᵀ x*(A, b, λ) through LAPACK's general solver (not the oracle)."""
+    return float(w @ scipy.linalg.solve(A.T @ A + lam * np.eye(A.shape[1]), A.T @ b))
+
+
+def test_ridge_backward_matches_central_differences():
+    """Every entry of ∂L/∂A, ∂L/∂b and ∂L/∂λ against fp64 central differences
+    (truncation O(h²), rounding O(u/h)): a dropped term of the adjoint
+    formula, a sign or a transposed outer product fails by orders."""
+    rng = np.random.default_rng(5)
+    n, d, lam = 9, 4, 0.37
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    w = rng.standard_normal(d)
+    _, _, dA, db, dlam = o.ridge_backward(A, b, lam, w)
+    h = 1e-5
+    fd = np.zeros_like(A)
+    for i in range(n):
+        for j in range(d):
+            Ap, Am = A.copy(), A.copy()
+            Ap[i, j] += h
+            Am[i, j] -= h
+            fd[i, j] = (_ridge_loss(Ap, b, lam, w) - _ridge_loss(Am, b, lam, w)) / (2 * h)
+    assert np.max(np.abs(fd - dA)) <= 1e-7 * max(1.0, np.max(np.abs(dA)))
+    fdb = np.array([(_ridge_loss(A, b + h * e, lam, w) - _ridge_loss(A, b - h * e, lam, w)) / (2 * h)
+                    for e in np.eye(n)])
+    assert np.max(np.abs(fdb - db)) <= 1e-7 * max(1.0, np.max(np.abs(db)))
+    fdl = (_ridge_loss(A, b, lam + h, w) - _ridge_loss(A, b, lam - h, w)) / (2 * h)
+    assert abs(fdl - dlam) <= 1e-7 * max(1.0, abs(dlam))
+
+
+def test_ridge_backward_orthonormal_columns_closed_form():
+    """AᵀA = I ⇒ x* = Aᵀb/(1+λ), so for L = wᵀx*: ∂L/∂b = A w/(1+λ) and
+    ∂L/∂λ = −wᵀAᵀb/(1+λ)²; along A(t) = (1+t)Q the chain rule gives
+    dL/dt = Σ_ij (∂L/∂A)_ij Q_ij."""
+    rng = np.random.default_rng(6)
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 6)))
+    b = rng.standard_normal(20)
+    w = rng.standard_normal(6)
+    lam = 0.8
+    x, v, dA, db, dlam = o.ridge_backward(Q, b, lam, w)
+    np.testing.assert_allclose(x, Q.T @ b / (1 + lam), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(db, Q @ w / (1 + lam), rtol=1e-12, atol=1e-14)
+    assert abs(dlam - (-(w @ (Q.T @ b)) / (1 + lam) ** 2)) <= 1e-12
+    # x*((1+t)Q) = (1+t)Qᵀb/((1+t)² + λ) in closed form
+    def L(t):
+        return (1 + t) * (w @ (Q.T @ b)) / ((1 + t) ** 2 + lam)
+    t = 1e-6
+    fd = (L(t) - L(-t)) / (2 * t)
+    assert abs(fd - np.sum(dA * Q)) <= 1e-8
