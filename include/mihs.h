@@ -263,6 +263,46 @@ int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda,
                           const float* b, const double* x, double lambda,
                           double* g, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Differentiation of the solution x(A, b, λ) = (AᵀA + λI)⁻¹Aᵀb.  The paper
+ * does not differentiate the solve; these follow from differentiating the
+ * normal equations (AᵀA + λI)x = Aᵀb of the ridge problem of Section 1:
+ * with the adjoint v = (AᵀA + λI)⁻¹ḡ of an upstream gradient ḡ = ∂L/∂x and
+ * the residual r = b − Ax,
+ *   ∂L/∂A = r vᵀ − (Av) xᵀ,   ∂L/∂b = Av,   ∂L/∂λ = −xᵀv.
+ * ---------------------------------------------------------------------- */
+
+/* The gradients above for a given v, in one pass over A (reads A, writes dA).
+ *   A, b   as in mihs_solve (n×d, leading dimension lda; b n).
+ *   x, v   d-vectors (the solution and the adjoint).
+ *   dA     optional n×d output, leading dimension ldda ≥ d.
+ *   db     optional n-vector output.
+ *   dlambda optional DEVICE double: −xᵀv accumulated in fp64.
+ * b may be NULL only when dA is (then r is not needed).  All device memory,
+ * enqueued on `stream`, no synchronisation, no allocation.
+ * Errors: INVALID_ARG, CUDA. */
+int mihs_backward_grads(const float* A, int64_t n, int64_t d, int64_t lda,
+                        const float* b, const float* x, const float* v,
+                        float* dA, int64_t ldda, float* db, double* dlambda,
+                        void* stream);
+
+/* Backward of mihs_solve: the adjoint system (AᵀA + λI)v = ḡ is solved by
+ * Algorithm 1 with the handle's SA (the Hessian is symmetric, so the sketch
+ * of the forward solve preconditions it as well; the stop test is
+ * ‖ḡ − (AᵀA + λI)v‖ ≤ tol·‖ḡ‖), then mihs_backward_grads runs.
+ *   gx     d-vector ḡ.
+ *   v      d-vector output (the adjoint; its input value is the starting
+ *          point when opts->warm_start, else ignored).
+ *   other arguments as in mihs_solve and mihs_backward_grads.
+ * The adjoint solve has its own cached graph in the handle, so forward and
+ * backward solves that alternate do not rebuild each other's graphs.
+ * Returns like mihs_solve: with info non-NULL the status of the adjoint
+ * solve (the gradients are written in every case). */
+int mihs_backward(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
+                  double lambda, const float* x, const float* gx,
+                  const mihs_opts* opts, float* v, float* dA, int64_t ldda,
+                  float* db, double* dlambda, mihs_info* info, void* stream);
+
 /* Trace of the last solve on this handle: the relative residual
  * ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step (i = 0, 1, …, at most 1024 entries)
  * into the HOST array host_out[0..cap), the number written in *count.

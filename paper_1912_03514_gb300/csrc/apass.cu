@@ -112,7 +112,7 @@ apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
     const long long rw0 = r0 + (long long)it * R + (long long)warp * RW;
     float bv[RW];
 #pragma unroll
-    for (int k = 0; k < RW; ++k) bv[k] = rw0 + k < r1 ? __ldg(b + rw0 + k) : 0.f;
+    for (int k = 0; k < RW; ++k) bv[k] = (b != nullptr && rw0 + k < r1) ? __ldg(b + rw0 + k) : 0.f;
     if (!mbar_wait(&full[s], ph, kWaitLimitNs)) {
       atomicExch(&g_apass_error, MIHS_ERR_TIMEOUT);
       break;
@@ -187,8 +187,8 @@ apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
 // g[j] = Σ_p partials[p][j] − λ x[j]; 32 columns × 8 partial groups per block.
 __global__ void __launch_bounds__(256)
 apass_finalize_kernel(const float* __restrict__ partials, int P, int d, int dpad,
-                      const float* __restrict__ x, float lambda, float* __restrict__ g,
-                      const SolveCtl* __restrict__ ctl, int gate) {
+                      const float* __restrict__ x, float lambda, const float* __restrict__ rhs,
+                      float* __restrict__ g, const SolveCtl* __restrict__ ctl, int gate) {
   if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
   __shared__ float red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -203,6 +203,7 @@ apass_finalize_kernel(const float* __restrict__ partials, int P, int d, int dpad
     float t = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += red[k][lane];
+    if (rhs != nullptr) t += rhs[j];
     g[j] = t - (x != nullptr ? lambda * x[j] : 0.f);
   }
 }
@@ -271,10 +272,11 @@ int apass_device_error(int* code) {
 }
 
 int launch_apass_finalize(const float* partials, int P, int64_t d, const float* x,
-                          float lambda, float* g, const SolveCtl* ctl, cudaStream_t s, int gate) {
+                          float lambda, float* g, const SolveCtl* ctl, cudaStream_t s, int gate,
+                          const float* rhs) {
   const int64_t dpad = apass_dpad(d);
   apass_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)dpad,
-                                                                   x, lambda, g, ctl, gate);
+                                                                   x, lambda, rhs, g, ctl, gate);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

@@ -146,44 +146,41 @@ struct mihs_sketch_s {
   double* x_prev64 = nullptr;
   float* x32_shadow = nullptr;
   int P_dd = 0;
-  cudaGraphExec_t exec_dd = nullptr;
-  cudaGraph_t graph_dd = nullptr;
-  bool graph_dd_failed = false;
   double last_sd = 0; // sd estimated by the last solve that was given sd ≤ 0
   SolveCtl* ctl;
   SolveCtl* ctl_host; // pinned
   // Device-side outer loop: a CUDA graph holding one conditional WHILE node
   // whose body is (A-pass, partial-sum reduce, AAb + heavy ball); the AAb
-  // kernel clears the condition when the stop test fires.  Rebuilt when the
+  // kernel clears the condition when the stop test fires.  One graph per
+  // kind of solve (plain, refinement, adjoint), each rebuilt when that
   // solve's pointers or scalars change.
   cudaStream_t cap = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  bool graph_failed = false;
   struct Key {
     const float* A; int64_t lda; const float* b; void* x;
     double lam, alpha, beta; float eps; int max_passes;
+    const float* rhs;  // adjoint solves: g = rhs − AᵀAx − λx (b null)
     bool operator==(const Key& o) const {
-      return A == o.A && lda == o.lda && b == o.b && x == o.x && lam == o.lam &&
+      return A == o.A && lda == o.lda && b == o.b && x == o.x && rhs == o.rhs && lam == o.lam &&
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
-  } key = {}, key_dd = {};
+  };
+  struct GraphSlot {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Key key = {};
+    bool failed = false;  // capture failed once: host-driven steps from then on
+  } slots[3];
 };
+
+enum SolveKind { kSolvePlain = 0, kSolveRefined = 1, kSolveAdjoint = 2 };
 
 namespace {
 
-void drop_graph(mihs_sketch_s* sk) {
-  if (sk->exec) cudaGraphExecDestroy(sk->exec);
-  if (sk->graph) cudaGraphDestroy(sk->graph);
-  sk->exec = nullptr;
-  sk->graph = nullptr;
-}
-
-void drop_graph_dd(mihs_sketch_s* sk) {
-  if (sk->exec_dd) cudaGraphExecDestroy(sk->exec_dd);
-  if (sk->graph_dd) cudaGraphDestroy(sk->graph_dd);
-  sk->exec_dd = nullptr;
-  sk->graph_dd = nullptr;
+void drop_graph(mihs_sketch_s::GraphSlot& gs) {
+  if (gs.exec) cudaGraphExecDestroy(gs.exec);
+  if (gs.graph) cudaGraphDestroy(gs.graph);
+  gs.exec = nullptr;
+  gs.graph = nullptr;
 }
 
 // One outer step of Algorithm 1 (gradient, partial-sum reduce, AAb_Solver +
@@ -210,7 +207,7 @@ int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
     rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const float*>(key.x),
                               sk->partials, sk->ctl, s);
     if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, static_cast<const float*>(key.x),
-                                        (float)key.lam, sk->g, sk->ctl, s);
+                                        (float)key.lam, sk->g, sk->ctl, s, -1, key.rhs);
   }
   if (!rc) rc = launch_aab(a, s);
   return rc;
@@ -218,10 +215,11 @@ int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
 
 // Captures the loop body into a conditional WHILE node.  Returns MIHS_OK or
 // an error (the caller then falls back to host-driven iterations).
-int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto, bool refined) {
-  cudaGraph_t& graph = refined ? sk->graph_dd : sk->graph;
-  cudaGraphExec_t& exec = refined ? sk->exec_dd : sk->exec;
-  if (refined) drop_graph_dd(sk); else drop_graph(sk);
+int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto, bool refined,
+                mihs_sketch_s::GraphSlot& gs) {
+  cudaGraph_t& graph = gs.graph;
+  cudaGraphExec_t& exec = gs.exec;
+  drop_graph(gs);
   if (!sk->cap) MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&sk->cap, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   MIHS_CUDA_TRY(cudaGraphCreate(&g, 0));
@@ -250,7 +248,7 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
     return MIHS_ERR_CUDA;
   }
   MIHS_CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
-  if (refined) sk->key_dd = key; else sk->key = key;
+  gs.key = key;
   return MIHS_OK;
 }
 
@@ -542,8 +540,7 @@ int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream) {
 int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk == nullptr) return MIHS_OK;
   cudaDeviceSynchronize();
-  drop_graph(sk);
-  drop_graph_dd(sk);
+  for (auto& gs : sk->slots) drop_graph(gs);
   if (sk->cap) cudaStreamDestroy(sk->cap);
   if (sk->dd_partials) cudaFree(sk->dd_partials);
   cudaFreeHost(sk->ctl_host);
@@ -552,13 +549,16 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   return MIHS_OK;
 }
 
+// Algorithm 1 on H x = Aᵀb + rhs (rhs null for the ridge problem itself; b
+// null and rhs = ḡ for the adjoint solve H v = ḡ).
 static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
-                      const mihs_opts* opts, void* xv, bool refined, mihs_info* info, void* stream) {
-  set_error("");
+                      const mihs_opts* opts, void* xv, bool refined, mihs_info* info, void* stream,
+                      const float* rhs = nullptr) {
   MIHS_ARG(sk != nullptr && opts != nullptr, "mihs_solve: null handle or opts");
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve");
   if (rc) return rc;
-  MIHS_ARG(b != nullptr && xv != nullptr, "mihs_solve: null b or x");
+  MIHS_ARG((b != nullptr || rhs != nullptr) && xv != nullptr, "mihs_solve: null b or x");
+  MIHS_ARG(!(refined && rhs != nullptr), "mihs_solve: no right-hand-side offset in refinement solves");
   MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve: lambda must be > 0");
   MIHS_ARG(opts->sd < (double)sk->m, "mihs_solve: sd=%g must be < m=%lld", opts->sd, (long long)sk->m);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
@@ -604,10 +604,10 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   MIHS_CHECK_LAUNCH();
   count_launch();
   if (opts->warm_start) {
-    // ‖Aᵀb‖ = ‖g(0)‖ for the relative residual.
+    // ‖g(0)‖ (= ‖Aᵀb‖ for the ridge problem) for the relative residual.
     rc = launch_apass_partial(A, n, d, lda, b, nullptr, sk->partials, nullptr, s);
     if (rc) return rc;
-    rc = launch_apass_finalize(sk->partials, sk->P, d, nullptr, 0.f, sk->g, nullptr, s);
+    rc = launch_apass_finalize(sk->partials, sk->P, d, nullptr, 0.f, sk->g, nullptr, s, -1, rhs);
     if (rc) return rc;
     ctl_set_gnorm0_kernel<<<1, 256, 0, s>>>(sk->ctl, sk->g, (int)d);
     MIHS_CHECK_LAUNCH();
@@ -648,21 +648,20 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   a.ctl = sk->ctl;
   a.hist = sk->hist;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
-  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes};
+  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs};
   bool graph_ran = false;
-  bool& failed = refined ? sk->graph_dd_failed : sk->graph_failed;
-  cudaGraphExec_t& exec = refined ? sk->exec_dd : sk->exec;
-  const mihs_sketch_s::Key& cached = refined ? sk->key_dd : sk->key;
-  if (!timing_on() && !failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
-    if (!(exec && cached == key)) {
-      if (build_graph(sk, key, a, refined) != MIHS_OK) {
-        if (refined) drop_graph_dd(sk); else drop_graph(sk);
-        failed = true;  // keep the message; use host-driven steps from now on
+  mihs_sketch_s::GraphSlot& gs =
+      sk->slots[refined ? kSolveRefined : (rhs != nullptr ? kSolveAdjoint : kSolvePlain)];
+  if (!timing_on() && !gs.failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
+    if (!(gs.exec && gs.key == key)) {
+      if (build_graph(sk, key, a, refined, gs) != MIHS_OK) {
+        drop_graph(gs);
+        gs.failed = true;  // keep the message; use host-driven steps from now on
         cudaGetLastError();
       }
     }
-    if (exec) {
-      MIHS_CUDA_TRY(cudaGraphLaunch(exec, s));
+    if (gs.exec) {
+      MIHS_CUDA_TRY(cudaGraphLaunch(gs.exec, s));
       graph_ran = true;
     }
   }
@@ -697,12 +696,38 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
 
 int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
                const mihs_opts* opts, float* x, mihs_info* info, void* stream) {
+  set_error("");
   return solve_impl(sk, A, lda, b, lambda, opts, x, false, info, stream);
 }
 
 int mihs_solve_refined(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
                        const mihs_opts* opts, double* x, mihs_info* info, void* stream) {
+  set_error("");
   return solve_impl(sk, A, lda, b, lambda, opts, x, true, info, stream);
+}
+
+int mihs_backward_grads(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const float* x,
+                        const float* v, float* dA, int64_t ldda, float* db, double* dlambda, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_backward_grads");
+  if (rc) return rc;
+  MIHS_ARG(x != nullptr && v != nullptr, "mihs_backward_grads: null x or v");
+  MIHS_ARG(dA == nullptr || (b != nullptr && ldda >= d), "mihs_backward_grads: dA needs b and ldda >= d");
+  return launch_backward_grads(A, n, d, lda, b, x, v, dA, ldda, db, dlambda, static_cast<cudaStream_t>(stream));
+}
+
+int mihs_backward(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda, const float* x,
+                  const float* gx, const mihs_opts* opts, float* v, float* dA, int64_t ldda, float* db,
+                  double* dlambda, mihs_info* info, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr, "mihs_backward: null handle");
+  MIHS_ARG(gx != nullptr && x != nullptr && v != nullptr, "mihs_backward: null gx, x or v");
+  MIHS_ARG(dA == nullptr || (b != nullptr && ldda >= sk->d), "mihs_backward: dA needs b and ldda >= d");
+  const int st = solve_impl(sk, A, lda, nullptr, lambda, opts, v, false, info, stream, gx);
+  if (st < 0) return st;
+  const int rc = launch_backward_grads(A, sk->n, sk->d, lda, b, x, v, dA, ldda, db, dlambda,
+                                       static_cast<cudaStream_t>(stream));
+  return rc ? rc : st;
 }
 
 int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda, const float* b,

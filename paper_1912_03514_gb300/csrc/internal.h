@@ -13,8 +13,8 @@ namespace mihs {
 int apass_num_partials(int64_t n, int64_t d);
 // Row pitch (floats) of the partial buffer.
 inline int64_t apass_dpad(int64_t d) { return round_up(d, 4); }
-// partials[p][j] = Σ_{rows of block p} A[i][j]·(b[i] − A[i]·x).  x may be
-// NULL (taken as 0).  Skips all work when ctl != NULL and ctl->done.
+// partials[p][j] = Σ_{rows of block p} A[i][j]·(b[i] − A[i]·x).  x and b
+// may be NULL (taken as 0).  Skips all work when ctl != NULL and ctl->done.
 // A bounded wait that runs out sets ctl->status = MIHS_ERR_TIMEOUT and
 // ctl->done (when ctl != NULL) and the library-wide device error word.
 // gate ≥ 0: run only while ctl->phase == gate (refinement solves).
@@ -23,10 +23,17 @@ int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda,
                          SolveCtl* ctl, cudaStream_t s, int gate = -1);
 // Reads and clears the library-wide device error word (synchronises).
 int apass_device_error(int* code);
-// g[j] = Σ_p partials[p][j] − λ·x[j] in a fixed order.
+// g[j] = rhs[j] + Σ_p partials[p][j] − λ·x[j] in a fixed order (rhs may be null).
 int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const float* x, float lambda, float* g,
-                          const SolveCtl* ctl, cudaStream_t s, int gate = -1);
+                          const SolveCtl* ctl, cudaStream_t s, int gate = -1,
+                          const float* rhs = nullptr);
+
+// ---- gradients of the solution (backward.cu) ------------------------------
+// dlambda = −xᵀv (fp64); db = Av; dA = r vᵀ − (Av) xᵀ with r = b − Ax.  Any of
+// dA, db, dlambda may be NULL; b may be NULL only when dA is.
+int launch_backward_grads(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const float* x,
+                          const float* v, float* dA, int64_t ldda, float* db, double* dlambda, cudaStream_t s);
 
 // ---- compensated gradient (apass_dd.cu) -------------------------------------
 // Same pass with x in fp64 and double-float sums; partials are (hi, lo) pairs.
@@ -85,7 +92,7 @@ int estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lamb
                 uint64_t seed, double* sd_out, cudaStream_t s);
 
 // ---- per-kernel event timing (api.cu) -------------------------------------
-enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kNumTimers = 4 };
+enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kTimerBackward = 4, kNumTimers = 5 };
 bool timing_on();
 void timing_begin(int which, cudaStream_t s);
 void timing_end(int which, cudaStream_t s);

@@ -83,6 +83,9 @@ def lib() -> ctypes.CDLL:
         "mihs_gradient_refined": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
                               ctypes.POINTER(_Info), _vp]),
+        "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "mihs_backward": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _i64,
+                                 _vp, _vp, ctypes.POINTER(_Info), _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -132,7 +135,7 @@ def launch_count() -> int:
     return int(lib().mihs_launch_count())
 
 
-TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD = 0, 1, 2, 3
+TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD, TIMER_BACKWARD = 0, 1, 2, 3, 4
 
 
 def timing(on: bool) -> None:
@@ -235,6 +238,27 @@ def aab_heavy_ball(SA: torch.Tensor, g: torch.Tensor, lam: float, eps_sub: float
                                      _stream(stream)))
 
 
+def _grad_outputs(n, d, dev, want_dA, want_db, want_dlambda):
+    dA = torch.empty(n, d, dtype=torch.float32, device=dev) if want_dA else None
+    db = torch.empty(n, dtype=torch.float32, device=dev) if want_db else None
+    dl = torch.empty((), dtype=torch.float64, device=dev) if want_dlambda else None
+    return dA, db, dl
+
+
+def backward_grads(A: torch.Tensor, b: torch.Tensor | None, x: torch.Tensor, v: torch.Tensor,
+                   want_dA: bool = True, want_db: bool = True, want_dlambda: bool = True, stream=None):
+    """∂L/∂A = r vᵀ − (Av)xᵀ, ∂L/∂b = Av, ∂L/∂λ = −xᵀv for a given adjoint v
+    (mihs_backward_grads).  Returns (dA, db, dlambda), None where not wanted."""
+    pa, n, d, lda = _mat(A, "A")
+    dA, db, dl = _grad_outputs(n, d, A.device, want_dA, want_db, want_dlambda)
+    _check(lib().mihs_backward_grads(pa, n, d, lda, _vec(b, n, "b") if b is not None else None,
+                                     _vec(x, d, "x"), _vec(v, d, "v"),
+                                     dA.data_ptr() if dA is not None else None, d,
+                                     db.data_ptr() if db is not None else None,
+                                     dl.data_ptr() if dl is not None else None, _stream(stream)))
+    return dA, db, dl
+
+
 @dataclass
 class SolveInfo:
     outer_iters: int
@@ -318,6 +342,33 @@ class Sketch:
             return x, None
         return x, SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status)
 
+    def backward(self, A: torch.Tensor, b: torch.Tensor, lam: float, sd: float, x: torch.Tensor,
+                 gx: torch.Tensor, tol: float = 1e-6, max_outer: int = 100, eps_sub: float = 0.1,
+                 max_inner: int = 0, v: torch.Tensor | None = None, warm_start: bool = False,
+                 want_dA: bool = True, want_db: bool = True, want_dlambda: bool = True,
+                 want_info: bool = True, stream=None):
+        """Adjoint solve (AᵀA + λI)v = ḡ with this sketch, then the gradients
+        (mihs_backward).  Returns (dA, db, dlambda, v, SolveInfo or None)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        if v is None:
+            v = torch.empty(d, dtype=torch.float32, device=A.device)
+        dA, db, dl = _grad_outputs(n, d, A.device, want_dA, want_db, want_dlambda)
+        o = lib().mihs_default_opts()
+        o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+        o.max_inner, o.sd, o.warm_start = int(max_inner), float(sd), int(bool(warm_start))
+        info = _Info()
+        rc = lib().mihs_backward(self._h, pa, lda, _vec(b, n, "b"), float(lam), _vec(x, d, "x"),
+                                 _vec(gx, d, "gx"), ctypes.byref(o), _vec(v, d, "v"),
+                                 dA.data_ptr() if dA is not None else None, d,
+                                 db.data_ptr() if db is not None else None,
+                                 dl.data_ptr() if dl is not None else None,
+                                 ctypes.byref(info) if want_info else None, _stream(stream))
+        _check(rc, allow_not_converged=True)
+        si = SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status) if want_info else None
+        return dA, db, dl, v, si
+
     def history(self):
         """Relative residual ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step of the last solve."""
         buf = (ctypes.c_float * 1024)()
@@ -374,3 +425,46 @@ def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: floa
         out.copy_(x, non_blocking=True)
         return out, info
     return x, info
+
+
+class RidgeSolve(torch.autograd.Function):
+    """x = (AᵀA + λI)⁻¹Aᵀb by M-IHS, differentiable in A, b and λ.
+
+    The forward pass sketches A and runs Algorithm 1; the backward pass runs
+    the adjoint solve with the same sketch and one fused pass over A
+    (mihs_backward).  λ may be a Python number or a 0-d tensor."""
+
+    @staticmethod
+    def forward(ctx, A, b, lam, family, m, sd, seed, tol, max_outer, eps_sub):
+        lam_f = float(lam)
+        sk = Sketch(A, family, m, seed)
+        x, _ = sk.solve(A, b, lam_f, sd, tol=tol, max_outer=max_outer, eps_sub=eps_sub, want_info=False)
+        ctx.sk, ctx.lam, ctx.sd = sk, lam_f, sd
+        ctx.kw = dict(tol=tol, max_outer=max_outer, eps_sub=eps_sub)
+        ctx.lam_like = lam if torch.is_tensor(lam) else None
+        ctx.save_for_backward(A, b, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        A, b, x = ctx.saved_tensors
+        need_A, need_b, need_lam = ctx.needs_input_grad[:3]
+        dA, db, dl, _, _ = ctx.sk.backward(A, b, ctx.lam, ctx.sd, x, gx.contiguous().float(),
+                                           want_dA=need_A, want_db=need_b,
+                                           want_dlambda=need_lam and ctx.lam_like is not None,
+                                           want_info=False, **ctx.kw)
+        if dl is not None:
+            dl = dl.to(dtype=ctx.lam_like.dtype).reshape(ctx.lam_like.shape)
+        return dA, db, dl, None, None, None, None, None, None, None
+
+
+def ridge_solve(A: torch.Tensor, b: torch.Tensor, lam, family="countsketch", m: int | None = None,
+                sd: float = 0.0, seed: int = 0, tol: float = 1e-6, max_outer: int = 100,
+                eps_sub: float = 0.1) -> torch.Tensor:
+    """Differentiable ridge solve (RidgeSolve).  m defaults to min(n, 4·sd)
+    rounded up to a multiple of 4 when sd > 0, else to min(n, d)."""
+    n, d = A.shape
+    if m is None:
+        m = min(n, ((int(4 * sd) + 3) // 4) * 4) if sd > 0 else min(n, d)
+    return RidgeSolve.apply(A, b, lam, family, int(m), float(sd), int(seed), float(tol), int(max_outer),
+                            float(eps_sub))
