@@ -242,7 +242,8 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
 
 /* Algorithm 1 with compensated refinement: the same iteration with the
  * iterate x in fp64.  Steps use the plain fp32 gradient until the relative
- * residual is below 1e-6, then the gradient g = Aᵀ(b − Ax) − λx computed by a
+ * residual is below 1e-6 or has set no new minimum for three steps, then the
+ * gradient g = Aᵀ(b − Ax) − λx computed by a
  * compensated pass over A (double-float sums: TwoProduct/TwoSum in fp32
  * pairs, fp64 partial sums), while SA, AAb_Solver and its stop test stay
  * fp32 (the sketch only preconditions; the fixed point of the iteration is
@@ -302,6 +303,20 @@ int mihs_backward(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
                   double lambda, const float* x, const float* gx,
                   const mihs_opts* opts, float* v, float* dA, int64_t ldda,
                   float* db, double* dlambda, mihs_info* info, void* stream);
+
+/* mihs_backward with the adjoint solved by compensated refinement (as in
+ * mihs_solve_refined): x (the solution, e.g. from mihs_solve_refined) and v
+ * (the adjoint: output, and the starting point when opts->warm_start) are
+ * DEVICE double arrays.  For adjoint right-hand sides whose fp32 residual
+ * floor (≈ κ(H)·u₃₂·‖ḡ‖ at worst) is above the wanted tolerance.  The
+ * gradients stay fp32 and are formed from x and v rounded to fp32.  The
+ * first refined solve on a handle allocates its workspace (cudaMalloc).
+ * Errors and return value as mihs_backward. */
+int mihs_backward_refined(mihs_sketch_t sk, const float* A, int64_t lda,
+                          const float* b, double lambda, const double* x,
+                          const float* gx, const mihs_opts* opts, double* v,
+                          float* dA, int64_t ldda, float* db, double* dlambda,
+                          mihs_info* info, void* stream);
 
 /* Trace of the last solve on this handle: the relative residual
  * ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step (i = 0, 1, …, at most 1024 entries)

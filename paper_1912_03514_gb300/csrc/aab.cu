@@ -247,8 +247,17 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const bool bad = !(theta1 <= 3.0e38f);
     const bool conv = tol > 0.f && theta1 <= tol * g0;
     const bool capped = outer >= max_outer;
-    // Refinement solves: from here on the compensated gradient (next step).
-    if (phase == 0 && theta1 <= switch_tol * g0 && rank == 0 && tid == 0) P.ctl->phase = 1;
+    // Refinement solves: from the next step on the compensated gradient, once
+    // the plain residual is below switch_tol or has set no new minimum for
+    // three steps (it has reached its fp32 floor, which for a generic
+    // right-hand side can lie above switch_tol).
+    if (phase == 0 && rank == 0 && tid == 0) {
+      const float gmin = P.ctl->gmin;
+      const int stall = theta1 < gmin ? 0 : P.ctl->stall + 1;
+      if (theta1 < gmin) P.ctl->gmin = theta1;
+      P.ctl->stall = stall;
+      if (theta1 <= switch_tol * g0 || stall >= 3) P.ctl->phase = 1;
+    }
     if (bad || conv || capped) {
       if (rank == 0 && tid == 0) {
         P.ctl->gnorm = theta1;

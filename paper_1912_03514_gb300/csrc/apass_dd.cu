@@ -140,7 +140,7 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
     const int s = it % stages;
     const uint32_t ph = (uint32_t)(it / stages) & 1u;
     const long long row = r0 + (long long)it * R + warp;
-    const float bi = row < r1 ? __ldg(b + row) : 0.f;
+    const float bi = (b != nullptr && row < r1) ? __ldg(b + row) : 0.f;
     if (!mbar_wait(&full[s], ph, kWaitLimitNs)) {
       atomicExch(&g_apass_dd_error, MIHS_ERR_TIMEOUT);
       break;
@@ -242,7 +242,8 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
 __global__ void __launch_bounds__(256)
 apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int dpad,
                          const double* __restrict__ x, double lambda, double* __restrict__ g64,
-                         float* __restrict__ g32, const SolveCtl* __restrict__ ctl, int gate) {
+                         float* __restrict__ g32, const SolveCtl* __restrict__ ctl, int gate,
+                         const float* __restrict__ rhs) {
   if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -259,6 +260,7 @@ apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int 
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += red[k][lane];
+    if (rhs != nullptr) t += (double)rhs[j];
     if (x != nullptr) t -= lambda * x[j];
     if (g64 != nullptr) g64[j] = t;
     if (g32 != nullptr) g32[j] = (float)t;
@@ -323,9 +325,10 @@ int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const flo
 }
 
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
-                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate) {
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate,
+                             const float* rhs) {
   apass_dd_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)apass_dpad(d), x,
-                                                                     lambda, g64, g32, ctl, gate);
+                                                                     lambda, g64, g32, ctl, gate, rhs);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

@@ -88,6 +88,8 @@ __global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int pha
   c.status = MIHS_OK;
   c.phase = phase;
   c.switch_tol = switch_tol;
+  c.gmin = 3.0e38f;
+  c.stall = 0;
   *ctl = c;
 }
 
@@ -145,6 +147,7 @@ struct mihs_sketch_s {
   float2* dd_partials = nullptr;
   double* x_prev64 = nullptr;
   float* x32_shadow = nullptr;
+  float* bw32 = nullptr;  // 2·dp: fp32 roundings of x and v for refined backward solves
   int P_dd = 0;
   double last_sd = 0; // sd estimated by the last solve that was given sd ≤ 0
   SolveCtl* ctl;
@@ -169,10 +172,8 @@ struct mihs_sketch_s {
     cudaGraphExec_t exec = nullptr;
     Key key = {};
     bool failed = false;  // capture failed once: host-driven steps from then on
-  } slots[3];
+  } slots[4];  // indexed by (refined ? 1 : 0) + (adjoint ? 2 : 0)
 };
-
-enum SolveKind { kSolvePlain = 0, kSolveRefined = 1, kSolveAdjoint = 2 };
 
 namespace {
 
@@ -195,13 +196,13 @@ int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
     if (phase != 1) {
       rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, sk->x32_shadow, sk->partials, sk->ctl, s, 0);
       if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, sk->x32_shadow, (float)key.lam, sk->g,
-                                          sk->ctl, s, 0);
+                                          sk->ctl, s, 0, key.rhs);
     }
     if (!rc && phase != 0) {
       rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const double*>(key.x),
                            sk->dd_partials, sk->ctl, s, 1);
       if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, static_cast<const double*>(key.x),
-                                             key.lam, nullptr, sk->g, sk->ctl, s, 1);
+                                             key.lam, nullptr, sk->g, sk->ctl, s, 1, key.rhs);
     }
   } else {
     rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const float*>(key.x),
@@ -558,7 +559,6 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve");
   if (rc) return rc;
   MIHS_ARG((b != nullptr || rhs != nullptr) && xv != nullptr, "mihs_solve: null b or x");
-  MIHS_ARG(!(refined && rhs != nullptr), "mihs_solve: no right-hand-side offset in refinement solves");
   MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve: lambda must be > 0");
   MIHS_ARG(opts->sd < (double)sk->m, "mihs_solve: sd=%g must be < m=%lld", opts->sd, (long long)sk->m);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
@@ -569,7 +569,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
     sk->P_dd = apass_dd_num_partials(n, d);
     char* p = nullptr;
     const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + sizeof(double) * (size_t)sk->dp +
-                         sizeof(float) * (size_t)sk->dp;
+                         3 * sizeof(float) * (size_t)sk->dp;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       set_error("mihs_solve_refined: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -578,6 +578,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
     sk->dd_partials = reinterpret_cast<float2*>(p);
     sk->x_prev64 = reinterpret_cast<double*>(p + sizeof(float2) * (size_t)sk->P_dd * sk->dp);
     sk->x32_shadow = reinterpret_cast<float*>(sk->x_prev64 + sk->dp);
+    sk->bw32 = sk->x32_shadow + sk->dp;
   }
   // sd ≤ 0: estimate it from SA (Algorithm 4 with the paper's T = 2,
   // ε_tr = 0.5); an over-estimate only slows the rate (Remark after
@@ -597,8 +598,8 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   const size_t xbytes = (refined ? sizeof(double) : sizeof(float)) * (size_t)d;
 
   // Refinement solves start with plain fp32 gradients and switch to the
-  // compensated pass once the relative residual is below 1e-6 (well above the
-  // fp32 floor); plain solves never switch.
+  // compensated pass once the relative residual is below 1e-6 or stops
+  // improving (the fp32 floor); plain solves never switch.
   const float switch_tol = refined ? 1e-6f : 0.f;
   ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol, refined ? 0 : 1, switch_tol);
   MIHS_CHECK_LAUNCH();
@@ -650,8 +651,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
   const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs};
   bool graph_ran = false;
-  mihs_sketch_s::GraphSlot& gs =
-      sk->slots[refined ? kSolveRefined : (rhs != nullptr ? kSolveAdjoint : kSolvePlain)];
+  mihs_sketch_s::GraphSlot& gs = sk->slots[(refined ? 1 : 0) + (rhs != nullptr ? 2 : 0)];
   if (!timing_on() && !gs.failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
     if (!(gs.exec && gs.key == key)) {
       if (build_graph(sk, key, a, refined, gs) != MIHS_OK) {
@@ -727,6 +727,29 @@ int mihs_backward(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
   if (st < 0) return st;
   const int rc = launch_backward_grads(A, sk->n, sk->d, lda, b, x, v, dA, ldda, db, dlambda,
                                        static_cast<cudaStream_t>(stream));
+  return rc ? rc : st;
+}
+
+int mihs_backward_refined(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, double lambda,
+                          const double* x, const float* gx, const mihs_opts* opts, double* v, float* dA,
+                          int64_t ldda, float* db, double* dlambda, mihs_info* info, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr, "mihs_backward_refined: null handle");
+  MIHS_ARG(gx != nullptr && x != nullptr && v != nullptr, "mihs_backward_refined: null gx, x or v");
+  MIHS_ARG(dA == nullptr || (b != nullptr && ldda >= sk->d), "mihs_backward_refined: dA needs b and ldda >= d");
+  const int st = solve_impl(sk, A, lda, nullptr, lambda, opts, v, true, info, stream, gx);
+  if (st < 0) return st;
+  // The gradients are fp32 outputs: the pass takes x and v rounded to fp32.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = (int)sk->d;
+  float* x32 = sk->bw32;
+  float* v32 = sk->bw32 + sk->dp;
+  f64_to_f32_kernel<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(x, x32, d);
+  MIHS_CHECK_LAUNCH();
+  f64_to_f32_kernel<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(v, v32, d);
+  MIHS_CHECK_LAUNCH();
+  count_launch(2);
+  const int rc = launch_backward_grads(A, sk->n, sk->d, lda, b, x32, v32, dA, ldda, db, dlambda, s);
   return rc ? rc : st;
 }
 

@@ -50,16 +50,17 @@ __device__ __forceinline__ float dot4(const float4 a, const float4 b) {
 
 // Vector path: d, lda, ldda multiples of 4 and 16-byte aligned rows.  Lane
 // `l` holds columns 4(32c + l) … 4(32c + l) + 3 of chunk c < CH, CH =
-// ⌈d/128⌉; x and v live in registers (CH ≤ 8) or shared memory (CH = 16).
-// RW rows per warp iteration give each warp RW·CH independent 16-byte loads
-// in flight.
+// ⌈d/128⌉; x and v live in registers (CH ≤ 4) or shared memory (CH ≥ 8:
+// held in registers they cap the CTA count per SM and, measured at 2²⁰×1024,
+// the pass ran at 0.57 of HBM bandwidth instead of 0.97).  RW rows per warp
+// iteration give each warp RW·CH independent 16-byte loads in flight.
 template <int CH, int RW>
 __global__ void __launch_bounds__(kThreads)
     backward_rows_vec_kernel(const float* __restrict__ A, long long n, int d, long long lda,
                              const float* __restrict__ b, const float* __restrict__ x,
                              const float* __restrict__ v, float* __restrict__ dA, long long ldda,
                              float* __restrict__ db) {
-  constexpr bool XS = CH > 8;
+  constexpr bool XS = CH >= 8;
   __shared__ float4 xs4[XS ? CH * 32 : 1], vs4[XS ? CH * 32 : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d4 = d >> 2;
@@ -212,7 +213,7 @@ int launch_backward_grads(const float* A, int64_t n, int64_t d, int64_t lda, con
   else if (ch <= 1) rc = launch_rows(backward_rows_vec_kernel<1, 4>, n, args, s);
   else if (ch <= 2) rc = launch_rows(backward_rows_vec_kernel<2, 4>, n, args, s);
   else if (ch <= 4) rc = launch_rows(backward_rows_vec_kernel<4, 2>, n, args, s);
-  else if (ch <= 8) rc = launch_rows(backward_rows_vec_kernel<8, 1>, n, args, s);
+  else if (ch <= 8) rc = launch_rows(backward_rows_vec_kernel<8, 2>, n, args, s);
   else rc = launch_rows(backward_rows_vec_kernel<16, 1>, n, args, s);
   timing_end(kTimerBackward, s);
   return rc;

@@ -65,8 +65,9 @@ struct SolveCtl {
   float gnorm0;      // ‖Aᵀb‖
   float gnorm;       // ‖g‖ of the current x
   int phase;         // refinement solves: 0 = plain fp32 gradient, 1 = compensated
-  float switch_tol;  // switch to phase 1 once ‖g‖ ≤ switch_tol·‖Aᵀb‖
-  float pad;
+  float switch_tol;  // switch to phase 1 once ‖g‖ ≤ switch_tol·‖Aᵀb‖ ...
+  float gmin;        // ... or once ‖g‖ has set no new minimum (gmin) for
+  int stall;         //     three steps (stall counts them)
 };
 
 // ------------------------------------------------------------- device side

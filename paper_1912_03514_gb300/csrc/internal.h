@@ -40,9 +40,11 @@ int launch_backward_grads(const float* A, int64_t n, int64_t d, int64_t lda, con
 int apass_dd_num_partials(int64_t n, int64_t d);
 int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
                     float2* partials, SolveCtl* ctl, cudaStream_t s, int gate = -1);
-// g64[j] = Σ_p (hi + lo) − λ·x[j] in fp64; g32 (optional) its fp32 rounding.
+// g64[j] = rhs[j] + Σ_p (hi + lo) − λ·x[j] in fp64 (rhs may be null); g32
+// (optional) its fp32 rounding.  b of launch_apass_dd may be null (taken as 0).
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
-                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate = -1);
+                             double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate = -1,
+                             const float* rhs = nullptr);
 int apass_dd_device_error(int* code);
 
 // ---- AAb_Solver (aab.cu) --------------------------------------------------

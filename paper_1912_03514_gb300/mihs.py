@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
         "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
                               ctypes.POINTER(_Info), _vp]),
         "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "mihs_backward_refined": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp,
+                                         _i64, _vp, _vp, ctypes.POINTER(_Info), _vp]),
         "mihs_backward": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _i64,
                                  _vp, _vp, ctypes.POINTER(_Info), _vp]),
     }
@@ -369,6 +371,36 @@ class Sketch:
         si = SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status) if want_info else None
         return dA, db, dl, v, si
 
+    def backward_refined(self, A: torch.Tensor, b: torch.Tensor, lam: float, sd: float, x: torch.Tensor,
+                         gx: torch.Tensor, tol: float = 1e-10, max_outer: int = 200, eps_sub: float = 0.1,
+                         max_inner: int = 0, v: torch.Tensor | None = None, warm_start: bool = False,
+                         want_dA: bool = True, want_db: bool = True, want_dlambda: bool = True,
+                         want_info: bool = True, stream=None):
+        """mihs_backward_refined: the adjoint solved with compensated refinement
+        (x and v fp64).  Returns (dA, db, dlambda, v, SolveInfo or None)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        for t, nm in ((x, "x"),) + (((v, "v"),) if v is not None else ()):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.numel() == d and t.is_contiguous()):
+                raise ValueError(f"{nm} must be a contiguous CUDA fp64 vector of length d")
+        if v is None:
+            v = torch.empty(d, dtype=torch.float64, device=A.device)
+        dA, db, dl = _grad_outputs(n, d, A.device, want_dA, want_db, want_dlambda)
+        o = lib().mihs_default_opts()
+        o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+        o.max_inner, o.sd, o.warm_start = int(max_inner), float(sd), int(bool(warm_start))
+        info = _Info()
+        rc = lib().mihs_backward_refined(self._h, pa, lda, _vec(b, n, "b"), float(lam), x.data_ptr(),
+                                         _vec(gx, d, "gx"), ctypes.byref(o), v.data_ptr(),
+                                         dA.data_ptr() if dA is not None else None, d,
+                                         db.data_ptr() if db is not None else None,
+                                         dl.data_ptr() if dl is not None else None,
+                                         ctypes.byref(info) if want_info else None, _stream(stream))
+        _check(rc, allow_not_converged=True)
+        si = SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status) if want_info else None
+        return dA, db, dl, v, si
+
     def history(self):
         """Relative residual ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step of the last solve."""
         buf = (ctypes.c_float * 1024)()
@@ -432,14 +464,20 @@ class RidgeSolve(torch.autograd.Function):
 
     The forward pass sketches A and runs Algorithm 1; the backward pass runs
     the adjoint solve with the same sketch and one fused pass over A
-    (mihs_backward).  λ may be a Python number or a 0-d tensor."""
+    (mihs_backward).  λ may be a Python number or a 0-d tensor.  With
+    `refine`, both solves use compensated refinement (mihs_solve_refined,
+    mihs_backward_refined) and x is returned in fp64."""
 
     @staticmethod
-    def forward(ctx, A, b, lam, family, m, sd, seed, tol, max_outer, eps_sub):
+    def forward(ctx, A, b, lam, family, m, sd, seed, tol, max_outer, eps_sub, refine):
         lam_f = float(lam)
         sk = Sketch(A, family, m, seed)
-        x, _ = sk.solve(A, b, lam_f, sd, tol=tol, max_outer=max_outer, eps_sub=eps_sub, want_info=False)
-        ctx.sk, ctx.lam, ctx.sd = sk, lam_f, sd
+        kw = dict(tol=tol, max_outer=max_outer, eps_sub=eps_sub, want_info=False)
+        if refine:
+            x, _ = sk.solve_refined(A, b, lam_f, sd, **kw)
+        else:
+            x, _ = sk.solve(A, b, lam_f, sd, **kw)
+        ctx.sk, ctx.lam, ctx.sd, ctx.refine = sk, lam_f, sd, refine
         ctx.kw = dict(tol=tol, max_outer=max_outer, eps_sub=eps_sub)
         ctx.lam_like = lam if torch.is_tensor(lam) else None
         ctx.save_for_backward(A, b, x)
@@ -449,22 +487,23 @@ class RidgeSolve(torch.autograd.Function):
     def backward(ctx, gx):
         A, b, x = ctx.saved_tensors
         need_A, need_b, need_lam = ctx.needs_input_grad[:3]
-        dA, db, dl, _, _ = ctx.sk.backward(A, b, ctx.lam, ctx.sd, x, gx.contiguous().float(),
-                                           want_dA=need_A, want_db=need_b,
-                                           want_dlambda=need_lam and ctx.lam_like is not None,
-                                           want_info=False, **ctx.kw)
+        bw = ctx.sk.backward_refined if ctx.refine else ctx.sk.backward
+        dA, db, dl, _, _ = bw(A, b, ctx.lam, ctx.sd, x, gx.contiguous().float(),
+                              want_dA=need_A, want_db=need_b,
+                              want_dlambda=need_lam and ctx.lam_like is not None,
+                              want_info=False, **ctx.kw)
         if dl is not None:
             dl = dl.to(dtype=ctx.lam_like.dtype).reshape(ctx.lam_like.shape)
-        return dA, db, dl, None, None, None, None, None, None, None
+        return dA, db, dl, None, None, None, None, None, None, None, None
 
 
 def ridge_solve(A: torch.Tensor, b: torch.Tensor, lam, family="countsketch", m: int | None = None,
                 sd: float = 0.0, seed: int = 0, tol: float = 1e-6, max_outer: int = 100,
-                eps_sub: float = 0.1) -> torch.Tensor:
+                eps_sub: float = 0.1, refine: bool = False) -> torch.Tensor:
     """Differentiable ridge solve (RidgeSolve).  m defaults to min(n, 4·sd)
     rounded up to a multiple of 4 when sd > 0, else to min(n, d)."""
     n, d = A.shape
     if m is None:
         m = min(n, ((int(4 * sd) + 3) // 4) * 4) if sd > 0 else min(n, d)
     return RidgeSolve.apply(A, b, lam, family, int(m), float(sd), int(seed), float(tol), int(max_outer),
-                            float(eps_sub))
+                            float(eps_sub), bool(refine))

@@ -164,6 +164,15 @@ def problem_bandwidth(device: str = "cpu", seed: int = 1001,
                         name=f"ridge-{n}x{d}-poly1-lam1e-4", device=device)
 
 
+def problem_differentiable(device: str = "cpu", seed: int = 1004,
+                           n: int = 1 << 20, d: int = 1024) -> RidgeProblem:
+    """2²⁰×1024, σ_i = i^(−1.5), λ = 1e-4 (sd ≈ 25.5), 40 dB SNR, m = 4·sd
+    rounded up to a multiple of 4: the workload of the differentiable solve."""
+    sigma = profile_polynomial(d, 1.5)
+    return make_problem(n, d, sigma, 1e-4, 40.0, seed,
+                        name=f"ridge-{n}x{d}-poly1.5-lam1e-4", device=device)
+
+
 def problem_scaled(n: int, d: int, seed: int, decades: float = 4.0,
                    sd_frac: float = 0.25, snr_db: float = 30.0,
                    device: str = "cpu") -> RidgeProblem:

@@ -205,3 +205,73 @@ def test_ridge_solve_autograd_matches_torch_fp64():
     assert rel(A.grad, A64.grad) <= 1e-4
     assert rel(b.grad, b64.grad) <= 1e-4
     assert abs(lam.grad.item() - l64.grad.item()) <= 1e-4 * abs(l64.grad.item())
+
+
+def _ill_conditioned():
+    """σᵢ = i^(−1.5), λ = 1e-4 (κ(H) ≈ 1e4): the differentiable workload's
+    profile at a size the oracle solves quickly."""
+    n, d = 65536, 512
+    p = W.make_problem(n, d, W.profile_polynomial(d, 1.5), 1e-4, 40.0, seed=80)
+    w = np.random.default_rng(81).standard_normal(d).astype(np.float32)
+    return p, w
+
+
+def test_backward_refined_matches_oracle():
+    """mihs_backward_refined: the adjoint reaches 1e-10 (the fp32 adjoint
+    stalls orders of magnitude above); every gradient within its rigorous
+    bound: x and v errors (fp64 vs the oracle, then rounded to fp32) pushed
+    through the formulas componentwise, plus the fused pass's rounding."""
+    p, w = _ill_conditioned()
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    An, bn = p.A.double().numpy(), p.b.double().numpy()
+    wt = torch.from_numpy(w).to(DEV)
+    xs, vs, dAs, dbs, dls = o.ridge_backward(An, bn, p.lam, w.astype(np.float64))
+    with mihs.Sketch(A, "countsketch", p.m, seed=9) as sk:
+        x64, ix = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-11, max_outer=300)
+        dA, db, dl, v64, iv = sk.backward_refined(A, b, p.lam, p.sd, x64, wt, tol=1e-10, max_outer=300)
+        x32, _ = sk.solve(A, b, p.lam, p.sd, tol=1e-10, max_outer=300)
+        _, _, _, v32p, iv32 = sk.backward(A, b, p.lam, p.sd, x32, wt, tol=1e-10, max_outer=300)
+    assert ix.converged and iv.converged, (ix, iv)
+    vn = v64.cpu().numpy()
+    err_v = o.rel_error(vn, vs)
+    assert err_v <= 1e-8, err_v
+    assert err_v < 1e-2 * o.rel_error(v32p.cpu().double().numpy(), vs)
+    x32n = x64.cpu().float().double().numpy()
+    v32n = v64.cpu().float().double().numpy()
+    Aa = np.abs(An)
+    ex, ev_ = np.abs(x32n - xs), np.abs(v32n - vs)
+    e_q, eA = _grad_bounds(An, bn, x32n, v32n)
+    assert np.all(np.abs(db.cpu().double().numpy() - dbs) <= Aa @ ev_ + e_q)
+    rs, qs = bn - An @ xs, An @ vs
+    bound_A = (np.outer(Aa @ ex, np.abs(v32n)) + np.outer(np.abs(rs), ev_)
+               + np.outer(Aa @ ev_, np.abs(x32n)) + np.outer(np.abs(qs), ex) + eA)
+    assert np.all(np.abs(dA.cpu().double().numpy() - dAs) <= bound_A)
+    bound_l = ex @ np.abs(v32n) + np.abs(xs) @ ev_ + 4 * p.d * 2.0 ** -53 * (np.abs(x32n) @ np.abs(v32n))
+    assert abs(dl.item() - dls) <= bound_l
+
+
+def test_ridge_solve_refined_autograd_matches_torch_fp64():
+    p, w = _ill_conditioned()
+    wt = torch.from_numpy(w)
+    A = p.A.to(DEV).requires_grad_(True)
+    b = p.b.to(DEV).requires_grad_(True)
+    lam = torch.tensor(p.lam, dtype=torch.float64, device=DEV, requires_grad=True)
+    x = mihs.ridge_solve(A, b, lam, family="countsketch", m=p.m, sd=p.sd, seed=4, tol=1e-10, max_outer=300,
+                         refine=True)
+    assert x.dtype == torch.float64
+    (x * wt.to(DEV).double()).sum().backward()
+    A64 = p.A.double().requires_grad_(True)
+    b64 = p.b.double().requires_grad_(True)
+    l64 = torch.tensor(p.lam, dtype=torch.float64, requires_grad=True)
+    x64 = torch.linalg.solve(A64.T @ A64 + l64 * torch.eye(p.d, dtype=torch.float64), A64.T @ b64)
+    (x64 * wt.double()).sum().backward()
+
+    def rel(a, r):
+        return (a.detach().cpu().double() - r).norm().item() / r.norm().item()
+
+    # fp64 solves to 1e-10 with κ(H) ≈ 1e4: x within ~1e-6 (dense fp64 solve
+    # of the normal equations itself errs by ~κ²·u₆₄); gradients are fp32
+    assert rel(x, x64.detach()) <= 1e-6
+    assert rel(A.grad, A64.grad) <= 1e-5
+    assert rel(b.grad, b64.grad) <= 1e-5
+    assert abs(lam.grad.item() - l64.grad.item()) <= 1e-5 * abs(l64.grad.item())
