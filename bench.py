@@ -341,7 +341,7 @@ def main():
                    "ms_per_step": round(ms_r, 4), "steps": n_ref, "tol": args.refined_tol,
                    "status": {f: inf_r[f].status for f in families},
                    "outer_iters": {f: inf_r[f].outer_iters for f in families},
-                   "switch_tol": 1e-6, "plain_steps": pl_n, "compensated_steps": dd_n,
+                   "switch_tol": 1e-7, "plain_steps": pl_n, "compensated_steps": dd_n,
                    "apass_dd_avg_us": round(dd_avg_s * 1e6, 2),
                    "apass_dd_frac_of_hbm": round(bytes_per_pass / dd_avg_s / 1e9 / peaks["hbm_gbs"], 4)}
 

@@ -242,7 +242,7 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
 
 /* Algorithm 1 with compensated refinement: the same iteration with the
  * iterate x in fp64.  Steps use the plain fp32 gradient until the relative
- * residual is below 1e-6 or has set no new minimum for three steps, then the
+ * residual is below 1e-7 or has set no new minimum for three steps, then the
  * gradient g = Aᵀ(b − Ax) − λx computed by a
  * compensated pass over A (double-float sums: TwoProduct/TwoSum in fp32
  * pairs, fp64 partial sums), while SA, AAb_Solver and its stop test stay

@@ -20,13 +20,18 @@ namespace {
 
 // Consumer warps per block: 8, or 7 for rows wider than 1024 so that the
 // block has 256 threads and each may hold 255 registers (the double-float
-// column accumulators need 8 registers per float4 column group).
+// column accumulators need 8 registers per float4 column group).  Rows up to
+// 1024 wide run two blocks per SM (≤ 112 registers a thread): the pass is
+// bound by the latency of its dependent TwoSum chains, and one block of
+// eight consumer warps left each scheduler without an eligible warp 45% of
+// the time.
 template <int CH>
 struct DdCfg {
   static constexpr int NC = CH > 8 ? 7 : 8;
   static constexpr int kThreads = (NC + 1) * 32;
+  static constexpr int kBlocksPerSm = CH > 8 ? 1 : 2;
+  static constexpr size_t kRingBudget = CH > 8 ? 150 * 1024 : 96 * 1024;
 };
-constexpr size_t kRingBudget = 150 * 1024;
 
 __device__ int g_apass_dd_error = 0;
 
@@ -68,8 +73,8 @@ __device__ __forceinline__ DF df_shfl_xor_sum(DF v) {
   return v;
 }
 
-template <int CH>
-__global__ void __launch_bounds__(DdCfg<CH>::kThreads, 1)
+template <int CH, bool RAGGED>
+__global__ void __launch_bounds__(DdCfg<CH>::kThreads, DdCfg<CH>::kBlocksPerSm)
 apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const float* __restrict__ b,
                 const double* __restrict__ x, float2* __restrict__ partials, int dpad, int rows_per_cta,
                 int stages, SolveCtl* __restrict__ ctl, int gate) {
@@ -151,6 +156,7 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
       // copied padding may hold anything.  Read twice (dot, then accumulate)
       // instead of being kept in registers.
       auto chunk = [&](int c) {
+        if (!RAGGED) return row4[lane + 32 * c];  // d = 128·CH: no ragged group
         const int col = 4 * lane + 128 * c;
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col < d) {
@@ -163,7 +169,9 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
         }
         return t;
       };
-      DF sum = {0.f, 0.f};
+      // Four independent double-float chains (one per float4 component) so
+      // that consecutive TwoSums do not wait on each other.
+      DF sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sw = {0.f, 0.f};
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int col = 4 * lane + 128 * c;
@@ -172,14 +180,18 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
         const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
         float p, e;
         df_prod(t.x, h4.x, l4.x, p, e);
-        df_add(sum, p, e);
+        df_add(sx, p, e);
         df_prod(t.y, h4.y, l4.y, p, e);
-        df_add(sum, p, e);
+        df_add(sy, p, e);
         df_prod(t.z, h4.z, l4.z, p, e);
-        df_add(sum, p, e);
+        df_add(sz, p, e);
         df_prod(t.w, h4.w, l4.w, p, e);
-        df_add(sum, p, e);
+        df_add(sw, p, e);
       }
+      df_add(sx, sy.hi, sy.lo);
+      df_add(sz, sw.hi, sw.lo);
+      df_add(sx, sz.hi, sz.lo);
+      DF sum = sx;
       sum = df_shfl_xor_sum(sum);
       // r = b − (sum.hi + sum.lo), renormalised to a double-float pair
       float rh, re;
@@ -271,29 +283,35 @@ struct DdKernel {
   const void* fn;
   int chunks;
   int nc;  // consumer warps = rows per stage
+  int blocks_per_sm;
+  size_t ring_budget;
 };
 
 template <int CH>
-DdKernel make_dd() {
-  return DdKernel{reinterpret_cast<const void*>(&apass_dd_kernel<CH>), CH, DdCfg<CH>::NC};
+DdKernel make_dd(bool ragged) {
+  using C = DdCfg<CH>;
+  const void* fn = ragged ? reinterpret_cast<const void*>(&apass_dd_kernel<CH, true>)
+                          : reinterpret_cast<const void*>(&apass_dd_kernel<CH, false>);
+  return DdKernel{fn, CH, C::NC, C::kBlocksPerSm, C::kRingBudget};
 }
 
 DdKernel pick_dd(int64_t d) {
   const int ch = (int)((d + 127) / 128);
-  if (ch <= 1) return make_dd<1>();
-  if (ch <= 2) return make_dd<2>();
-  if (ch <= 4) return make_dd<4>();
-  if (ch <= 8) return make_dd<8>();
-  if (ch <= 12) return make_dd<12>();
-  return make_dd<16>();
+  if (ch <= 1) return make_dd<1>(d != 128);
+  if (ch <= 2) return make_dd<2>(d != 256);
+  if (ch <= 4) return make_dd<4>(d != 512);
+  if (ch <= 8) return make_dd<8>(d != 1024);
+  if (ch <= 12) return make_dd<12>(d != 1536);
+  return make_dd<16>(d != 2048);
 }
 
 }  // namespace
 
 int apass_dd_num_partials(int64_t n, int64_t d) {
-  const int nc = pick_dd(d).nc;
+  const DdKernel k = pick_dd(d);
+  const int nc = k.nc;
   const int64_t by_rows = (n + nc - 1) / nc;
-  int64_t P = num_sms();
+  int64_t P = (int64_t)num_sms() * k.blocks_per_sm;
   if (P > by_rows) P = by_rows;
   return (int)(P < 1 ? 1 : P);
 }
@@ -306,7 +324,7 @@ int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const flo
   const int R = k.nc;
   const int rows_per_cta = (int)round_up((n + P - 1) / P, R);
   const size_t stage_bytes = (size_t)R * dpad * sizeof(float);
-  int stages = (int)(kRingBudget / stage_bytes);
+  int stages = (int)(k.ring_budget / stage_bytes);
   stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
   // The ring must also hold the NC × dpad float2 warp pairs at the end.
   while ((size_t)stages * stage_bytes < (size_t)k.nc * dpad * sizeof(float2)) ++stages;

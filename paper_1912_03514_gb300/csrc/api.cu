@@ -598,9 +598,9 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   const size_t xbytes = (refined ? sizeof(double) : sizeof(float)) * (size_t)d;
 
   // Refinement solves start with plain fp32 gradients and switch to the
-  // compensated pass once the relative residual is below 1e-6 or stops
+  // compensated pass once the relative residual is below 1e-7 or stops
   // improving (the fp32 floor); plain solves never switch.
-  const float switch_tol = refined ? 1e-6f : 0.f;
+  const float switch_tol = refined ? 1e-7f : 0.f;
   ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol, refined ? 0 : 1, switch_tol);
   MIHS_CHECK_LAUNCH();
   count_launch();
