@@ -26,6 +26,8 @@ Contents and the passage each follows:
   theorem1_params ...... β*, α*, rate of Theorem 1.
   mihs ................. Algorithm 1 (M-IHS for n ≥ d).
   hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
+  ridge_path ........... x*(λ) for every λ of a path (the plain definition
+                          per λ; Algorithm 1 applied to each λ on its own).
   ridge_backward ....... gradients of x*(A, b, λ) through the normal equations
                           of Section 1 (not in the paper: the adjoint of the
                           linear solve; parity pinned by central differences).
@@ -291,6 +293,26 @@ def stat_dim(sigma, lam):
 
 def stat_dim_of(A, lam):
     return stat_dim(np.linalg.svd(np.asarray(A, dtype=np.float64), compute_uv=False), lam)
+
+
+def ridge_path(A, b, lambdas, refine: int = 2):
+    """x*(λ_l) = (AᵀA + λ_l I)⁻¹Aᵀb for each λ_l: one fp64 Gram, then per λ a
+    Cholesky, two triangular solves and `refine` refinement steps (as in
+    exact_solve).  Returns an array of shape (len(lambdas), d)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    b64 = np.asarray(b, dtype=np.float64)
+    G = A64.T @ A64
+    Atb = A64.T @ b64
+    out = []
+    for lam in lambdas:
+        H = G + lam * np.eye(G.shape[0])
+        L = np.linalg.cholesky(H)
+        hsolve = lambda v: np.linalg.solve(L.T, np.linalg.solve(L, v))
+        x = hsolve(Atb)
+        for _ in range(refine):
+            x = x + hsolve(A64.T @ (b64 - A64 @ x) - lam * x)
+        out.append(x)
+    return np.array(out)
 
 
 def ridge_backward(A, b, lam, gbar, x=None):

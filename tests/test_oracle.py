@@ -489,3 +489,23 @@ def test_ridge_backward_orthonormal_columns_closed_form():
     t = 1e-6
     fd = (L(t) - L(-t)) / (2 * t)
     assert abs(fd - np.sum(dA * Q)) <= 1e-8
+
+
+# ------------------------------------------------------------------ λ-paths
+def test_ridge_path_against_svd_filter_factors_and_limits():
+    """Each λ of a path against the SVD closed form (Eq. tsvdsol); ‖x*(λ)‖
+    strictly decreasing in λ (the filter factors σ²/(σ²+λ) all decrease);
+    λ·x*(λ) → Aᵀb as λ → ∞."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((60, 12)) @ np.diag(np.logspace(0, -3, 12))
+    b = rng.standard_normal(60)
+    lams = np.logspace(-6, 1, 16)
+    X = o.ridge_path(A, b, lams)
+    for lam, x in zip(lams, X):
+        ref = o.svd_solve(A, b, lam)
+        assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    norms = np.linalg.norm(X, axis=1)
+    assert np.all(np.diff(norms) < 0)
+    big = 1e8
+    xb = o.ridge_path(A, b, [big])[0]
+    assert np.linalg.norm(big * xb - A.T @ b) <= 1e-6 * np.linalg.norm(A.T @ b)
