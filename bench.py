@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-backward", action="store_true", help="skip the differentiable-solve leg")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
-    ap.add_argument("--profile-op", choices=["apass", "aab", "aab-late", "gaussian", "countsketch", "srht"],
+    ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "aab", "aab-late", "gaussian",
+                                            "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
 
@@ -530,6 +531,12 @@ def run_profile_op(args, local):
         fn = lambda: mihs.aab_solve(SA, g, p.lam, 0.1, delta=delta)
     elif op == "apass":
         fn = lambda: mihs.gradient(A, b, x, p.lam, g=g)
+    elif op == "apass-dd":
+        x64, g64 = x.double(), torch.empty(p.d, device=dev, dtype=torch.float64)
+        fn = lambda: mihs.gradient_refined(A, b, x64, p.lam, g=g64)
+    elif op == "backward":
+        v = W.randn((p.d,), seed=6, scale=0.01).to(dev)
+        fn = lambda: mihs.backward_grads(A, b, x, v)
     else:
         SA = torch.empty(p.m, p.d, device=dev)
         fn = lambda: mihs.sketch_apply(A, op, p.m, 3, SA=SA)

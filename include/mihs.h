@@ -73,12 +73,14 @@ int mihs_device_status(int* code);
 
 /* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
  * the records and starts recording CUDA events on the launching stream around
- * every gradient A-pass kernel (timer 0), AAb_Solver kernel (timer 1),
- * sketch call (timer 2) and compensated A-pass kernel (timer 3); while it is on, mihs_solve runs its steps as host-
- * driven launches and reads the stop flag back after each step, so only
- * launches that did work are recorded.  mihs_timing(0) stops recording.
- * mihs_timing_read synchronises on the recorded events and returns the summed
- * duration (ms) and the number of launches of one timer. */
+ * every launch of: the gradient A-pass (timer 0), AAb_Solver (timer 1), a
+ * sketch call (timer 2), the compensated A-pass (timer 3), the backward
+ * gradient pass (timer 4) and the λ-path gradient pass (timer 5).  While it
+ * is on, solves run their steps as host-driven launches and read the stop
+ * state back after each step, so only launches that did work are recorded.
+ * mihs_timing(0) stops recording.  mihs_timing_read synchronises on the
+ * recorded events and returns the summed duration (ms) and the number of
+ * launches of one timer. */
 int mihs_timing(int on);
 int mihs_timing_read(int which, double* total_ms, int64_t* count);
 
@@ -263,6 +265,64 @@ int mihs_solve_refined(mihs_sketch_t sk, const float* A, int64_t lda, const floa
 int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda,
                           const float* b, const double* x, double lambda,
                           double* g, void* stream);
+
+/* ------------------------------------------------------------------------
+ * λ-paths and batches.  Algorithm 1 for several regularisation values on
+ * one matrix: SA does not depend on λ (AAb_Solver takes λ as an argument,
+ * Algorithm 5), so one sketch serves the whole path, and the gradients of
+ * all iterates are formed in ONE pass over A per outer step.  Each λ_l keeps
+ * its own iterate, momentum parameters β_l = sd_l/m, α_l = (1 − β_l)²
+ * (Corollary 3) and stop test; the path stops when every λ has.
+ * ---------------------------------------------------------------------- */
+
+/* The path's gradient step on its own: G_l = Aᵀ(b − A·X_l) − λ_l·X_l for
+ * l < nl ≤ 16 in one pass over A.  X and G DEVICE, λ-major (row l of pitch
+ * ldx / ldg ≥ d); lambdas HOST (λ_l ≥ 0).  d ≤ 1024.  Allocates
+ * stream-ordered scratch for the split-K partials.  Errors: INVALID_ARG,
+ * UNSUPPORTED, CUDA, OOM. */
+int mihs_gradient_path(const float* A, int64_t n, int64_t d, int64_t lda,
+                       const float* b, int nl, const double* lambdas,
+                       const float* X, int64_t ldx, float* G, int64_t ldg,
+                       void* stream);
+
+/* Solve the ridge problem (A, b, λ_l) for l < nlambda with the handle's SA.
+ *   lambdas  HOST array of nlambda values > 0.
+ *   sds      HOST array of nlambda statistical dimensions (< m), or NULL:
+ *            each estimated from SA by Algorithm 4 (T = 2, ε_tr = 0.5,
+ *            capped at 0.95·m; the call then synchronises).
+ *   opts     tol, max_outer, eps_sub, max_inner, warm_start as in
+ *            mihs_solve (opts->sd is ignored).
+ *   X        DEVICE nlambda × d, λ-major: X + l·ldx is x(λ_l) (the starting
+ *            point when opts->warm_start, the solution on exit); ldx ≥ d.
+ *   infos    optional HOST array of nlambda; when non-NULL the call
+ *            synchronises and returns the worst status.
+ * λ values are processed in groups of 16 (one device-side graph loop per
+ * group, cached in the handle).  d ≤ 1024 (MIHS_ERR_UNSUPPORTED beyond).
+ * The first path solve on a handle allocates its workspace (cudaMalloc). */
+int mihs_solve_path(mihs_sketch_t sk, const float* A, int64_t lda,
+                    const float* b, int nlambda, const double* lambdas,
+                    const double* sds, const mihs_opts* opts, float* X,
+                    int64_t ldx, mihs_info* infos, void* stream);
+
+/* One problem of a batch: its handle (sketched from its A), A, b and the
+ * λ-major output X (nlambda × d, pitch ldx), all device memory. */
+typedef struct {
+  mihs_sketch_t sk;
+  const float* A;
+  int64_t lda;
+  const float* b;
+  float* X;
+  int64_t ldx;
+} mihs_problem;
+
+/* mihs_solve_path for nprob independent problems sharing one λ list:
+ * the problems run concurrently on internal streams forked from and joined
+ * back into `stream`.  sds: HOST nprob × nlambda (row i for problem i) or
+ * NULL; infos: HOST nprob × nlambda or NULL (then no synchronisation).
+ * Every problem must have its own handle.  Returns the worst status. */
+int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda,
+                       const double* lambdas, const double* sds,
+                       const mihs_opts* opts, mihs_info* infos, void* stream);
 
 /* ------------------------------------------------------------------------
  * Differentiation of the solution x(A, b, λ) = (AᵀA + λI)⁻¹Aᵀb.  The paper

@@ -61,6 +61,11 @@ struct AabParams {
   int cols_log2;
   int sa_in_smem;
   int sa_vec;          // SA rows may be read as float4 (ldsa % 4 == 0, 16-byte aligned)
+  int path;            // λ-path mode: cluster row blockIdx.y solves λ_y
+  PathScalars ps;
+  long long path_ldg, path_ldx;
+  int* path_ndone;
+  int* path_all_done;
 };
 
 // Deterministic block-wide sum; every thread returns the same value.
@@ -153,6 +158,20 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int d = P.d, dp = P.dp;
+  // λ-path mode: the clusters of grid row blockIdx.y solve λ_y with their own
+  // g, x, x⁻ and control block; the path's stop counter ends the graph loop
+  // once every λ has stopped.
+  const int li = P.path ? (int)blockIdx.y : 0;
+  const float* g_in = P.g + (long long)li * P.path_ldg;
+  SolveCtl* ctl_ = P.ctl != nullptr ? P.ctl + li : nullptr;
+  float* x_ = P.x != nullptr ? P.x + (long long)li * P.path_ldx : nullptr;
+  float* xprev_ = P.x_prev != nullptr ? P.x_prev + (long long)li * P.path_ldg : nullptr;
+  float* delta_ = P.path ? nullptr : P.delta;
+  int* passes_ = P.path ? nullptr : P.passes;
+  float* hist_ = P.path ? nullptr : P.hist;
+  const float lam_ = P.path ? P.ps.lam[li] : P.lambda;
+  const float alpha_ = P.path ? P.ps.alpha[li] : P.alpha;
+  const float beta_ = P.path ? P.ps.beta[li] : P.beta;
 
   extern __shared__ float4 smem4[];
   float* v = reinterpret_cast<float*>(smem4);  // replicated d-vectors
@@ -172,20 +191,20 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
   // rank 0 writes it, after the last barrier.
   int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1;
   float tol = 0.f, gnorm0 = 0.f, switch_tol = 0.f;
-  if (P.ctl != nullptr) {
-    done = P.ctl->done;
-    outer = P.ctl->outer;
-    max_outer = P.ctl->max_outer;
-    g0known = P.ctl->gnorm0_known;
-    tol = P.ctl->tol;
-    gnorm0 = P.ctl->gnorm0;
-    phase = P.ctl->phase;
-    switch_tol = P.ctl->switch_tol;
+  if (ctl_ != nullptr) {
+    done = ctl_->done;
+    outer = ctl_->outer;
+    max_outer = ctl_->max_outer;
+    g0known = ctl_->gnorm0_known;
+    tol = ctl_->tol;
+    gnorm0 = ctl_->gnorm0;
+    phase = ctl_->phase;
+    switch_tol = ctl_->switch_tol;
   }
   cluster.sync();  // every block is running before any DSMEM access
   if (done) {
     // Already stopped: make sure a device-side loop around this kernel ends.
-    if (P.cond != 0ull && rank == 0 && tid == 0)
+    if (P.cond != 0ull && !P.path && rank == 0 && tid == 0)
       cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
     return;
   }
@@ -224,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
   // θ₁ v = g
   float gsq = 0.f;
   for (int j = tid; j < dp; j += kThreads) {
-    const float gj = j < d ? P.g[j] : 0.f;
+    const float gj = j < d ? g_in[j] : 0.f;
     v[j] = gj;
     gsq = fmaf(gj, gj, gsq);
     xs[j] = 0.f;
@@ -235,15 +254,15 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
   if (staged_async) {
     // Every thread waits for the rows (also on the early-exit paths below, so
     // that no copy is still landing when the block exits).
-    if (!mbar_wait(stage_bar, 0u, kWaitLimitNs) && tid == 0 && P.ctl != nullptr) {
-      P.ctl->status = MIHS_ERR_TIMEOUT;
-      P.ctl->done = 1;
+    if (!mbar_wait(stage_bar, 0u, kWaitLimitNs) && tid == 0 && ctl_ != nullptr) {
+      ctl_->status = MIHS_ERR_TIMEOUT;
+      ctl_->done = 1;
     }
   }
 
-  if (P.ctl != nullptr) {  // stop test of Algorithm 1 on ‖g‖ = θ₁
+  if (ctl_ != nullptr) {  // stop test of Algorithm 1 on ‖g‖ = θ₁
     const float g0 = g0known ? gnorm0 : theta1;
-    if (P.hist != nullptr && rank == 0 && tid == 0 && outer < kHistCap) P.hist[outer] = theta1;
+    if (hist_ != nullptr && rank == 0 && tid == 0 && outer < kHistCap) hist_[outer] = theta1;
     const bool bad = !(theta1 <= 3.0e38f);
     const bool conv = tol > 0.f && theta1 <= tol * g0;
     const bool capped = outer >= max_outer;
@@ -252,20 +271,27 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     // three steps (it has reached its fp32 floor, which for a generic
     // right-hand side can lie above switch_tol).
     if (phase == 0 && rank == 0 && tid == 0) {
-      const float gmin = P.ctl->gmin;
-      const int stall = theta1 < gmin ? 0 : P.ctl->stall + 1;
-      if (theta1 < gmin) P.ctl->gmin = theta1;
-      P.ctl->stall = stall;
-      if (theta1 <= switch_tol * g0 || stall >= 3) P.ctl->phase = 1;
+      const float gmin = ctl_->gmin;
+      const int stall = theta1 < gmin ? 0 : ctl_->stall + 1;
+      if (theta1 < gmin) ctl_->gmin = theta1;
+      ctl_->stall = stall;
+      if (theta1 <= switch_tol * g0 || stall >= 3) ctl_->phase = 1;
     }
     if (bad || conv || capped) {
       if (rank == 0 && tid == 0) {
-        P.ctl->gnorm = theta1;
-        P.ctl->gnorm0 = g0;
-        P.ctl->gnorm0_known = 1;
-        P.ctl->status = bad ? MIHS_ERR_NUMERIC : (conv ? MIHS_OK : MIHS_NOT_CONVERGED);
-        P.ctl->done = 1;
-        if (P.cond != 0ull) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
+        ctl_->gnorm = theta1;
+        ctl_->gnorm0 = g0;
+        ctl_->gnorm0_known = 1;
+        ctl_->status = bad ? MIHS_ERR_NUMERIC : (conv ? MIHS_OK : MIHS_NOT_CONVERGED);
+        ctl_->done = 1;
+        if (P.path) {
+          if (atomicAdd(P.path_ndone, 1) + 1 == P.ps.nl) {  // the last λ of the path to stop
+            *P.path_all_done = 1;
+            if (P.cond != 0ull) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
+          }
+        } else if (P.cond != 0ull) {
+          cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
+        }
       }
       return;  // no DSMEM access has happened since the barrier
     }
@@ -303,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     __syncthreads();
     float rho = sqrtf(scal[2]);
 
-    const float lam = P.lambda;
+    const float lam = lam_;
     float rhobar = sqrtf(rho * rho + lam);
     float c = rho / rhobar;
     float s = sqrtf(lam) / rhobar;
@@ -403,11 +429,11 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const int e1 = min(d, c0 + P.cols_per);
     for (int j = c0 + tid; j < e1; j += kThreads) {
       const float dj = xs[j];
-      if (P.delta != nullptr) P.delta[j] = dj;
-      if (P.x != nullptr) {
-        const float xj = P.x[j], xp = P.x_prev[j];
-        P.x[j] = xj + P.alpha * dj + P.beta * (xj - xp);
-        P.x_prev[j] = xj;
+      if (delta_ != nullptr) delta_[j] = dj;
+      if (x_ != nullptr) {
+        const float xj = x_[j], xp = xprev_[j];
+        x_[j] = xj + alpha_ * dj + beta_ * (xj - xp);
+        xprev_[j] = xj;
       }
       if (P.x64 != nullptr) {
         const double xj = P.x64[j], xp = P.x_prev64[j];
@@ -419,14 +445,14 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     }
   }
   if (rank == 0 && tid == 0) {
-    if (P.passes != nullptr) *P.passes = k;
-    if (P.ctl != nullptr) {
-      P.ctl->outer = outer + 1;
-      P.ctl->inner_total += k;
-      P.ctl->gnorm = theta1;
+    if (passes_ != nullptr) *passes_ = k;
+    if (ctl_ != nullptr) {
+      ctl_->outer = outer + 1;
+      ctl_->inner_total += k;
+      ctl_->gnorm = theta1;
       if (!g0known) {
-        P.ctl->gnorm0 = theta1;
-        P.ctl->gnorm0_known = 1;
+        ctl_->gnorm0 = theta1;
+        ctl_->gnorm0_known = 1;
       }
     }
   }
@@ -562,6 +588,16 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   P.ctl = a.ctl;
   P.cond = a.cond;
   P.hist = a.hist;
+  P.path = a.path;
+  P.ps = a.ps;
+  P.path_ldg = a.path_ldg;
+  P.path_ldx = a.path_ldx;
+  P.path_ndone = a.path_ndone;
+  P.path_all_done = a.path_all_done;
+  if (a.path && (a.ps.nl < 1 || a.ps.nl > 16 || a.x64 != nullptr)) {
+    set_error("aab: path mode needs 1..16 λ and an fp32 iterate");
+    return MIHS_ERR_INVALID_ARG;
+  }
   const ClusterPlan cp = plan_cluster(a.m, P.dp);
   if (cp.cl == 0) {
     set_error("aab: no thread-block cluster fits for m=%d d=%d", a.m, a.d);
@@ -589,7 +625,7 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   attr[0].val.clusterDim.x = cp.cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(cp.cl);
+  cfg.gridDim = dim3(cp.cl, a.path ? a.ps.nl : 1);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = cp.smem;
   cfg.stream = s;

@@ -93,6 +93,42 @@ __global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int pha
   *ctl = c;
 }
 
+// λ-path control blocks: one per λ (plain solves), the stop counter cleared.
+__global__ void path_init_kernel(SolveCtl* ctl, int* cnt, int nl, int max_outer, float tol) {
+  const int l = threadIdx.x;
+  if (l < nl) {
+    SolveCtl c = {};
+    c.max_outer = max_outer;
+    c.tol = tol;
+    c.status = MIHS_OK;
+    c.phase = 1;
+    c.gmin = 3.0e38f;
+    ctl[l] = c;
+  }
+  if (l == 0) {
+    cnt[0] = 0;
+    cnt[1] = 0;
+  }
+}
+
+// ‖g‖ (g = Aᵀb) as the path's common relative-residual denominator.
+__global__ void path_set_gnorm0_kernel(SolveCtl* ctl, int nl, const float* g, int d) {
+  __shared__ float red[32];
+  float s = 0.f;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s = fmaf(g[j], g[j], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int l = 0; l < nl; ++l) {
+      ctl[l].gnorm0 = sqrtf(t);
+      ctl[l].gnorm0_known = 1;
+    }
+  }
+}
+
 __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int d) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < d) b[j] = (float)a[j];
@@ -173,6 +209,29 @@ struct mihs_sketch_s {
     Key key = {};
     bool failed = false;  // capture failed once: host-driven steps from then on
   } slots[4];  // indexed by (refined ? 1 : 0) + (adjoint ? 2 : 0)
+  // λ-path workspace (allocated on the first path solve): split-K partials
+  // (P_path × 16 × dp), G and X⁻ (16 × dp each), 16 control blocks and the
+  // path's stop counter / flag.
+  float* path_partials = nullptr;
+  float* path_g = nullptr;
+  float* path_xprev = nullptr;
+  SolveCtl* path_ctl = nullptr;
+  int* path_cnt = nullptr;  // [0] λ stopped, [1] all stopped
+  SolveCtl* path_ctl_host = nullptr;  // pinned, path_ctl_cap entries (one per λ of the last path)
+  int path_ctl_cap = 0;
+  int P_path = 0;
+  struct PathKey {
+    const float* A; int64_t lda; const float* b; float* X; int64_t ldx;
+    PathScalars ps; float eps; int max_passes;
+    bool operator==(const PathKey& o) const {
+      return A == o.A && lda == o.lda && b == o.b && X == o.X && ldx == o.ldx && eps == o.eps &&
+             max_passes == o.max_passes && std::memcmp(&ps, &o.ps, sizeof(ps)) == 0;
+    }
+  };
+  cudaGraph_t path_graph = nullptr;
+  cudaGraphExec_t path_exec = nullptr;
+  PathKey path_key = {};
+  bool path_graph_failed = false;
 };
 
 namespace {
@@ -214,13 +273,15 @@ int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
   return rc;
 }
 
-// Captures the loop body into a conditional WHILE node.  Returns MIHS_OK or
-// an error (the caller then falls back to host-driven iterations).
-int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto, bool refined,
-                mihs_sketch_s::GraphSlot& gs) {
-  cudaGraph_t& graph = gs.graph;
-  cudaGraphExec_t& exec = gs.exec;
-  drop_graph(gs);
+// Captures `body(cond, stream)` into the body graph of a conditional WHILE
+// node.  Returns MIHS_OK or an error (the caller then falls back to
+// host-driven iterations).
+template <typename Body>
+int build_while_graph(mihs_sketch_s* sk, int m, int d, cudaGraph_t& graph, cudaGraphExec_t& exec, Body body) {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
   if (!sk->cap) MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&sk->cap, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   MIHS_CUDA_TRY(cudaGraphCreate(&g, 0));
@@ -234,13 +295,11 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
   np.conditional.size = 1;
   cudaGraphNode_t node;
   MIHS_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  aab_prepare((int)sk->m, (int)sk->d);
-  MIHS_CUDA_TRY(cudaStreamBeginCaptureToGraph(sk->cap, body, nullptr, nullptr, 0,
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  aab_prepare(m, d);
+  MIHS_CUDA_TRY(cudaStreamBeginCaptureToGraph(sk->cap, bodyg, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal));
-  AabLaunch a = proto;
-  a.cond = (unsigned long long)h;
-  int rc = launch_step(sk, key, a, refined, sk->cap);
+  int rc = body((unsigned long long)h, sk->cap);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(sk->cap, &out);
   if (rc) return rc;
@@ -249,8 +308,30 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
     return MIHS_ERR_CUDA;
   }
   MIHS_CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
-  gs.key = key;
   return MIHS_OK;
+}
+
+int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunch& proto, bool refined,
+                mihs_sketch_s::GraphSlot& gs) {
+  const int rc = build_while_graph(sk, (int)sk->m, (int)sk->d, gs.graph, gs.exec,
+                                   [&](unsigned long long cond, cudaStream_t cs) {
+                                     AabLaunch a = proto;
+                                     a.cond = cond;
+                                     return launch_step(sk, key, a, refined, cs);
+                                   });
+  if (rc == MIHS_OK) gs.key = key;
+  return rc;
+}
+
+// One outer step of Algorithm 1 for every λ of a path: the shared gradient
+// pass, its reduce, and one AAb_Solver cluster per λ (+ heavy ball).
+int launch_path_step(mihs_sketch_s* sk, const mihs_sketch_s::PathKey& k, const AabLaunch& a, cudaStream_t s) {
+  const int* all_done = sk->path_cnt + 1;
+  int rc = launch_apass_path(k.A, sk->n, sk->d, k.lda, k.b, k.X, k.ldx, k.ps.nl, sk->path_partials, all_done, s);
+  if (!rc) rc = launch_apass_path_finalize(sk->path_partials, sk->P_path, sk->d, k.X, k.ldx, k.ps, sk->path_g,
+                                           sk->dp, all_done, s);
+  if (!rc) rc = launch_aab(a, s);
+  return rc;
 }
 
 }  // namespace
@@ -278,14 +359,16 @@ uint64_t mihs_launch_count(void) { return g_launches.load(); }
 int mihs_device_status(int* code) {
   set_error("");
   MIHS_ARG(code != nullptr, "mihs_device_status: null code");
-  int a = 0, g = 0, dd = 0;
+  int a = 0, g = 0, dd = 0, pa = 0;
   int rc = apass_device_error(&a);
   if (rc) return rc;
   rc = gauss_tc_device_error(&g);
   if (rc) return rc;
   rc = apass_dd_device_error(&dd);
   if (rc) return rc;
-  *code = a ? a : (g ? g : dd);
+  rc = apass_path_device_error(&pa);
+  if (rc) return rc;
+  *code = a ? a : (g ? g : (dd ? dd : pa));
   return MIHS_OK;
 }
 
@@ -542,8 +625,12 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk == nullptr) return MIHS_OK;
   cudaDeviceSynchronize();
   for (auto& gs : sk->slots) drop_graph(gs);
+  if (sk->path_exec) cudaGraphExecDestroy(sk->path_exec);
+  if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
   if (sk->cap) cudaStreamDestroy(sk->cap);
   if (sk->dd_partials) cudaFree(sk->dd_partials);
+  if (sk->path_partials) cudaFree(sk->path_partials);
+  if (sk->path_ctl_host) cudaFreeHost(sk->path_ctl_host);
   cudaFreeHost(sk->ctl_host);
   cudaFree(sk->SA);
   delete sk;
@@ -751,6 +838,273 @@ int mihs_backward_refined(mihs_sketch_t sk, const float* A, int64_t lda, const f
   count_launch(2);
   const int rc = launch_backward_grads(A, sk->n, sk->d, lda, b, x32, v32, dA, ldda, db, dlambda, s);
   return rc ? rc : st;
+}
+
+// Enqueues the λ-path solves of one problem (groups of ≤ 16 λ), copying each
+// group's control blocks into the handle's pinned host array when
+// want_info.  Does not synchronise unless an sd has to be estimated.
+static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, int nlambda,
+                        const double* lambdas, const double* sds, const mihs_opts* opts, float* X, int64_t ldx,
+                        bool want_info, cudaStream_t s) {
+  MIHS_ARG(sk != nullptr && opts != nullptr && lambdas != nullptr && X != nullptr && b != nullptr,
+           "mihs_solve_path: null argument");
+  int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve_path");
+  if (rc) return rc;
+  const int64_t n = sk->n, d = sk->d;
+  MIHS_ARG(nlambda >= 1, "mihs_solve_path: nlambda must be >= 1");
+  MIHS_ARG(ldx >= d, "mihs_solve_path: ldx=%lld < d", (long long)ldx);
+  MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve_path: bad max_outer");
+  MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve_path: eps_sub must be >= 0");
+  for (int l = 0; l < nlambda; ++l) {
+    MIHS_ARG(lambdas[l] > 0.0 && std::isfinite(lambdas[l]), "mihs_solve_path: lambda[%d] must be > 0", l);
+    if (sds != nullptr)
+      MIHS_ARG(sds[l] < (double)sk->m, "mihs_solve_path: sd[%d]=%g must be < m", l, sds[l]);
+  }
+  if (d > apass_path_max_d()) {
+    set_error("mihs_solve_path: d=%lld > %d is not supported", (long long)d, apass_path_max_d());
+    return MIHS_ERR_UNSUPPORTED;
+  }
+  if (sk->path_partials == nullptr) {
+    sk->P_path = apass_path_num_partials(n);
+    const size_t fl = (size_t)sk->P_path * 16 * sk->dp + 2 * 16 * (size_t)sk->dp;
+    const size_t bytes = fl * sizeof(float) + 16 * sizeof(SolveCtl) + 4 * sizeof(int);
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      set_error("mihs_solve_path: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+    }
+    sk->path_partials = reinterpret_cast<float*>(p);
+    sk->path_g = sk->path_partials + (size_t)sk->P_path * 16 * sk->dp;
+    sk->path_xprev = sk->path_g + 16 * (size_t)sk->dp;
+    sk->path_ctl = reinterpret_cast<SolveCtl*>(p + fl * sizeof(float));
+    sk->path_cnt = reinterpret_cast<int*>(sk->path_ctl + 16);
+  }
+  if (want_info) {
+    if (sk->path_ctl_host != nullptr && sk->path_ctl_cap < nlambda) {
+      cudaFreeHost(sk->path_ctl_host);
+      sk->path_ctl_host = nullptr;
+    }
+    if (sk->path_ctl_host == nullptr) {
+      MIHS_CUDA_TRY(cudaMallocHost(&sk->path_ctl_host, sizeof(SolveCtl) * (size_t)nlambda));
+      sk->path_ctl_cap = nlambda;
+    }
+  }
+  for (int l0 = 0; l0 < nlambda; l0 += 16) {
+    const int nl = nlambda - l0 < 16 ? nlambda - l0 : 16;
+    PathScalars ps = {};
+    ps.nl = nl;
+    for (int l = 0; l < nl; ++l) {
+      const double lam = lambdas[l0 + l];
+      double sd = sds != nullptr ? sds[l0 + l] : 0.0;
+      if (!(sd > 0.0)) {  // Algorithm 4 on SA (T = 2, ε_tr = 0.5), capped below m
+        rc = estimate_sd(sk->SA, sk->m, sk->d, sk->dp, lam, 2, 0.5, sk->seed ^ 0x4855544348ull, &sd, s);
+        if (rc) return rc;
+        if (!(sd > 0.0)) sd = 1.0;
+        if (sd > 0.95 * (double)sk->m) sd = 0.95 * (double)sk->m;
+      }
+      const double beta = sd / (double)sk->m;  // Corollary 3
+      ps.lam[l] = (float)lam;
+      ps.beta[l] = (float)beta;
+      ps.alpha[l] = (float)((1.0 - beta) * (1.0 - beta));
+    }
+    float* Xg = X + (size_t)l0 * ldx;
+    path_init_kernel<<<1, 32, 0, s>>>(sk->path_ctl, sk->path_cnt, nl, opts->max_outer, (float)opts->tol);
+    MIHS_CHECK_LAUNCH();
+    count_launch();
+    if (opts->warm_start) {
+      rc = launch_apass_partial(A, n, d, lda, b, nullptr, sk->partials, nullptr, s);
+      if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, d, nullptr, 0.f, sk->g, nullptr, s);
+      if (rc) return rc;
+      path_set_gnorm0_kernel<<<1, 256, 0, s>>>(sk->path_ctl, nl, sk->g, (int)d);
+      MIHS_CHECK_LAUNCH();
+      count_launch();
+    } else {
+      MIHS_CUDA_TRY(cudaMemset2DAsync(Xg, (size_t)ldx * sizeof(float), 0, (size_t)d * sizeof(float), nl, s));
+    }
+    MIHS_CUDA_TRY(cudaMemcpy2DAsync(sk->path_xprev, (size_t)sk->dp * sizeof(float), Xg, (size_t)ldx * sizeof(float),
+                                    (size_t)d * sizeof(float), nl, cudaMemcpyDeviceToDevice, s));
+    AabLaunch a = {};
+    a.SA = sk->SA;
+    a.m = (int)sk->m;
+    a.d = (int)d;
+    a.ldsa = sk->dp;
+    a.g = sk->path_g;
+    a.eps = (float)opts->eps_sub;
+    a.max_passes = cap_passes(sk->m, d, opts->max_inner);
+    a.x = Xg;
+    a.x_prev = sk->path_xprev;
+    a.ctl = sk->path_ctl;
+    a.path = 1;
+    a.ps = ps;
+    a.path_ldg = sk->dp;
+    a.path_ldx = ldx;
+    a.path_ndone = sk->path_cnt;
+    a.path_all_done = sk->path_cnt + 1;
+    const mihs_sketch_s::PathKey key = {A, lda, b, Xg, ldx, ps, a.eps, a.max_passes};
+    bool graph_ran = false;
+    if (!timing_on() && !sk->path_graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
+      if (!(sk->path_exec && sk->path_key == key)) {
+        const int brc = build_while_graph(sk, (int)sk->m, (int)d, sk->path_graph, sk->path_exec,
+                                          [&](unsigned long long cond, cudaStream_t cs) {
+                                            AabLaunch b2 = a;
+                                            b2.cond = cond;
+                                            return launch_path_step(sk, key, b2, cs);
+                                          });
+        if (brc == MIHS_OK) {
+          sk->path_key = key;
+        } else {
+          if (sk->path_exec) cudaGraphExecDestroy(sk->path_exec);
+          if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
+          sk->path_exec = nullptr;
+          sk->path_graph = nullptr;
+          sk->path_graph_failed = true;  // host-driven steps from now on
+          cudaGetLastError();
+        }
+      }
+      if (sk->path_exec) {
+        MIHS_CUDA_TRY(cudaGraphLaunch(sk->path_exec, s));
+        graph_ran = true;
+      }
+    }
+    if (!graph_ran) {
+      const bool poll = timing_on();
+      for (int it = 0; it <= opts->max_outer; ++it) {
+        rc = launch_path_step(sk, key, a, s);
+        if (rc) return rc;
+        if (poll) {
+          int flag = 0;
+          MIHS_CUDA_TRY(cudaMemcpyAsync(&flag, sk->path_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+          MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+          if (flag) break;
+        }
+      }
+    }
+    if (want_info)
+      MIHS_CUDA_TRY(cudaMemcpyAsync(sk->path_ctl_host + l0, sk->path_ctl, sizeof(SolveCtl) * (size_t)nl,
+                                    cudaMemcpyDeviceToHost, s));
+  }
+  return MIHS_OK;
+}
+
+// Fills infos[0..nlambda) from the handle's host copies (after a sync) and
+// returns the worst status.
+static int path_infos(mihs_sketch_t sk, int nlambda, mihs_info* infos) {
+  int worst = MIHS_OK;
+  for (int l = 0; l < nlambda; ++l) {
+    const SolveCtl& c = sk->path_ctl_host[l];
+    infos[l].outer_iters = c.outer;
+    infos[l].inner_iters_total = c.inner_total;
+    infos[l].rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
+    infos[l].status = c.done ? c.status : MIHS_NOT_CONVERGED;
+    if (infos[l].status < 0) worst = infos[l].status;
+    else if (worst == MIHS_OK && infos[l].status != MIHS_OK) worst = infos[l].status;
+  }
+  return worst;
+}
+
+int mihs_gradient_path(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, int nl,
+                       const double* lambdas, const float* X, int64_t ldx, float* G, int64_t ldg, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_gradient_path");
+  if (rc) return rc;
+  MIHS_ARG(b != nullptr && X != nullptr && G != nullptr && lambdas != nullptr, "mihs_gradient_path: null argument");
+  MIHS_ARG(nl >= 1 && nl <= 16, "mihs_gradient_path: nl=%d must be in 1..16", nl);
+  MIHS_ARG(ldx >= d && ldg >= d, "mihs_gradient_path: ldx and ldg must be >= d");
+  if (d > apass_path_max_d()) {
+    set_error("mihs_gradient_path: d=%lld > %d is not supported", (long long)d, apass_path_max_d());
+    return MIHS_ERR_UNSUPPORTED;
+  }
+  PathScalars ps = {};
+  ps.nl = nl;
+  for (int l = 0; l < nl; ++l) {
+    MIHS_ARG(lambdas[l] >= 0.0 && std::isfinite(lambdas[l]), "mihs_gradient_path: lambda[%d] must be >= 0", l);
+    ps.lam[l] = (float)lambdas[l];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = apass_path_num_partials(n);
+  StreamScratch scratch;
+  rc = scratch.alloc(sizeof(float) * (size_t)P * 16 * apass_dpad(d), s);
+  if (rc) return rc;
+  float* part = static_cast<float*>(scratch.p);
+  rc = launch_apass_path(A, n, d, lda, b, X, ldx, nl, part, nullptr, s);
+  if (rc) return rc;
+  return launch_apass_path_finalize(part, P, d, X, ldx, ps, G, ldg, nullptr, s);
+}
+
+int mihs_solve_path(mihs_sketch_t sk, const float* A, int64_t lda, const float* b, int nlambda,
+                    const double* lambdas, const double* sds, const mihs_opts* opts, float* X, int64_t ldx,
+                    mihs_info* infos, void* stream) {
+  set_error("");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int rc = path_enqueue(sk, A, lda, b, nlambda, lambdas, sds, opts, X, ldx, infos != nullptr, s);
+  if (rc || infos == nullptr) return rc;
+  MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+  return path_infos(sk, nlambda, infos);
+}
+
+int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const double* lambdas,
+                       const double* sds, const mihs_opts* opts, mihs_info* infos, void* stream) {
+  set_error("");
+  MIHS_ARG(nprob >= 0 && (nprob == 0 || probs != nullptr), "mihs_solve_batched: bad problem array");
+  for (int i = 0; i < nprob; ++i)
+    for (int j = 0; j < i; ++j)
+      MIHS_ARG(probs[i].sk != probs[j].sk, "mihs_solve_batched: problems %d and %d share a handle", j, i);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Independent problems run on a few internal streams forked from and
+  // joined back into the caller's stream.
+  constexpr int kStreams = 4;
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> pool;  // per device
+  static std::vector<std::vector<cudaEvent_t>> evs;
+  int dev = 0;
+  MIHS_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> ev;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)pool.size() <= dev) {
+      pool.resize(dev + 1);
+      evs.resize(dev + 1);
+    }
+    if (pool[dev].empty()) {
+      for (int k = 0; k < kStreams; ++k) {
+        cudaStream_t t;
+        cudaEvent_t e;
+        MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        pool[dev].push_back(t);
+        evs[dev].push_back(e);
+      }
+      cudaEvent_t e;
+      MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      evs[dev].push_back(e);  // the fork event
+    }
+    st = pool[dev];
+    ev = evs[dev];
+  }
+  MIHS_CUDA_TRY(cudaEventRecord(ev[kStreams], s));
+  for (int k = 0; k < kStreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kStreams], 0));
+  int rc = MIHS_OK;
+  for (int i = 0; i < nprob && rc == MIHS_OK; ++i) {
+    const mihs_problem& q = probs[i];
+    rc = path_enqueue(q.sk, q.A, q.lda, q.b, nlambda, lambdas, sds != nullptr ? sds + (size_t)i * nlambda : nullptr,
+                      opts, q.X, q.ldx, infos != nullptr, st[i % kStreams]);
+    if (rc) set_error("mihs_solve_batched: problem %d: %s", i, mihs_last_error());
+  }
+  for (int k = 0; k < kStreams; ++k) {
+    MIHS_CUDA_TRY(cudaEventRecord(ev[k], st[k]));
+    MIHS_CUDA_TRY(cudaStreamWaitEvent(s, ev[k], 0));
+  }
+  if (rc || infos == nullptr) return rc;
+  MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+  int worst = MIHS_OK;
+  for (int i = 0; i < nprob; ++i) {
+    const int w = path_infos(probs[i].sk, nlambda, infos + (size_t)i * nlambda);
+    if (w < 0) worst = w;
+    else if (worst == MIHS_OK && w != MIHS_OK) worst = w;
+  }
+  return worst;
 }
 
 int mihs_gradient_refined(const float* A, int64_t n, int64_t d, int64_t lda, const float* b,

@@ -29,6 +29,25 @@ int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const SolveCtl* ctl, cudaStream_t s, int gate = -1,
                           const float* rhs = nullptr);
 
+// ---- λ-path gradient (apass_path.cu) ---------------------------------------
+// Per-λ scalars of a path solve (passed by value to the kernels).
+struct PathScalars {
+  int nl;              // λ values in use (≤ 16)
+  float lam[16], alpha[16], beta[16];
+};
+int apass_path_num_partials(int64_t n);
+int apass_path_max_d();
+// partials[p][l][j] (p < P, l < 16, row pitch dpad) = Σ_{rows of block p}
+// A[i][j]·(b[i] − A[i]·X[l]) for l < nl; X λ-major with row pitch ldx.  Skips
+// all work when *all_done (may be NULL).
+int launch_apass_path(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const float* X,
+                      int64_t ldx, int nl, float* partials, const int* all_done, cudaStream_t s);
+// G[l][j] = Σ_p partials[p][l][j] − λ_l·X[l][j] (fixed order), G λ-major (ldg).
+int launch_apass_path_finalize(const float* partials, int P, int64_t d, const float* X, int64_t ldx,
+                               const PathScalars& sc, float* G, int64_t ldg, const int* all_done,
+                               cudaStream_t s);
+int apass_path_device_error(int* code);
+
 // ---- gradients of the solution (backward.cu) ------------------------------
 // dlambda = −xᵀv (fp64); db = Av; dA = r vᵀ − (Av) xᵀ with r = b − Ax.  Any of
 // dA, db, dlambda may be NULL; b may be NULL only when dA is.
@@ -68,6 +87,15 @@ struct AabLaunch {
   SolveCtl* ctl;       // solve mode (stop test, counters); may be NULL
   float* hist;         // solve mode: ‖g‖ of every gradient step (kHistCap entries); may be NULL
   unsigned long long cond;  // graph conditional handle to clear when the solve stops (0: none)
+  // λ-path mode (path != 0): one cluster per λ_l (l < ps.nl) with g, x, x⁻
+  // and ctl offset by l (g and x⁻ pitch path_ldg, x pitch path_ldx), the
+  // scalars from ps; *path_ndone counts stopped λ and the last one sets
+  // *path_all_done and clears cond.  delta, passes, hist and x64 unused.
+  int path;
+  PathScalars ps;
+  int64_t path_ldg, path_ldx;
+  int* path_ndone;
+  int* path_all_done;
 };
 int launch_aab(const AabLaunch& a, cudaStream_t s);
 // Picks and caches the cluster shape for (m, d) (call outside stream capture).
@@ -94,7 +122,7 @@ int estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lamb
                 uint64_t seed, double* sd_out, cudaStream_t s);
 
 // ---- per-kernel event timing (api.cu) -------------------------------------
-enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kTimerBackward = 4, kNumTimers = 5 };
+enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kTimerBackward = 4, kTimerApassPath = 5, kNumTimers = 6 };
 bool timing_on();
 void timing_begin(int which, cudaStream_t s);
 void timing_end(int which, cudaStream_t s);

@@ -20,6 +20,7 @@ from . import _build
 GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
 FAMILIES = {"gaussian": GAUSSIAN, "countsketch": COUNTSKETCH, "srht": SRHT}
 OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC, UNSUPPORTED = -1, -2, -3, -4, -5, -6
 
 
 class MihsError(RuntimeError):
@@ -32,6 +33,11 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("eps_sub", ctypes.c_double), ("max_inner", ctypes.c_int),
                 ("sd", ctypes.c_double), ("warm_start", ctypes.c_int)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("sk", ctypes.c_void_p), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("b", ctypes.c_void_p), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
@@ -84,6 +90,10 @@ def lib() -> ctypes.CDLL:
         "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
                               ctypes.POINTER(_Info), _vp]),
         "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "mihs_gradient_path": (_int, [_vp, _i64, _i64, _i64, _vp, _int, _vp, _vp, _i64, _vp, _i64, _vp]),
+        "mihs_solve_path": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp, ctypes.POINTER(_Opts), _vp, _i64, _vp,
+                                   _vp]),
+        "mihs_solve_batched": (_int, [_int, _vp, _int, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp]),
         "mihs_backward_refined": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp,
                                          _i64, _vp, _vp, ctypes.POINTER(_Info), _vp]),
         "mihs_backward": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _i64,
@@ -137,7 +147,7 @@ def launch_count() -> int:
     return int(lib().mihs_launch_count())
 
 
-TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD, TIMER_BACKWARD = 0, 1, 2, 3, 4
+TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD, TIMER_BACKWARD, TIMER_APASS_PATH = 0, 1, 2, 3, 4, 5
 
 
 def timing(on: bool) -> None:
@@ -259,6 +269,66 @@ def backward_grads(A: torch.Tensor, b: torch.Tensor | None, x: torch.Tensor, v: 
                                      db.data_ptr() if db is not None else None,
                                      dl.data_ptr() if dl is not None else None, _stream(stream)))
     return dA, db, dl
+
+
+def _dbl_array(vals):
+    vals = [float(v) for v in vals]
+    return (ctypes.c_double * len(vals))(*vals), len(vals)
+
+
+def gradient_path(A: torch.Tensor, b: torch.Tensor, X: torch.Tensor, lambdas, G: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """G_l = Aᵀ(b − A·X_l) − λ_l·X_l for the rows X_l of the λ-major X (nl × d),
+    in one pass over A (mihs_gradient_path)."""
+    pa, n, d, lda = _mat(A, "A")
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == d and X.stride(1) == 1):
+        raise ValueError("X must be a CUDA fp32 nl x d matrix with unit column stride")
+    lam, nl = _dbl_array(lambdas)
+    if nl != X.shape[0]:
+        raise ValueError("one λ per row of X")
+    if G is None:
+        G = torch.empty(nl, d, dtype=torch.float32, device=A.device)
+    _check(lib().mihs_gradient_path(pa, n, d, lda, _vec(b, n, "b"), nl, lam, X.data_ptr(), X.stride(0),
+                                    G.data_ptr(), G.stride(0), _stream(stream)))
+    return G
+
+
+def _infos(arr, k):
+    return [SolveInfo(arr[i].outer_iters, arr[i].inner_iters_total, arr[i].rel_resid, arr[i].status)
+            for i in range(k)]
+
+
+def _path_opts(tol, max_outer, eps_sub, max_inner, warm_start):
+    o = lib().mihs_default_opts()
+    o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+    o.max_inner, o.warm_start = int(max_inner), int(bool(warm_start))
+    return o
+
+
+def solve_batched(problems, lambdas, sds=None, tol: float = 1e-6, max_outer: int = 100, eps_sub: float = 0.1,
+                  max_inner: int = 0, warm_start: bool = False, want_info: bool = True, stream=None):
+    """mihs_solve_batched: `problems` is a list of (Sketch, A, b, X) with X a
+    λ-major nl × d CUDA tensor per problem; sds (optional) is nprob × nl.
+    Returns a list (per problem) of lists (per λ) of SolveInfo, or None."""
+    lam, nl = _dbl_array(lambdas)
+    arr = (_Problem * len(problems))()
+    for i, (sk, A, b, X) in enumerate(problems):
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (sk.n, sk.d) or tuple(X.shape) != (nl, d) or X.stride(1) != 1:
+            raise ValueError(f"problem {i}: shapes do not match")
+        arr[i] = _Problem(sk._h.value, pa, lda, _vec(b, n, "b"), X.data_ptr(), X.stride(0))
+    sd_arr = None
+    if sds is not None:
+        flat = [float(v) for row in sds for v in row]
+        sd_arr = (ctypes.c_double * len(flat))(*flat)
+    o = _path_opts(tol, max_outer, eps_sub, max_inner, warm_start)
+    infos = (_Info * (len(problems) * nl))() if want_info else None
+    rc = lib().mihs_solve_batched(len(problems), arr, nl, lam, sd_arr, ctypes.byref(o), infos, _stream(stream))
+    _check(rc, allow_not_converged=True)
+    if not want_info:
+        return None
+    flat = _infos(infos, len(problems) * nl)
+    return [flat[i * nl:(i + 1) * nl] for i in range(len(problems))]
 
 
 @dataclass
@@ -400,6 +470,28 @@ class Sketch:
         _check(rc, allow_not_converged=True)
         si = SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status) if want_info else None
         return dA, db, dl, v, si
+
+    def solve_path(self, A: torch.Tensor, b: torch.Tensor, lambdas, sds=None, tol: float = 1e-6,
+                   max_outer: int = 100, eps_sub: float = 0.1, max_inner: int = 0,
+                   X: torch.Tensor | None = None, warm_start: bool = False, want_info: bool = True,
+                   stream=None):
+        """Algorithm 1 for every λ of `lambdas` with this sketch (mihs_solve_path).
+        Returns (X, [SolveInfo] or None) with X λ-major (nl × d)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        lam, nl = _dbl_array(lambdas)
+        if X is None:
+            X = torch.empty(nl, d, dtype=torch.float32, device=A.device)
+        if not (X.is_cuda and X.dtype == torch.float32 and tuple(X.shape) == (nl, d) and X.stride(1) == 1):
+            raise ValueError("X must be a CUDA fp32 nl x d matrix with unit column stride")
+        sd_arr = _dbl_array(sds)[0] if sds is not None else None
+        o = _path_opts(tol, max_outer, eps_sub, max_inner, warm_start)
+        infos = (_Info * nl)() if want_info else None
+        rc = lib().mihs_solve_path(self._h, pa, lda, _vec(b, n, "b"), nl, lam, sd_arr, ctypes.byref(o),
+                                   X.data_ptr(), X.stride(0), infos, _stream(stream))
+        _check(rc, allow_not_converged=True)
+        return X, (_infos(infos, nl) if want_info else None)
 
     def history(self):
         """Relative residual ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step of the last solve."""
