@@ -101,15 +101,18 @@ def _haar(d: int, gen: torch.Generator) -> torch.Tensor:
 def make_problem(n: int, d: int, sigma: np.ndarray, lam: float, snr_db: float,
                  seed: int, m: int | None = None, sd_factor: float = 4.0,
                  name: str = "custom", device: str = "cpu",
-                 chunk_rows: int = 1 << 15) -> RidgeProblem:
+                 chunk_rows: int = 1 << 15, device_rng: bool = False) -> RidgeProblem:
     """Build ``A = G diag(σ) Vᵀ/√n`` and ``b = A x0 + ω`` (see module doc).
 
     Random draws come from a CPU ``torch.Generator`` seeded with ``seed`` so the
     bytes do not depend on the device; the n×d×d product runs on ``device``
     (fp64 on CPU, fp32 without TF32 on CUDA) in row chunks.  Tensors are
-    returned on ``device``.
+    returned on ``device``.  With ``device_rng`` (CUDA only) the n×d Gaussian
+    G is drawn by a CUDA generator seeded with ``seed`` instead (much faster
+    for multi-GB batches; the bytes then depend on the torch build).
     """
     gen = torch.Generator(device="cpu").manual_seed(int(seed))
+    dgen = torch.Generator(device=device).manual_seed(int(seed)) if device_rng else None
     sigma = np.asarray(sigma, dtype=np.float64)
     assert sigma.shape == (d,)
     V = _haar(d, gen)
@@ -125,7 +128,10 @@ def make_problem(n: int, d: int, sigma: np.ndarray, lam: float, snr_db: float,
     try:
         for r0 in range(0, n, chunk_rows):
             r1 = min(n, r0 + chunk_rows)
-            G = torch.randn(r1 - r0, d, generator=gen, dtype=torch.float32)
+            if dgen is not None:
+                G = torch.randn(r1 - r0, d, generator=dgen, dtype=torch.float32, device=device)
+            else:
+                G = torch.randn(r1 - r0, d, generator=gen, dtype=torch.float32)
             A[r0:r1] = (G.to(device=device, dtype=cdt) @ M).to(torch.float32)
     finally:
         if on_cuda:
@@ -171,6 +177,31 @@ def problem_differentiable(device: str = "cpu", seed: int = 1004,
     sigma = profile_polynomial(d, 1.5)
     return make_problem(n, d, sigma, 1e-4, 40.0, seed,
                         name=f"ridge-{n}x{d}-poly1.5-lam1e-4", device=device)
+
+
+def batch_lambda_path(device: str = "cpu", seed: int = 1003, count: int = 64, nlambda: int = 16,
+                      n_range=(8192, 262144), d_choices=(64, 128, 256, 512, 1024),
+                      device_rng: bool = False):
+    """The batched λ-path workload: `count` matrices with n log-uniform in
+    n_range (a multiple of 16), d uniform over d_choices, σ_i =
+    10^(−r(i−1)/(d−1)) with r ~ U[2, 6], 30 dB SNR; one log-spaced path of
+    `nlambda` values in [1e-6, 1e-1] shared by all; per matrix
+    m = min(4·sd(λ_min), n) rounded up to a multiple of 4 and sd(λ_l) from
+    the nominal profile.  Returns (problems, lambdas, sds) with sds[i][l]."""
+    rng = np.random.default_rng(int(seed))
+    lams = list(np.logspace(-6, -1, nlambda))
+    probs, sds = [], []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1]))) / 16.0)) * 16
+        d = int(rng.choice(d_choices))
+        r = float(rng.uniform(2.0, 6.0))
+        sigma = profile_exponential(d, r)
+        sd_row = [nominal_sd(sigma, l) for l in lams]
+        m = min(n, round_up(4.0 * max(sd_row), 4))
+        probs.append(make_problem(n, d, sigma, lams[0], 30.0, int(seed) * 1000 + i, m=m,
+                                  name=f"path-{i}-{n}x{d}-exp{r:.2f}", device=device, device_rng=device_rng))
+        sds.append(sd_row)
+    return probs, lams, sds
 
 
 def problem_scaled(n: int, d: int, seed: int, decades: float = 4.0,
