@@ -298,6 +298,10 @@ int mihs_gradient_path(const float* A, int64_t n, int64_t d, int64_t lda,
  *            synchronises and returns the worst status.
  * λ values are processed in groups of 16 (one device-side graph loop per
  * group, cached in the handle).  d ≤ 1024 (MIHS_ERR_UNSUPPORTED beyond).
+ * Each step runs AAb_Solver as one thread-block cluster per λ; with the
+ * environment variable MIHS_PATH_AAB=grid, as one cooperative grid for all λ
+ * that holds SA in the shared memory of up to every SM (when it fits).  Do
+ * not run two path solves at the same time on different streams.
  * The first path solve on a handle allocates its workspace (cudaMalloc). */
 int mihs_solve_path(mihs_sketch_t sk, const float* A, int64_t lda,
                     const float* b, int nlambda, const double* lambdas,
@@ -316,8 +320,8 @@ typedef struct {
 } mihs_problem;
 
 /* mihs_solve_path for nprob independent problems sharing one λ list:
- * the problems run concurrently on internal streams forked from and joined
- * back into `stream`.  sds: HOST nprob × nlambda (row i for problem i) or
+ * the problems run concurrently on four internal streams (one with
+ * MIHS_PATH_AAB=grid) forked from and joined back into `stream`.  sds: HOST nprob × nlambda (row i for problem i) or
  * NULL; infos: HOST nprob × nlambda or NULL (then no synchronisation).
  * Every problem must have its own handle.  Returns the worst status. */
 int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda,

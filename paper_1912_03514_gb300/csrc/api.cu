@@ -213,6 +213,7 @@ struct mihs_sketch_s {
   // (P_path × 16 × dp), G and X⁻ (16 × dp each), 16 control blocks and the
   // path's stop counter / flag.
   float* path_partials = nullptr;
+  float* path_aab_ws = nullptr;  // global scratch of the cooperative multi-λ AAb kernel
   float* path_g = nullptr;
   float* path_xprev = nullptr;
   SolveCtl* path_ctl = nullptr;
@@ -330,8 +331,18 @@ int launch_path_step(mihs_sketch_s* sk, const mihs_sketch_s::PathKey& k, const A
   int rc = launch_apass_path(k.A, sk->n, sk->d, k.lda, k.b, k.X, k.ldx, k.ps.nl, sk->path_partials, all_done, s);
   if (!rc) rc = launch_apass_path_finalize(sk->path_partials, sk->P_path, sk->d, k.X, k.ldx, k.ps, sk->path_g,
                                            sk->dp, all_done, s);
-  if (!rc) rc = launch_aab(a, s);
-  return rc;
+  if (rc) return rc;
+  // One thread-block cluster per λ (default), or all λ in one cooperative
+  // grid with SA spread over the SMs' shared memory (MIHS_PATH_AAB=grid).
+  // Both are latency-bound per pass; measured on GB300 the cluster form was
+  // faster (the grid form pays two grid-wide barriers per pass and keeps
+  // computing every λ until the slowest inner solve ends).
+  const char* env = std::getenv("MIHS_PATH_AAB");
+  if (env != nullptr && std::strcmp(env, "grid") == 0) {
+    rc = launch_aab_path(a, sk->path_aab_ws, s);
+    if (rc != MIHS_ERR_UNSUPPORTED) return rc;
+  }
+  return launch_aab(a, s);
 }
 
 }  // namespace
@@ -359,7 +370,7 @@ uint64_t mihs_launch_count(void) { return g_launches.load(); }
 int mihs_device_status(int* code) {
   set_error("");
   MIHS_ARG(code != nullptr, "mihs_device_status: null code");
-  int a = 0, g = 0, dd = 0, pa = 0;
+  int a = 0, g = 0, dd = 0, pa = 0, ab = 0;
   int rc = apass_device_error(&a);
   if (rc) return rc;
   rc = gauss_tc_device_error(&g);
@@ -368,7 +379,9 @@ int mihs_device_status(int* code) {
   if (rc) return rc;
   rc = apass_path_device_error(&pa);
   if (rc) return rc;
-  *code = a ? a : (g ? g : (dd ? dd : pa));
+  rc = aab_path_device_error(&ab);
+  if (rc) return rc;
+  *code = a ? a : (g ? g : (dd ? dd : (pa ? pa : ab)));
   return MIHS_OK;
 }
 
@@ -866,7 +879,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
   }
   if (sk->path_partials == nullptr) {
     sk->P_path = apass_path_num_partials(n);
-    const size_t fl = (size_t)sk->P_path * 16 * sk->dp + 2 * 16 * (size_t)sk->dp;
+    const size_t fl = (size_t)sk->P_path * 16 * sk->dp + 2 * 16 * (size_t)sk->dp + aab_path_ws_floats((int)sk->dp);
     const size_t bytes = fl * sizeof(float) + 16 * sizeof(SolveCtl) + 4 * sizeof(int);
     char* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -877,6 +890,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
     sk->path_partials = reinterpret_cast<float*>(p);
     sk->path_g = sk->path_partials + (size_t)sk->P_path * 16 * sk->dp;
     sk->path_xprev = sk->path_g + 16 * (size_t)sk->dp;
+    sk->path_aab_ws = sk->path_xprev + 16 * (size_t)sk->dp;
     sk->path_ctl = reinterpret_cast<SolveCtl*>(p + fl * sizeof(float));
     sk->path_cnt = reinterpret_cast<int*>(sk->path_ctl + 16);
   }
@@ -1051,9 +1065,13 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
     for (int j = 0; j < i; ++j)
       MIHS_ARG(probs[i].sk != probs[j].sk, "mihs_solve_batched: problems %d and %d share a handle", j, i);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Independent problems run on a few internal streams forked from and
-  // joined back into the caller's stream.
+  // Independent problems run on internal streams forked from and joined back
+  // into the caller's stream: four of them, or one when the path steps use
+  // the cooperative grid form (two such grids must never wait for each
+  // other's blocks, so they are not run concurrently).
   constexpr int kStreams = 4;
+  const char* env = std::getenv("MIHS_PATH_AAB");
+  const int nstreams = (env != nullptr && std::strcmp(env, "grid") == 0) ? 1 : kStreams;
   static std::mutex mu;
   static std::vector<std::vector<cudaStream_t>> pool;  // per device
   static std::vector<std::vector<cudaEvent_t>> evs;
@@ -1084,15 +1102,15 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
     ev = evs[dev];
   }
   MIHS_CUDA_TRY(cudaEventRecord(ev[kStreams], s));
-  for (int k = 0; k < kStreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kStreams], 0));
+  for (int k = 0; k < nstreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kStreams], 0));
   int rc = MIHS_OK;
   for (int i = 0; i < nprob && rc == MIHS_OK; ++i) {
     const mihs_problem& q = probs[i];
     rc = path_enqueue(q.sk, q.A, q.lda, q.b, nlambda, lambdas, sds != nullptr ? sds + (size_t)i * nlambda : nullptr,
-                      opts, q.X, q.ldx, infos != nullptr, st[i % kStreams]);
+                      opts, q.X, q.ldx, infos != nullptr, st[i % nstreams]);
     if (rc) set_error("mihs_solve_batched: problem %d: %s", i, mihs_last_error());
   }
-  for (int k = 0; k < kStreams; ++k) {
+  for (int k = 0; k < nstreams; ++k) {
     MIHS_CUDA_TRY(cudaEventRecord(ev[k], st[k]));
     MIHS_CUDA_TRY(cudaStreamWaitEvent(s, ev[k], 0));
   }

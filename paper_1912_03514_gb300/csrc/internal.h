@@ -98,6 +98,13 @@ struct AabLaunch {
   int* path_all_done;
 };
 int launch_aab(const AabLaunch& a, cudaStream_t s);
+// λ-path mode with all λ in one cooperative grid that keeps SA in the
+// shared memory of all SMs (aab_path.cu); `ws` holds aab_path_ws_floats(dp)
+// floats.  Returns MIHS_ERR_UNSUPPORTED (nothing launched) when SA or d does
+// not fit, so that the caller can use launch_aab's one-cluster-per-λ form.
+size_t aab_path_ws_floats(int dp);
+int aab_path_device_error(int* code);
+int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s);
 // Picks and caches the cluster shape for (m, d) (call outside stream capture).
 void aab_prepare(int m, int d);
 

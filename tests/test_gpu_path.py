@@ -58,8 +58,16 @@ def _certified(A, b, lam, x, xs):
     return np.linalg.norm(x - xs) <= np.linalg.norm(r) / lam * (1 + 1e-9) + 1e-300, np.linalg.norm(r)
 
 
+@pytest.fixture(params=["grid", "cluster"])
+def aab_form(request, monkeypatch):
+    """Both AAb forms of a path step: one thread-block cluster per λ (default)
+    and all λ in one cooperative grid."""
+    monkeypatch.setenv("MIHS_PATH_AAB", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("family", ["gaussian", "countsketch", "srht"])
-def test_path_solve_matches_oracle(family):
+def test_path_solve_matches_oracle(family, aab_form):
     p = W.problem_small()
     A, b = p.A.to(DEV), p.b.to(DEV)
     lams = list(np.logspace(-3, -1, 16))
@@ -83,7 +91,7 @@ def test_path_solve_matches_oracle(family):
     assert np.linalg.norm(Xn[5] - x5.cpu().double().numpy()) <= 2e-4 * np.linalg.norm(XS[5])
 
 
-def test_path_estimated_sd_and_groups_of_16():
+def test_path_estimated_sd_and_groups_of_16(aab_form):
     """sd from Algorithm 4 per λ, and 20 λ (two groups of the path loop)."""
     p = W.problem_scaled(8192, 128, seed=31)
     A, b = p.A.to(DEV), p.b.to(DEV)
@@ -99,7 +107,7 @@ def test_path_estimated_sd_and_groups_of_16():
         assert _certified(An, bn, lams[l], Xn[l], XS[l])[0]
 
 
-def test_path_warm_start_and_determinism():
+def test_path_warm_start_and_determinism(aab_form):
     p = W.problem_small()
     A, b = p.A.to(DEV), p.b.to(DEV)
     lams = list(np.logspace(-2.5, -1, 8))
@@ -113,7 +121,7 @@ def test_path_warm_start_and_determinism():
     assert torch.equal(X3, X1)
 
 
-def test_solve_batched_matches_oracle():
+def test_solve_batched_matches_oracle(aab_form):
     probs = [W.problem_small(seed=1000),
              W.problem_scaled(3000, 100, seed=41),
              W.problem_scaled(16384, 512, seed=42, sd_frac=0.1)]
@@ -156,3 +164,30 @@ def test_path_invalid_arguments():
         X = torch.empty(1, 64, device=DEV)
         with pytest.raises(mihs.MihsError):
             mihs.solve_batched([(sk, A, b, X), (sk, A, b, X)], [0.1], sds=[[4.0], [4.0]])
+
+
+def test_path_wide_sketch_grid_matches_cluster():
+    """A sketch too large for one cluster (m = 2048, d = 1024: 8 MB of SA):
+    the cooperative grid form and the cluster form reach the same solutions
+    (both within the oracle's certificate)."""
+    import os
+    q = W.problem_scaled(16384, 1024, seed=55, decades=3.0, sd_frac=0.5)
+    A, b = q.A.to(DEV), q.b.to(DEV)
+    lams = list(np.logspace(-3, -1, 16))
+    sds = [W.nominal_sd(q.sigma, l) for l in lams]
+    m = 2048
+    out = {}
+    for form in ("grid", "cluster"):
+        os.environ["MIHS_PATH_AAB"] = form
+        try:
+            with mihs.Sketch(A, "countsketch", m, seed=8) as sk:
+                X, infos = sk.solve_path(A, b, lams, sds=sds, tol=1e-6, max_outer=200)
+        finally:
+            os.environ.pop("MIHS_PATH_AAB", None)
+        assert all(i.converged for i in infos), (form, infos)
+        out[form] = X.cpu().double().numpy()
+    An, bn = q.A.double().numpy(), q.b.double().numpy()
+    XS = o.ridge_path(An, bn, lams)
+    for form, Xn in out.items():
+        for l in range(len(lams)):
+            assert _certified(An, bn, lams[l], Xn[l], XS[l])[0], (form, l)
