@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched λ-path leg")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
-    ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "aab", "aab-late", "gaussian",
+    ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "gaussian",
                                             "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
@@ -585,6 +585,7 @@ def run_batched(args, dev, ws, peaks, peak_src):
 
 def run_profile_op(args, local):
     """W + K launches of one operation on the workload, timed with CUDA events."""
+    import numpy as np
     import torch
 
     from paper_1912_03514_gb300 import mihs
@@ -609,6 +610,17 @@ def run_profile_op(args, local):
     elif op == "apass-dd":
         x64, g64 = x.double(), torch.empty(p.d, device=dev, dtype=torch.float64)
         fn = lambda: mihs.gradient_refined(A, b, x64, p.lam, g=g64)
+    elif op == "path":
+        # one λ-path solve (16 λ in [1e-6, 1e-1]) on an exponential profile of 3
+        # decades with m = 4·sd(λ_min): the shape of the batched workload's
+        # widest sketches (the AAb form follows MIHS_PATH_AAB)
+        q = W.problem_scaled(args.n, args.d, seed=5, decades=3.0, sd_frac=0.9, device=str(dev))
+        lams = list(np.logspace(-6, -1, 16))
+        sds = [W.nominal_sd(q.sigma, l) for l in lams]
+        m = min(q.n, int(np.ceil(max(sds))) * 4)
+        skp = mihs.Sketch(q.A, "gaussian", m, seed=3)
+        Xp = torch.empty(16, q.d, device=dev)
+        fn = lambda: skp.solve_path(q.A, q.b, lams, sds=sds, tol=1e-6, max_outer=100, X=Xp, want_info=False)
     elif op == "backward":
         v = W.randn((p.d,), seed=6, scale=0.01).to(dev)
         fn = lambda: mihs.backward_grads(A, b, x, v)
