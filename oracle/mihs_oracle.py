@@ -26,6 +26,10 @@ Contents and the passage each follows:
   theorem1_params ...... β*, α*, rate of Theorem 1.
   mihs ................. Algorithm 1 (M-IHS for n ≥ d).
   hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
+  quantize_sa .......... storage of SA in bf16, or fp8 e4m3 with one scale per
+                          128 × 128 tile (a format, not the paper's: the
+                          sketch only preconditions, Section 3.1); torch's
+                          CPU casts are the rounding step.
   ridge_path ........... x*(λ) for every λ of a path (the plain definition
                           per λ; Algorithm 1 applied to each λ on its own).
   ridge_backward ....... gradients of x*(A, b, λ) through the normal equations
@@ -293,6 +297,34 @@ def stat_dim(sigma, lam):
 
 def stat_dim_of(A, lam):
     return stat_dim(np.linalg.svd(np.asarray(A, dtype=np.float64), compute_uv=False), lam)
+
+
+def quantize_sa(SA, prec: str):
+    """Quantised SA and its decoded fp64 values.  'bf16': round to nearest
+    even.  'fp8': per 128 × 128 tile, scale = max|SA|/448 in fp32 (1 for a zero
+    tile), q = e4m3(SA/scale) (fp32 division, round to nearest even; the
+    largest magnitude maps to 448 exactly or rounds to it).  Returns
+    (q as a torch tensor, scales (fp32 array, tile rows × tile cols) or None,
+    decoded fp64 array)."""
+    import torch
+    SA32 = torch.as_tensor(np.asarray(SA, dtype=np.float32))
+    m, d = SA32.shape
+    if prec == "bf16":
+        q = SA32.to(torch.bfloat16)
+        return q, None, q.to(torch.float64).numpy()
+    if prec != "fp8":
+        raise ValueError(prec)
+    T = 128
+    ntr, ntc = (m + T - 1) // T, (((d + 3) // 4) * 4 + T - 1) // T
+    scales = np.ones((ntr, ntc), dtype=np.float32)
+    for tr in range(ntr):
+        for tc in range(ntc):
+            amax = np.float32(np.max(np.abs(SA32[tr * T:(tr + 1) * T, tc * T:(tc + 1) * T].numpy()), initial=0.0))
+            scales[tr, tc] = np.float32(amax / np.float32(448.0)) if amax > 0 else np.float32(1.0)
+    S = torch.from_numpy(np.repeat(np.repeat(scales, T, axis=0), T, axis=1)[:m, :d].copy())
+    q = (SA32 / S).to(torch.float8_e4m3fn)
+    dec = q.to(torch.float64).numpy() * S.to(torch.float64).numpy()
+    return q, scales, dec
 
 
 def ridge_path(A, b, lambdas, refine: int = 2):

@@ -509,3 +509,30 @@ def test_ridge_path_against_svd_filter_factors_and_limits():
     big = 1e8
     xb = o.ridge_path(A, b, [big])[0]
     assert np.linalg.norm(big * xb - A.T @ b) <= 1e-6 * np.linalg.norm(A.T @ b)
+
+
+# ------------------------------------------------------ quantised SA storage
+def test_quantize_sa_known_values():
+    """bf16: 1 + 2⁻⁸ is a tie and rounds to even (1), 1 + 3·2⁻⁹ rounds up to
+    1 + 2⁻⁷; fp8 e4m3: in a tile whose maximum is 448·s the scale is s, the
+    maximum decodes exactly, 2⁻⁹·s (the smallest subnormal) survives and
+    2⁻¹¹·s flushes to zero, 17·s is a tie between 16 and 18 (even: 16)."""
+    SA = np.zeros((3, 5), np.float32)
+    SA[0, 0] = 1 + 2.0 ** -8
+    SA[0, 1] = 1 + 3 * 2.0 ** -9
+    SA[0, 2] = -2.5
+    q, sc, dec = o.quantize_sa(SA, "bf16")
+    assert dec[0, 0] == 1.0 and dec[0, 1] == 1 + 2.0 ** -7 and dec[0, 2] == -2.5
+    s = np.float32(0.75)
+    SA = np.zeros((130, 131), np.float32)
+    SA[0, 0] = 448 * s
+    SA[1, 1] = 2.0 ** -9 * s
+    SA[2, 2] = 2.0 ** -11 * s
+    SA[3, 3] = 17 * s
+    SA[129, 130] = -3.0  # second tile row and column: its own scale
+    q, sc, dec = o.quantize_sa(SA, "fp8")
+    assert sc.shape == (2, 2) and sc[0, 0] == np.float32(448 * s) / np.float32(448)
+    assert sc[1, 1] == np.float32(3.0) / np.float32(448) and sc[0, 1] == 1.0
+    assert dec[0, 0] == 448 * s and dec[1, 1] == 2.0 ** -9 * s and dec[2, 2] == 0.0
+    assert dec[3, 3] == 16 * s
+    assert abs(dec[129, 130] + 3.0) <= 3.0 * 2.0 ** -4  # 3 mantissa bits
