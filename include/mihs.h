@@ -57,6 +57,9 @@ enum {
  *                    counter (i, 0, 3, 0).                                  */
 enum { MIHS_GAUSSIAN = 0, MIHS_COUNTSKETCH = 1, MIHS_SRHT = 2 };
 
+/* Storage precision of SA inside AAb_Solver (arithmetic is fp32 in all). */
+enum { MIHS_SA_FP32 = 0, MIHS_SA_BF16 = 1, MIHS_SA_FP8E4M3 = 2 };
+
 /* Human-readable name of a return code (static string). */
 const char* mihs_strerror(int code);
 /* Message describing the last failure on this host thread ("" if none). */
@@ -144,6 +147,24 @@ int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa,
                    const float* g, double lambda, double eps_sub, int max_inner,
                    float* delta, int* passes, void* stream);
 
+/* Quantised copy of an SA (device memory), as mihs_sketch_set_precision
+ * stores it: out is m × ldq elements of bf16 or fp8 e4m3 (ldq ≥ d, a multiple
+ * of 16; columns ≥ d are zero); for fp8, scales receives ⌈m/128⌉ × ⌈d₄/128⌉
+ * floats (row-major, d₄ = d rounded up to 4), scale = max |SA| over the
+ * 128 × 128 tile / 448 (1 for a zero tile), q = e4m3(SA/scale) rounded to
+ * nearest even and saturated.  Errors: INVALID_ARG, CUDA. */
+int mihs_quantize_sa(const float* SA, int64_t m, int64_t d, int64_t ldsa,
+                     int sa_prec, void* out, int64_t ldq, float* scales,
+                     void* stream);
+
+/* mihs_aab_solve on a quantised SA (the output of mihs_quantize_sa): the
+ * products decode each element (times its tile scale for fp8) and run in
+ * fp32.  Same arguments and errors as mihs_aab_solve otherwise. */
+int mihs_aab_solve_q(const void* SAq, int sa_prec, const float* scales,
+                     int64_t m, int64_t d, int64_t ldq, const float* g,
+                     double lambda, double eps_sub, int max_inner,
+                     float* delta, int* passes, void* stream);
+
 /* AAb_Solver followed by the heavy-ball step of Eq. mihs1:
  *     x⁺ = x + αΔ + β(x − x⁻),  then x⁻ ← x, x ← x⁺   (in place).
  * Same arguments as mihs_aab_solve plus α, β and the DEVICE d-vectors x and
@@ -192,6 +213,17 @@ int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m,
 /* Copy the handle's SA (m×d) into the caller's DEVICE buffer `dst` with
  * leading dimension ldd ≥ d, on `stream`. */
 int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream);
+
+/* Mixed-precision inner solve: store SA for AAb_Solver in bf16 or
+ * in fp8 e4m3 with one fp32 scale per 128 × 128 tile (scale = tile max / 448)
+ * while its arithmetic stays fp32.  The sketch only preconditions Algorithm 1
+ * (its fixed point is where the exact gradient vanishes, Section 3.1), so the
+ * solution is unchanged and only the rate can be; use mihs_solve_refined for
+ * targets below the fp32 floor.  Converts the current SA now and after every
+ * mihs_resketch; the first call for a quantised precision allocates the
+ * quantised copy (cudaMalloc).  MIHS_SA_FP32 switches back.  Sd estimation
+ * (Algorithm 4) keeps using the fp32 SA.  Errors: INVALID_ARG, OOM, CUDA. */
+int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream);
 
 /* Release a handle (synchronises the device first).  NULL is a no-op. */
 int mihs_sketch_destroy(mihs_sketch_t sk);

@@ -18,467 +18,25 @@
 //     branch and the result is deterministic.
 // The d-vectors of the recursion (v, d, x) are replicated per block (O(d)
 // work, negligible next to the O(md/CL) products).
-#include <cooperative_groups.h>
-
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <tuple>
 
-#include "internal.h"
-
-namespace cg = cooperative_groups;
+#include "aab_kernel.cuh"
 
 namespace mihs {
 
+using namespace aabk;
+
+AabKernelFn aabk::kernel_for_f32(int cl, int dp) { return kernel_for_type<float>(cl, dp); }
+
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr size_t kSmemBudget = 210 * 1024;
-
-struct AabParams {
-  const float* SA;
-  int m, d, dp;        // dp = d rounded up to 4
-  long long ldsa;
-  const float* g;
-  float lambda, eps;
-  int max_passes;
-  float* delta;
-  int* passes;
-  float alpha, beta;
-  float* x;
-  float* x_prev;
-  double* x64;
-  double* x_prev64;
-  float* x32_shadow;
-  double alpha64, beta64;
-  SolveCtl* ctl;
-  float* hist;
-  unsigned long long cond;
-  int rpc;             // rows per block
-  int rpc_pad;         // rpc rounded up to 4
-  int cols_per;        // column slice per block (a power of two ≥ 4)
-  int cols_log2;
-  int sa_in_smem;
-  int sa_vec;          // SA rows may be read as float4 (ldsa % 4 == 0, 16-byte aligned)
-  int path;            // λ-path mode: cluster row blockIdx.y solves λ_y
-  PathScalars ps;
-  long long path_ldg, path_ldx;
-  int* path_ndone;
-  int* path_all_done;
-};
-
-// Deterministic block-wide sum; every thread returns the same value.
-__device__ __forceinline__ float block_sum(float v, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) t += red[w];
-  __syncthreads();
-  return t;
-}
-
-__device__ __forceinline__ float4 load4_masked(const float* row, int j, int d, bool vec = true) {
-  // j is a multiple of 4 and j < dp; columns ≥ d read as zero.
-  if (vec && j + 4 <= d) return *reinterpret_cast<const float4*>(row + j);
-  if (j + 4 <= d) return make_float4(row[j], row[j + 1], row[j + 2], row[j + 3]);
-  float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (j < d) t.x = row[j];
-  if (j + 1 < d) t.y = row[j + 1];
-  if (j + 2 < d) t.z = row[j + 2];
-  return t;
-}
-
-// Σ over the cluster of one scalar slot: lane r loads rank r's value, then a
-// fixed butterfly sums them (identical wherever it is computed).
-template <int CL>
-__device__ __forceinline__ float cluster_scalar_sum(const float* my_rank_scal, int slot) {
-  const int lane = threadIdx.x & 31;
-  float v = lane < CL ? my_rank_scal[slot] : 0.f;
-  return warp_sum(v);
-}
-
-// Fused sweep over the block's rows of SA (each row read once per pass):
-//   w_i = SA_i·v − θ·p_i            (warp all-reduce of the row dot)
-//   u  += SA_iᵀ·w_i                 (lane ℓ accumulates columns 4ℓ + 128c)
-//   ρ²_part += w_i²
-// Warp `warp` takes rows warp, warp + 8, …; v and u live in registers (CH
-// float4 per lane), the per-warp u partials are written to `wpart`.
-template <int CH>
-__device__ __forceinline__ float fused_sweep(const float* SAc, long long ldc, int nr, int d,
-                                             const float* v, const float* p, float theta,
-                                             float* w, float* wpart, int dp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 vr[CH], ur[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int j = 4 * lane + 128 * c;
-    vr[c] = j < dp ? *reinterpret_cast<const float4*>(v + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    ur[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float rsq = 0.f;
-  for (int i = warp; i < nr; i += kWarps) {
-    const float* row = SAc + (long long)i * ldc;
-    float4 a[CH];
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int j = 4 * lane + 128 * c;
-      a[c] = j < dp ? load4_masked(row, j, d) : make_float4(0.f, 0.f, 0.f, 0.f);
-      s0 = fmaf(a[c].x, vr[c].x, s0);
-      s1 = fmaf(a[c].y, vr[c].y, s1);
-      s0 = fmaf(a[c].z, vr[c].z, s0);
-      s1 = fmaf(a[c].w, vr[c].w, s1);
-    }
-    const float wi = warp_sum(s0 + s1) - theta * p[i];
-    rsq = fmaf(wi, wi, rsq);
-    if (lane == 0) w[i] = wi;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      ur[c].x = fmaf(a[c].x, wi, ur[c].x);
-      ur[c].y = fmaf(a[c].y, wi, ur[c].y);
-      ur[c].z = fmaf(a[c].z, wi, ur[c].z);
-      ur[c].w = fmaf(a[c].w, wi, ur[c].w);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int j = 4 * lane + 128 * c;
-    if (j < dp) *reinterpret_cast<float4*>(wpart + (size_t)warp * dp + j) = ur[c];
-  }
-  return rsq;  // this warp's share of ρ² (same in all lanes)
-}
-
-template <int CL, int CH>
-__global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParams P) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int d = P.d, dp = P.dp;
-  // λ-path mode: the clusters of grid row blockIdx.y solve λ_y with their own
-  // g, x, x⁻ and control block; the path's stop counter ends the graph loop
-  // once every λ has stopped.
-  const int li = P.path ? (int)blockIdx.y : 0;
-  const float* g_in = P.g + (long long)li * P.path_ldg;
-  SolveCtl* ctl_ = P.ctl != nullptr ? P.ctl + li : nullptr;
-  float* x_ = P.x != nullptr ? P.x + (long long)li * P.path_ldx : nullptr;
-  float* xprev_ = P.x_prev != nullptr ? P.x_prev + (long long)li * P.path_ldg : nullptr;
-  float* delta_ = P.path ? nullptr : P.delta;
-  int* passes_ = P.path ? nullptr : P.passes;
-  float* hist_ = P.path ? nullptr : P.hist;
-  const float lam_ = P.path ? P.ps.lam[li] : P.lambda;
-  const float alpha_ = P.path ? P.ps.alpha[li] : P.alpha;
-  const float beta_ = P.path ? P.ps.beta[li] : P.beta;
-
-  extern __shared__ float4 smem4[];
-  float* v = reinterpret_cast<float*>(smem4);  // replicated d-vectors
-  float* dv = v + dp;
-  float* xs = dv + dp;
-  float* up = xs + dp;      // this block's SAᵀw (read remotely)
-  float* zsl = up + dp;     // this block's slice of θv (read remotely)
-  float* wpart = zsl + dp;  // kWarps × dp per-warp partials of SAᵀw
-  float* p = wpart + (size_t)kWarps * dp;  // own rows
-  float* w = p + P.rpc_pad;
-  float* red = w + P.rpc_pad;  // kWarps floats
-  float* scal = red + kWarps;  // [0] θ² partial, [1] ρ² partial (read remotely), [2] broadcast
-  uint64_t* stage_bar = reinterpret_cast<uint64_t*>(scal + 6);  // 8-byte aligned slot
-  float* sa = scal + 8;        // SA rows (when kept in smem)
-
-  // Solve-mode control block: read everything before the first barrier; only
-  // rank 0 writes it, after the last barrier.
-  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1;
-  float tol = 0.f, gnorm0 = 0.f, switch_tol = 0.f;
-  if (ctl_ != nullptr) {
-    done = ctl_->done;
-    outer = ctl_->outer;
-    max_outer = ctl_->max_outer;
-    g0known = ctl_->gnorm0_known;
-    tol = ctl_->tol;
-    gnorm0 = ctl_->gnorm0;
-    phase = ctl_->phase;
-    switch_tol = ctl_->switch_tol;
-  }
-  cluster.sync();  // every block is running before any DSMEM access
-  if (done) {
-    // Already stopped: make sure a device-side loop around this kernel ends.
-    if (P.cond != 0ull && !P.path && rank == 0 && tid == 0)
-      cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
-    return;
-  }
-  const float* lane_scal = cluster.map_shared_rank(scal, lane % CL);
-
-  const int r0 = rank * P.rpc;
-  const int nr = max(0, min(P.m, r0 + P.rpc) - r0);
-  const float* SAc;
-  long long ldc;
-  bool staged_async = false;
-  if (P.sa_in_smem && P.sa_vec && d == dp && nr > 0) {
-    // Whole rows by bulk asynchronous copies, counted in bytes on one mbarrier.
-    if (tid == 0) {
-      mbar_init(stage_bar, 1);
-      fence_mbar_init();
-      mbar_arrive_expect_tx(stage_bar, (uint32_t)nr * (uint32_t)dp * 4u);
-      for (int i = 0; i < nr; ++i)
-        bulk_copy_g2s(sa + (size_t)i * dp, P.SA + (long long)(r0 + i) * P.ldsa, (uint32_t)dp * 4u, stage_bar);
-    }
-    staged_async = true;
-    SAc = sa;
-    ldc = dp;
-  } else if (P.sa_in_smem) {
-    for (int i = 0; i < nr; ++i) {
-      const float* src = P.SA + (long long)(r0 + i) * P.ldsa;
-      for (int j = 4 * tid; j < dp; j += 4 * kThreads)
-        *reinterpret_cast<float4*>(sa + (size_t)i * dp + j) = load4_masked(src, j, d, P.sa_vec != 0);
-    }
-    SAc = sa;
-    ldc = dp;
-  } else {
-    SAc = P.SA + (long long)r0 * P.ldsa;
-    ldc = P.ldsa;
-  }
-
-  // θ₁ v = g
-  float gsq = 0.f;
-  for (int j = tid; j < dp; j += kThreads) {
-    const float gj = j < d ? g_in[j] : 0.f;
-    v[j] = gj;
-    gsq = fmaf(gj, gj, gsq);
-    xs[j] = 0.f;
-    dv[j] = 0.f;
-  }
-  for (int i = tid; i < P.rpc_pad; i += kThreads) p[i] = 0.f;
-  const float theta1 = sqrtf(block_sum(gsq, red));
-  if (staged_async) {
-    // Every thread waits for the rows (also on the early-exit paths below, so
-    // that no copy is still landing when the block exits).
-    if (!mbar_wait(stage_bar, 0u, kWaitLimitNs) && tid == 0 && ctl_ != nullptr) {
-      ctl_->status = MIHS_ERR_TIMEOUT;
-      ctl_->done = 1;
-    }
-  }
-
-  if (ctl_ != nullptr) {  // stop test of Algorithm 1 on ‖g‖ = θ₁
-    const float g0 = g0known ? gnorm0 : theta1;
-    if (hist_ != nullptr && rank == 0 && tid == 0 && outer < kHistCap) hist_[outer] = theta1;
-    const bool bad = !(theta1 <= 3.0e38f);
-    const bool conv = tol > 0.f && theta1 <= tol * g0;
-    const bool capped = outer >= max_outer;
-    // Refinement solves: from the next step on the compensated gradient, once
-    // the plain residual is below switch_tol or has set no new minimum for
-    // three steps (it has reached its fp32 floor, which for a generic
-    // right-hand side can lie above switch_tol).
-    if (phase == 0 && rank == 0 && tid == 0) {
-      const float gmin = ctl_->gmin;
-      const int stall = theta1 < gmin ? 0 : ctl_->stall + 1;
-      if (theta1 < gmin) ctl_->gmin = theta1;
-      ctl_->stall = stall;
-      if (theta1 <= switch_tol * g0 || stall >= 3) ctl_->phase = 1;
-    }
-    if (bad || conv || capped) {
-      if (rank == 0 && tid == 0) {
-        ctl_->gnorm = theta1;
-        ctl_->gnorm0 = g0;
-        ctl_->gnorm0_known = 1;
-        ctl_->status = bad ? MIHS_ERR_NUMERIC : (conv ? MIHS_OK : MIHS_NOT_CONVERGED);
-        ctl_->done = 1;
-        if (P.path) {
-          if (atomicAdd(P.path_ndone, 1) + 1 == P.ps.nl) {  // the last λ of the path to stop
-            *P.path_all_done = 1;
-            if (P.cond != 0ull) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
-          }
-        } else if (P.cond != 0ull) {
-          cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
-        }
-      }
-      return;  // no DSMEM access has happened since the barrier
-    }
-  }
-
-  int k = 0;
-  const int c0 = rank * P.cols_per;
-  const int c1 = min(dp, c0 + P.cols_per);
-  if (theta1 > 0.f) {
-    const float inv_theta1 = 1.0f / theta1;
-    for (int j = tid; j < dp; j += kThreads) v[j] *= inv_theta1;
-    __syncthreads();
-    // One sweep: w = SA v (p = 0 here), ρ² partial and u = SAᵀw (ρ p = w, the
-    // normalisation by ρ deferred so that one barrier publishes both).
-    float rsq_w = fused_sweep<CH>(SAc, ldc, nr, d, v, p, 0.f, w, wpart, dp);
-    if (lane == 0) red[warp] = rsq_w;
-    __syncthreads();
-    for (int j = tid; j < dp; j += kThreads) {
-      float t = 0.f;
-#pragma unroll
-      for (int q = 0; q < kWarps; ++q) t += wpart[(size_t)q * dp + j];
-      up[j] = t;
-    }
-    if (tid == 0) {
-      float t = 0.f;
-#pragma unroll
-      for (int q = 0; q < kWarps; ++q) t += red[q];
-      scal[1] = t;
-    }
-    cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-    if (warp == 0) {
-      const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
-      if (lane == 0) scal[2] = r2;
-    }
-    __syncthreads();
-    float rho = sqrtf(scal[2]);
-
-    const float lam = lam_;
-    float rhobar = sqrtf(rho * rho + lam);
-    float c = rho / rhobar;
-    float s = sqrtf(lam) / rhobar;
-    float phi = theta1 / rhobar;
-    {
-      const float inv = 1.0f / rhobar;
-      for (int j = tid; j < dp; j += kThreads) {
-        dv[j] = v[j] * inv;
-        xs[j] = phi * dv[j];
-      }
-    }
-    float t = __int_as_float(0x7f800000);  // +inf
-    if (rho > 0.f) {
-      const float inv = 1.0f / rho;
-      for (int i = tid; i < nr; i += kThreads) p[i] = w[i] * inv;
-    }
-
-    while (t >= P.eps && k < P.max_passes && rho > 0.f) {
-      // θ v := SAᵀ p − ρ v  with SAᵀp = (Σ_ranks SAᵀw)/ρ on this block's column slice
-      const float inv_rho = 1.0f / rho;
-      float zpart = 0.f;
-      for (int j = c0 + tid; j < c1; j += kThreads) {
-        float u[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) u[r] = cluster.map_shared_rank(up, r)[j];
-        float us = 0.f;
-#pragma unroll
-        for (int r = 0; r < CL; ++r) us += u[r];
-        const float z = j < d ? us * inv_rho - rho * v[j] : 0.f;
-        zsl[j] = z;
-        zpart = fmaf(z, z, zpart);
-      }
-      zpart = block_sum(zpart, red);
-      if (tid == 0) scal[0] = zpart;
-      cluster.sync();  // (B) slices of θv and θ² partials visible
-      if (warp == 0) {
-        const float t2 = cluster_scalar_sum<CL>(lane_scal, 0);
-        if (lane == 0) scal[2] = t2;
-      }
-      __syncthreads();
-      const float theta = sqrtf(scal[2]);
-      if (!(theta > 0.f)) break;  // invariant subspace: same decision everywhere
-      const float inv_theta = 1.0f / theta;
-      for (int j = tid; j < dp; j += kThreads)
-        v[j] = cluster.map_shared_rank(zsl, j >> P.cols_log2)[j] * inv_theta;
-      __syncthreads();
-      // ρ p := SA v − θ p (kept unnormalised in w until ρ is known), its ρ²
-      // partial and SAᵀw, in one sweep.
-      rsq_w = fused_sweep<CH>(SAc, ldc, nr, d, v, p, theta, w, wpart, dp);
-      if (lane == 0) red[warp] = rsq_w;
-      __syncthreads();
-      for (int j = tid; j < dp; j += kThreads) {
-        float tt = 0.f;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) tt += wpart[(size_t)q * dp + j];
-        up[j] = tt;
-      }
-      if (tid == 0) {
-        float tt = 0.f;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) tt += red[q];
-        scal[1] = tt;
-      }
-      cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-      if (warp == 0) {
-        const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
-        if (lane == 0) scal[2] = r2;
-      }
-      __syncthreads();
-      rho = sqrtf(scal[2]);
-      // Eldén's rotation of √λ into the bidiagonal, then the φ recursion and
-      // the forward-substitution update (Section 3.6).
-      const float lambar = sqrtf(lam + (s * theta) * (s * theta));
-      const float thetabar = c * theta;
-      rhobar = sqrtf(rho * rho + lambar * lambar);
-      const float inv_rhobar = 1.0f / rhobar;
-      c = rho * inv_rhobar;
-      s = lambar * inv_rhobar;
-      phi = -phi * thetabar * inv_rhobar;
-      for (int j = tid; j < dp; j += kThreads) {
-        const float dn = (v[j] - thetabar * dv[j]) * inv_rhobar;
-        dv[j] = dn;
-        xs[j] = fmaf(phi, dn, xs[j]);
-      }
-      t = fabsf(phi * rhobar) / theta1;
-      ++k;
-      if (rho > 0.f) {
-        const float inv = 1.0f / rho;
-        for (int i = tid; i < nr; i += kThreads) p[i] = w[i] * inv;
-      }
-      __syncthreads();
-    }
-  }
-
-  // Outputs: each block writes its column slice.
-  {
-    const int e1 = min(d, c0 + P.cols_per);
-    for (int j = c0 + tid; j < e1; j += kThreads) {
-      const float dj = xs[j];
-      if (delta_ != nullptr) delta_[j] = dj;
-      if (x_ != nullptr) {
-        const float xj = x_[j], xp = xprev_[j];
-        x_[j] = xj + alpha_ * dj + beta_ * (xj - xp);
-        xprev_[j] = xj;
-      }
-      if (P.x64 != nullptr) {
-        const double xj = P.x64[j], xp = P.x_prev64[j];
-        const double xn = xj + P.alpha64 * (double)dj + P.beta64 * (xj - xp);
-        P.x64[j] = xn;
-        P.x_prev64[j] = xj;
-        if (P.x32_shadow != nullptr) P.x32_shadow[j] = (float)xn;
-      }
-    }
-  }
-  if (rank == 0 && tid == 0) {
-    if (passes_ != nullptr) *passes_ = k;
-    if (ctl_ != nullptr) {
-      ctl_->outer = outer + 1;
-      ctl_->inner_total += k;
-      ctl_->gnorm = theta1;
-      if (!g0known) {
-        ctl_->gnorm0 = theta1;
-        ctl_->gnorm0_known = 1;
-      }
-    }
-  }
-  cluster.sync();  // keep this block's shared memory alive for remote readers
-}
-
-using AabKernelFn = void (*)(const AabParams);
-
-template <int CL>
-AabKernelFn kernel_for_ch(int ch) {
-  if (ch <= 2) return aab_cluster_kernel<CL, 2>;
-  if (ch <= 4) return aab_cluster_kernel<CL, 4>;
-  if (ch <= 8) return aab_cluster_kernel<CL, 8>;
-  return aab_cluster_kernel<CL, 16>;
-}
-
-// Kernel for a cluster size and a padded width dp (CH float4 per lane).
-AabKernelFn kernel_for(int cl, int dp) {
-  const int ch = (dp + 127) / 128;
-  switch (cl) {
-    case 1: return kernel_for_ch<1>(ch);
-    case 2: return kernel_for_ch<2>(ch);
-    case 4: return kernel_for_ch<4>(ch);
-    case 8: return kernel_for_ch<8>(ch);
-    default: return kernel_for_ch<16>(ch);
-  }
+AabKernelFn kernel_for(int cl, int dp, int sa_type) {
+  if (sa_type == MIHS_SA_BF16) return kernel_for_bf16(cl, dp);
+  if (sa_type == MIHS_SA_FP8E4M3) return kernel_for_fp8(cl, dp);
+  return kernel_for_f32(cl, dp);
 }
 
 struct ClusterPlan {
@@ -487,15 +45,21 @@ struct ClusterPlan {
   size_t smem;
 };
 
-size_t smem_bytes(int m, int dp, int cl, bool in_smem) {
+size_t elem_bytes(int sa_type) { return sa_type == MIHS_SA_BF16 ? 2 : (sa_type == MIHS_SA_FP8E4M3 ? 1 : 4); }
+
+// Shared-memory row pitch (elements) of SA kept in shared memory: dp for
+// fp32, the 16-element-aligned storage pitch for the quantised types.
+int smem_pitch(int dp, int sa_type) { return sa_type == MIHS_SA_FP32 ? dp : (int)round_up(dp, 16); }
+
+size_t smem_bytes(int m, int dp, int cl, bool in_smem, int sa_type) {
   const int rpc = (m + cl - 1) / cl;
   const int rpc_pad = (int)round_up(rpc, 4);
   size_t base = (size_t)((5 + kWarps) * dp + 2 * rpc_pad + kWarps + 8) * sizeof(float);
-  if (in_smem) base += (size_t)rpc * dp * sizeof(float);
+  if (in_smem) base += (size_t)rpc * smem_pitch(dp, sa_type) * elem_bytes(sa_type);
   return base;
 }
 
-bool cluster_fits(int cl, int dp, size_t smem) {
+bool cluster_fits(int cl, int dp, size_t smem, int sa_type) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -508,22 +72,23 @@ bool cluster_fits(int cl, int dp, size_t smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel_for(cl, dp), &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)kernel_for(cl, dp, sa_type), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return nclusters >= 1;
 }
 
-ClusterPlan plan_cluster_uncached(int m, int dp) {
+ClusterPlan plan_cluster_uncached(int m, int dp, int sa_type) {
   static bool attr_set = false;
   if (!attr_set) {
-    for (int cl : {1, 2, 4, 8, 16})
-      for (int w : {256, 512, 1024, 2048}) {
-        cudaFuncSetAttribute((void*)kernel_for(cl, w), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute((void*)kernel_for(cl, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBudget + 16 * 1024);
-      }
+    for (int t : {MIHS_SA_FP32, MIHS_SA_BF16, MIHS_SA_FP8E4M3})
+      for (int cl : {1, 2, 4, 8, 16})
+        for (int w : {256, 512, 1024, 2048}) {
+          cudaFuncSetAttribute((void*)kernel_for(cl, w, t), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+          cudaFuncSetAttribute((void*)kernel_for(cl, w, t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemBudget + 16 * 1024);
+        }
     attr_set = true;
   }
   int forced = 0;
@@ -533,35 +98,35 @@ ClusterPlan plan_cluster_uncached(int m, int dp) {
   for (int cl : sizes) {
     if (forced > 0 && cl != forced) continue;
     if (cl > m && cl > 1) break;
-    const size_t sm = smem_bytes(m, dp, cl, true);
-    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm)) return {cl, 1, sm};
+    const size_t sm = smem_bytes(m, dp, cl, true, sa_type);
+    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm, sa_type)) return {cl, 1, sm};
   }
   // Otherwise the largest launchable cluster reading SA from global memory (L2).
   for (int i = 4; i >= 0; --i) {
     const int cl = sizes[i];
     if (forced > 0 && cl != forced) continue;
     if (cl > m && cl > 1) continue;
-    const size_t sm = smem_bytes(m, dp, cl, false);
-    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm)) return {cl, 0, sm};
+    const size_t sm = smem_bytes(m, dp, cl, false, sa_type);
+    if (sm <= kSmemBudget && cluster_fits(cl, dp, sm, sa_type)) return {cl, 0, sm};
   }
   return {0, 0, 0};
 }
 
 std::mutex g_plan_mu;
-std::map<std::pair<int, int>, ClusterPlan> g_plans;  // (m, dp) → plan (current device)
+std::map<std::tuple<int, int, int>, ClusterPlan> g_plans;  // (m, dp, SA type) → plan (current device)
 
-ClusterPlan plan_cluster(int m, int dp) {
+ClusterPlan plan_cluster(int m, int dp, int sa_type) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  auto it = g_plans.find({m, dp});
+  auto it = g_plans.find({m, dp, sa_type});
   if (it != g_plans.end()) return it->second;
-  const ClusterPlan cp = plan_cluster_uncached(m, dp);
-  g_plans[{m, dp}] = cp;
+  const ClusterPlan cp = plan_cluster_uncached(m, dp, sa_type);
+  g_plans[{m, dp, sa_type}] = cp;
   return cp;
 }
 
 }  // namespace
 
-void aab_prepare(int m, int d) { (void)plan_cluster(m, (int)round_up(d, 4)); }
+void aab_prepare(int m, int d, int sa_type) { (void)plan_cluster(m, (int)round_up(d, 4), sa_type); }
 
 int launch_aab(const AabLaunch& a, cudaStream_t s) {
   AabParams P = {};
@@ -598,7 +163,14 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
     set_error("aab: path mode needs 1..16 λ and an fp32 iterate");
     return MIHS_ERR_INVALID_ARG;
   }
-  const ClusterPlan cp = plan_cluster(a.m, P.dp);
+  if (a.sa_type != MIHS_SA_FP32 && (a.ldsa % 16 != 0 || (reinterpret_cast<uintptr_t>(a.SA) & 15u) != 0 ||
+                                    (a.sa_type == MIHS_SA_FP8E4M3 && a.sa_scale == nullptr))) {
+    set_error("aab: quantised SA needs 16-byte aligned rows (ldsa %% 16 == 0) and fp8 tile scales");
+    return MIHS_ERR_INVALID_ARG;
+  }
+  P.sa_scale = a.sa_type == MIHS_SA_FP8E4M3 ? a.sa_scale : nullptr;
+  P.scale_ld = (int)((round_up(a.d, 4) + 127) / 128);
+  const ClusterPlan cp = plan_cluster(a.m, P.dp, a.sa_type);
   if (cp.cl == 0) {
     set_error("aab: no thread-block cluster fits for m=%d d=%d", a.m, a.d);
     return MIHS_ERR_UNSUPPORTED;
@@ -612,6 +184,7 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
     P.cols_log2 = lg;
   }
   P.sa_in_smem = cp.in_smem;
+  P.sa_pitch = smem_pitch(P.dp, a.sa_type);
   P.sa_vec = (a.ldsa % 4 == 0 && (reinterpret_cast<uintptr_t>(a.SA) & 15u) == 0) ? 1 : 0;
   if (!P.sa_in_smem && !P.sa_vec) {
     set_error("aab: SA of %d×%d does not fit in shared memory; its rows must then be 16-byte "
@@ -632,7 +205,7 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   timing_begin(kTimerAab, s);
-  MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel_for(cp.cl, P.dp), P));
+  MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel_for(cp.cl, P.dp, a.sa_type), P));
   timing_end(kTimerAab, s);
   count_launch();
   return MIHS_OK;

@@ -535,7 +535,8 @@ size_t aab_path_ws_floats(int dp) {
 
 int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s) {
   const int dp = (int)round_up(a.d, 4);
-  if (!a.path || a.d > 1024 || a.x64 != nullptr || ws == nullptr) return MIHS_ERR_UNSUPPORTED;
+  if (!a.path || a.d > 1024 || a.x64 != nullptr || ws == nullptr || a.sa_type != MIHS_SA_FP32)
+    return MIHS_ERR_UNSUPPORTED;
   const int nsm = num_sms();
   // rows per block: a multiple of 16 with at most one block per SM
   int R = (int)round_up((a.m + nsm - 1) / nsm, 16);
@@ -556,7 +557,7 @@ int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s) {
   MIHS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aab_path_kernel, kAThreads, smem));
   if (per_sm < 1 || G > per_sm * nsm) return MIHS_ERR_UNSUPPORTED;  // all blocks must be resident
   AabPathParams P = {};
-  P.SA = a.SA;
+  P.SA = static_cast<const float*>(a.SA);
   P.m = a.m;
   P.d = a.d;
   P.dp = dp;

@@ -174,6 +174,10 @@ struct mihs_sketch_s {
   uint64_t seed;
   int P;              // split-K partials of the A-pass
   float* SA;          // m × dp
+  int sa_prec = MIHS_SA_FP32;  // storage of SA inside AAb_Solver
+  void* SAq = nullptr;         // quantised SA (m × ldq) when sa_prec != fp32
+  float* sa_scales = nullptr;  // fp8 tile scales
+  int64_t ldq = 0;
   float* partials;    // P × dp
   float* g;           // dp
   float* x_prev;      // dp
@@ -198,8 +202,10 @@ struct mihs_sketch_s {
     const float* A; int64_t lda; const float* b; void* x;
     double lam, alpha, beta; float eps; int max_passes;
     const float* rhs;  // adjoint solves: g = rhs − AᵀAx − λx (b null)
+    int sa_prec;       // storage of SA read by AAb_Solver
     bool operator==(const Key& o) const {
-      return A == o.A && lda == o.lda && b == o.b && x == o.x && rhs == o.rhs && lam == o.lam &&
+      return A == o.A && lda == o.lda && b == o.b && x == o.x && rhs == o.rhs && sa_prec == o.sa_prec &&
+             lam == o.lam &&
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
   };
@@ -223,9 +229,10 @@ struct mihs_sketch_s {
   int P_path = 0;
   struct PathKey {
     const float* A; int64_t lda; const float* b; float* X; int64_t ldx;
-    PathScalars ps; float eps; int max_passes;
+    PathScalars ps; float eps; int max_passes; int sa_prec;
     bool operator==(const PathKey& o) const {
       return A == o.A && lda == o.lda && b == o.b && X == o.X && ldx == o.ldx && eps == o.eps &&
+             sa_prec == o.sa_prec &&
              max_passes == o.max_passes && std::memcmp(&ps, &o.ps, sizeof(ps)) == 0;
     }
   };
@@ -236,6 +243,20 @@ struct mihs_sketch_s {
 };
 
 namespace {
+
+// The SA that AAb_Solver reads: fp32, or the quantised copy.
+void set_sa(AabLaunch& a, const mihs_sketch_s* sk) {
+  if (sk->sa_prec != MIHS_SA_FP32 && sk->SAq != nullptr) {
+    a.SA = sk->SAq;
+    a.sa_type = sk->sa_prec;
+    a.sa_scale = sk->sa_scales;
+    a.ldsa = sk->ldq;
+  } else {
+    a.SA = sk->SA;
+    a.sa_type = MIHS_SA_FP32;
+    a.ldsa = sk->dp;
+  }
+}
 
 void drop_graph(mihs_sketch_s::GraphSlot& gs) {
   if (gs.exec) cudaGraphExecDestroy(gs.exec);
@@ -297,7 +318,7 @@ int build_while_graph(mihs_sketch_s* sk, int m, int d, cudaGraph_t& graph, cudaG
   cudaGraphNode_t node;
   MIHS_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
   cudaGraph_t bodyg = np.conditional.phGraph_out[0];
-  aab_prepare(m, d);
+  aab_prepare(m, d, sk->sa_prec);
   MIHS_CUDA_TRY(cudaStreamBeginCaptureToGraph(sk->cap, bodyg, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal));
   int rc = body((unsigned long long)h, sk->cap);
@@ -478,6 +499,41 @@ static int cap_passes(int64_t m, int64_t d, int max_inner) {
   return (int)(max_inner > 0 && max_inner < mn ? max_inner : mn);
 }
 
+int mihs_quantize_sa(const float* SA, int64_t m, int64_t d, int64_t ldsa, int sa_prec, void* out, int64_t ldq,
+                     float* scales, void* stream) {
+  set_error("");
+  MIHS_ARG(SA != nullptr && out != nullptr, "mihs_quantize_sa: null SA or out");
+  MIHS_ARG(m >= 1 && d >= 1 && d <= kMaxD && ldsa >= d, "mihs_quantize_sa: bad shape");
+  MIHS_ARG(sa_prec == MIHS_SA_BF16 || sa_prec == MIHS_SA_FP8E4M3, "mihs_quantize_sa: precision must be bf16 or fp8");
+  MIHS_ARG(ldq >= d && ldq % 16 == 0, "mihs_quantize_sa: ldq must be >= d and a multiple of 16");
+  MIHS_ARG(sa_prec != MIHS_SA_FP8E4M3 || scales != nullptr, "mihs_quantize_sa: fp8 needs a scale array");
+  return launch_quantize_sa(SA, m, d, ldsa, sa_prec, out, ldq, scales, static_cast<cudaStream_t>(stream));
+}
+
+int mihs_aab_solve_q(const void* SAq, int sa_prec, const float* scales, int64_t m, int64_t d, int64_t ldq,
+                     const float* g, double lambda, double eps_sub, int max_inner, float* delta, int* passes,
+                     void* stream) {
+  set_error("");
+  MIHS_ARG(sa_prec == MIHS_SA_BF16 || sa_prec == MIHS_SA_FP8E4M3, "mihs_aab_solve_q: precision must be bf16 or fp8");
+  MIHS_ARG(SAq != nullptr && g != nullptr && delta != nullptr, "mihs_aab_solve_q: null argument");
+  MIHS_ARG(m >= 1 && d >= 1 && d <= kMaxD && ldq >= d && ldq % 16 == 0, "mihs_aab_solve_q: bad shape");
+  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda) && eps_sub >= 0.0, "mihs_aab_solve_q: bad lambda or eps");
+  AabLaunch a = {};
+  a.SA = SAq;
+  a.sa_type = sa_prec;
+  a.sa_scale = scales;
+  a.m = (int)m;
+  a.d = (int)d;
+  a.ldsa = ldq;
+  a.g = g;
+  a.lambda = (float)lambda;
+  a.eps = (float)eps_sub;
+  a.max_passes = cap_passes(m, d, max_inner);
+  a.delta = delta;
+  a.passes = passes;
+  return launch_aab(a, static_cast<cudaStream_t>(stream));
+}
+
 int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa, const float* g,
                    double lambda, double eps_sub, int max_inner, float* delta, int* passes,
                    void* stream) {
@@ -594,7 +650,34 @@ int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, 
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_resketch");
   if (rc) return rc;
   sk->seed = seed;
-  return mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
+  rc = mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
+  if (rc || sk->sa_prec == MIHS_SA_FP32) return rc;
+  return launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sk->sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
+                            static_cast<cudaStream_t>(stream));
+}
+
+int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream) {
+  set_error("");
+  MIHS_ARG(sk != nullptr, "mihs_sketch_set_precision: null handle");
+  MIHS_ARG(sa_prec == MIHS_SA_FP32 || sa_prec == MIHS_SA_BF16 || sa_prec == MIHS_SA_FP8E4M3,
+           "mihs_sketch_set_precision: unknown precision %d", sa_prec);
+  if (sa_prec != MIHS_SA_FP32 && sk->SAq == nullptr) {
+    sk->ldq = sa_quant_ld(sk->d);
+    const size_t qbytes = round_up((int64_t)sk->m * sk->ldq, 256);  // ≤ 1 byte/element more than fp8 needs
+    const size_t bytes = 2 * qbytes + sizeof(float) * (size_t)sa_scale_count(sk->m, sk->d);
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      set_error("mihs_sketch_set_precision: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+    }
+    sk->SAq = p;
+    sk->sa_scales = reinterpret_cast<float*>(p + 2 * qbytes);
+  }
+  sk->sa_prec = sa_prec;
+  if (sa_prec == MIHS_SA_FP32) return MIHS_OK;
+  return launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
+                            static_cast<cudaStream_t>(stream));
 }
 
 int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m, int64_t* d, int64_t* n,
@@ -643,6 +726,7 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk->cap) cudaStreamDestroy(sk->cap);
   if (sk->dd_partials) cudaFree(sk->dd_partials);
   if (sk->path_partials) cudaFree(sk->path_partials);
+  if (sk->SAq) cudaFree(sk->SAq);
   if (sk->path_ctl_host) cudaFreeHost(sk->path_ctl_host);
   cudaFreeHost(sk->ctl_host);
   cudaFree(sk->SA);
@@ -726,10 +810,9 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   }
 
   AabLaunch a = {};
-  a.SA = sk->SA;
+  set_sa(a, sk);
   a.m = (int)sk->m;
   a.d = (int)d;
-  a.ldsa = sk->dp;
   a.g = sk->g;
   a.lambda = (float)lambda;
   a.eps = (float)opts->eps_sub;
@@ -749,7 +832,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   a.ctl = sk->ctl;
   a.hist = sk->hist;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
-  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs};
+  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs, sk->sa_prec};
   bool graph_ran = false;
   mihs_sketch_s::GraphSlot& gs = sk->slots[(refined ? 1 : 0) + (rhs != nullptr ? 2 : 0)];
   if (!timing_on() && !gs.failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
@@ -939,10 +1022,9 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
     MIHS_CUDA_TRY(cudaMemcpy2DAsync(sk->path_xprev, (size_t)sk->dp * sizeof(float), Xg, (size_t)ldx * sizeof(float),
                                     (size_t)d * sizeof(float), nl, cudaMemcpyDeviceToDevice, s));
     AabLaunch a = {};
-    a.SA = sk->SA;
+    set_sa(a, sk);
     a.m = (int)sk->m;
     a.d = (int)d;
-    a.ldsa = sk->dp;
     a.g = sk->path_g;
     a.eps = (float)opts->eps_sub;
     a.max_passes = cap_passes(sk->m, d, opts->max_inner);
@@ -955,7 +1037,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
     a.path_ldx = ldx;
     a.path_ndone = sk->path_cnt;
     a.path_all_done = sk->path_cnt + 1;
-    const mihs_sketch_s::PathKey key = {A, lda, b, Xg, ldx, ps, a.eps, a.max_passes};
+    const mihs_sketch_s::PathKey key = {A, lda, b, Xg, ldx, ps, a.eps, a.max_passes, sk->sa_prec};
     bool graph_ran = false;
     if (!timing_on() && !sk->path_graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
       if (!(sk->path_exec && sk->path_key == key)) {

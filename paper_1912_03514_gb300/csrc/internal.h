@@ -48,6 +48,12 @@ int launch_apass_path_finalize(const float* partials, int P, int64_t d, const fl
                                cudaStream_t s);
 int apass_path_device_error(int* code);
 
+// ---- quantised SA (sa_quant.cu) ---------------------------------------------
+int64_t sa_quant_ld(int64_t d);                 // row pitch (elements) of quantised SA
+int64_t sa_scale_count(int64_t m, int64_t d);   // fp8 tile scales
+int launch_quantize_sa(const float* SA, int64_t m, int64_t d, int64_t ldsa, int prec, void* out, int64_t ldq,
+                       float* scales, cudaStream_t s);
+
 // ---- gradients of the solution (backward.cu) ------------------------------
 // dlambda = −xᵀv (fp64); db = Av; dA = r vᵀ − (Av) xᵀ with r = b − Ax.  Any of
 // dA, db, dlambda may be NULL; b may be NULL only when dA is.
@@ -68,7 +74,9 @@ int apass_dd_device_error(int* code);
 
 // ---- AAb_Solver (aab.cu) --------------------------------------------------
 struct AabLaunch {
-  const float* SA;
+  const void* SA;      // element type per sa_type; ldsa in elements
+  int sa_type;         // MIHS_SA_FP32 (0), MIHS_SA_BF16, MIHS_SA_FP8E4M3 (quantised: ldsa % 16 == 0)
+  const float* sa_scale;  // fp8: one scale per 128 × 128 tile, ⌈dp/128⌉ per tile row
   int m, d;
   int64_t ldsa;
   const float* g;
@@ -106,7 +114,7 @@ size_t aab_path_ws_floats(int dp);
 int aab_path_device_error(int* code);
 int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s);
 // Picks and caches the cluster shape for (m, d) (call outside stream capture).
-void aab_prepare(int m, int d);
+void aab_prepare(int m, int d, int sa_type = 0);
 
 constexpr int kHistCap = 1024;
 

@@ -18,6 +18,8 @@ import torch
 from . import _build
 
 GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
+SA_FP32, SA_BF16, SA_FP8 = 0, 1, 2
+SA_PRECISIONS = {"fp32": SA_FP32, "bf16": SA_BF16, "fp8": SA_FP8}
 FAMILIES = {"gaussian": GAUSSIAN, "countsketch": COUNTSKETCH, "srht": SRHT}
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC, UNSUPPORTED = -1, -2, -3, -4, -5, -6
@@ -90,6 +92,9 @@ def lib() -> ctypes.CDLL:
         "mihs_solve": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp,
                               ctypes.POINTER(_Info), _vp]),
         "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "mihs_sketch_set_precision": (_int, [_vp, _int, _vp]),
+        "mihs_quantize_sa": (_int, [_vp, _i64, _i64, _i64, _int, _vp, _i64, _vp, _vp]),
+        "mihs_aab_solve_q": (_int, [_vp, _int, _vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
         "mihs_gradient_path": (_int, [_vp, _i64, _i64, _i64, _vp, _int, _vp, _vp, _i64, _vp, _i64, _vp]),
         "mihs_solve_path": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp, ctypes.POINTER(_Opts), _vp, _i64, _vp,
                                    _vp]),
@@ -271,6 +276,46 @@ def backward_grads(A: torch.Tensor, b: torch.Tensor | None, x: torch.Tensor, v: 
     return dA, db, dl
 
 
+def _prec(p) -> int:
+    if isinstance(p, str):
+        if p not in SA_PRECISIONS:
+            raise ValueError(f"unknown SA precision {p!r} (fp32, bf16, fp8)")
+        return SA_PRECISIONS[p]
+    return int(p)
+
+
+def quantize_sa(SA: torch.Tensor, prec, stream=None):
+    """mihs_quantize_sa: returns (q, scales) with q an m × ldq tensor
+    (bfloat16, or uint8 holding fp8 e4m3 bytes), ldq = d rounded up to 16,
+    and scales the fp8 tile scales (⌈m/128⌉ × ⌈d₄/128⌉) or None."""
+    ps, m, d, ldsa = _mat(SA, "SA")
+    pr = _prec(prec)
+    ldq = (d + 15) // 16 * 16
+    if pr == SA_BF16:
+        q = torch.empty(m, ldq, dtype=torch.bfloat16, device=SA.device)
+        sc = None
+    else:
+        q = torch.empty(m, ldq, dtype=torch.uint8, device=SA.device)
+        sc = torch.empty((m + 127) // 128, ((d + 3) // 4 * 4 + 127) // 128, dtype=torch.float32, device=SA.device)
+    _check(lib().mihs_quantize_sa(ps, m, d, ldsa, pr, q.data_ptr(), ldq, sc.data_ptr() if sc is not None else None,
+                                  _stream(stream)))
+    return q, sc
+
+
+def aab_solve_q(q: torch.Tensor, prec, scales, d: int, g: torch.Tensor, lam: float, eps_sub: float = 0.1,
+                max_inner: int = 0, delta: torch.Tensor | None = None, passes: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """mihs_aab_solve_q on the output of quantize_sa."""
+    m, ldq = q.shape
+    if delta is None:
+        delta = torch.empty(d, dtype=torch.float32, device=q.device)
+    _check(lib().mihs_aab_solve_q(q.data_ptr(), _prec(prec), scales.data_ptr() if scales is not None else None,
+                                  m, d, ldq, _vec(g, d, "g"), float(lam), float(eps_sub), int(max_inner),
+                                  _vec(delta, d, "delta"), passes.data_ptr() if passes is not None else None,
+                                  _stream(stream)))
+    return delta
+
+
 def _dbl_array(vals):
     vals = [float(v) for v in vals]
     return (ctypes.c_double * len(vals))(*vals), len(vals)
@@ -362,6 +407,10 @@ class Sketch:
         if (n, d) != (self.n, self.d):
             raise ValueError("A does not match the sketch")
         _check(lib().mihs_resketch(self._h, pa, lda, seed & (2**64 - 1), _stream(stream)))
+
+    def set_precision(self, prec, stream=None) -> None:
+        """Storage of SA inside AAb_Solver: 'fp32', 'bf16' or 'fp8' (mihs_sketch_set_precision)."""
+        _check(lib().mihs_sketch_set_precision(self._h, _prec(prec), _stream(stream)))
 
     def sa(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.m, self.d, dtype=torch.float32, device=self.device)
