@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--refined-tol", type=float, default=1e-10)
     ap.add_argument("--no-backward", action="store_true", help="skip the differentiable-solve leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched λ-path leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (2^21 x 2048)")
+    ap.add_argument("--mixed-oracle", action="store_true",
+                    help="also solve the mixed-precision workload with the fp64 oracle on the host (slow)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "gaussian",
@@ -412,6 +415,11 @@ def main():
     if not args.no_batched:
         batched = run_batched(args, dev, ws, peaks, peak_src)
 
+    # ---------------- mixed precision: 2²¹ × 2048, κ(H) ≈ 1e6, refined to 1e-10
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, dev, ws)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         if A_host is None:
@@ -443,6 +451,7 @@ def main():
             "refined": refined,
             "differentiable": differentiable,
             "batched": batched,
+            "mixed": mixed,
             "not_converged": not_converged or None,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -580,6 +589,58 @@ def run_batched(args, dev, ws, peaks, peak_src):
                                    "peak_source": "derived: 152 SMs × 128 FP32 FMA/clk × 2 flops × 2.07 GHz"}}
     for sk in handles:
         sk.close()
+    return out
+
+
+def run_mixed(args, dev, ws):
+    """2²¹ × 2048, σ_i = 10^(−8(i−1)/2047), λ = 1e-6 (sd ≈ 768, κ(H) ≈ 1e6),
+    40 dB SNR, Gaussian sketch with m = 4·sd: compensated-refinement solves to
+    residual 1e-10 with SA stored in fp32, bf16 and fp8 inside AAb_Solver.
+    One step = sketch + refined solve."""
+    import numpy as np
+    import torch
+
+    from paper_1912_03514_gb300 import mihs
+    from paper_1912_03514_gb300 import workloads as W
+    n, d, lam = 1 << 21, 2048, 1e-6
+    p = W.make_problem(n, d, W.profile_exponential(d, 8.0), lam, 40.0, seed=1002, device=str(dev), device_rng=True)
+    A, b = p.A, p.b
+    tol = 1e-10
+    sk = mihs.Sketch(A, "gaussian", p.m, seed=3)
+    x = torch.empty(d, dtype=torch.float64, device=dev)
+    out = {"workload": f"{p.name}, SNR 40 dB, λ = 1e-6 (sd {p.sd:.1f}, κ(H) ≈ 1e6), Gaussian m = {p.m}, "
+                       f"refinement to residual {tol:g}; A = {4 * n * d / 1e9:.1f} GB",
+           "unit": "solves/s", "by_sa_precision": {}}
+    xs = None
+    if args.mixed_oracle:
+        from oracle import mihs_oracle as o
+        xs = o.exact_solve(A.cpu().numpy(), b.cpu().numpy(), lam, refine=2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    for prec in ("fp32", "bf16", "fp8"):
+        def step(want_info=False):
+            sk.resketch(A, 3)
+            return sk.solve_refined(A, b, lam, p.sd, tol=tol, max_outer=300, x=x, want_info=want_info)[1]
+        sk.set_precision(prec)
+        try:
+            info = step(want_info=True)
+        except mihs.MihsError as e:  # a quantised SA can stop being an embedding
+            out["by_sa_precision"][prec] = {"status": e.code, "error": str(e).split(":")[0]}
+            continue
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws)
+        r = {"value": round(ws / (ms / 1e3), 3), "ms_per_step": round(ms, 2), "status": info.status,
+             "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
+             "rel_resid": float(f"{info.rel_resid:.3e}")}
+        if xs is not None:
+            from oracle import mihs_oracle as o
+            r["rel_err_vs_oracle"] = float(f"{o.rel_error(x.cpu().numpy(), xs):.3e}")
+        out["by_sa_precision"][prec] = r
+    sk.close()
     return out
 
 
