@@ -25,6 +25,10 @@ Contents and the passage each follows:
   momentum_params ...... β = sd/m, α = (1−β)² (Corollary 3, Algorithm 1).
   theorem1_params ...... β*, α*, rate of Theorem 1.
   mihs ................. Algorithm 1 (M-IHS for n ≥ d).
+  dual_mihs ............ Algorithm 2 (Dual M-IHS for n ≤ d) on the dual
+                          problem of Eq. intro_dual, x = Aᵀν (Eq. dual_relation).
+  exact_solve_dual ..... the plain definition through the dual:
+                          x* = Aᵀ(AAᵀ + λI)⁻¹b.
   hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
   quantize_sa .......... storage of SA in bf16, or fp8 e4m3 with one scale per
                           128 × 128 tile (a format, not the paper's: the
@@ -568,6 +572,46 @@ def mihs(A, b, lam, SA, sd, N, x1=None, eps_sub=0.1, tol=None, inner="aab",
     info = dict(outer=outer, inner_total=inner_total, resid=resid, history=hist,
                 alpha=float(alpha), beta=float(beta))
     return x.astype(np.float64), info
+
+
+def exact_solve_dual(A, b, lam):
+    """x* = Aᵀν*, ν* = (AAᵀ + λI)⁻¹b (Eq. dual_relation): an n × n Cholesky,
+    the natural form when n ≤ d."""
+    A64 = np.asarray(A, dtype=np.float64)
+    K = A64 @ A64.T + lam * np.eye(A64.shape[0])
+    L = np.linalg.cholesky(K)
+    nu = np.linalg.solve(L.T, np.linalg.solve(L, np.asarray(b, dtype=np.float64)))
+    return A64.T @ nu, nu
+
+
+def dual_mihs(A, b, lam, SAt, sd, N, eps_sub=0.1, tol=None, max_inner=None, dtype=np.float64):
+    """Algorithm 2 with the given sketch SAt = S·Aᵀ (m × n, S sketching the
+    d coordinates).  Each of at most N iterations: g = b − AAᵀν − λν (the
+    negative gradient of the dual objective of Eq. intro_dual); stop if tol
+    is set and ‖g‖ ≤ tol·‖b‖ (= ‖g(0)‖); Δν = AAb_Solver(SAt, g, λ, ε_sub);
+    ν ← ν + αΔν + β(ν − ν⁻) with β = sd/m, α = (1 − β)², ν¹ = ν⁰ = 0.  Then
+    x = Aᵀν.  Returns (x, ν, info)."""
+    A = np.asarray(A, dtype=dtype)
+    b = np.asarray(b, dtype=dtype)
+    SAt = np.asarray(SAt, dtype=dtype)
+    m, n = SAt.shape
+    alpha, beta = momentum_params(sd, m)
+    alpha, beta = dtype(alpha), dtype(beta)
+    nu = np.zeros(n, dtype)
+    nu_prev = nu.copy()
+    gnorm0 = float(np.linalg.norm(b.astype(np.float64)))
+    inner_total, outer, resid = 0, 0, float("nan")
+    for _ in range(N):
+        g = b - A @ (A.T @ nu) - dtype(lam) * nu
+        resid = float(np.linalg.norm(g.astype(np.float64))) / gnorm0 if gnorm0 > 0 else 0.0
+        if tol is not None and resid <= tol:
+            break
+        delta, k = aab_solve(SAt, g, lam, eps_sub, max_iter=max_inner, dtype=dtype)
+        inner_total += k
+        nu, nu_prev = heavy_ball(nu, nu_prev, delta, alpha, beta)
+        outer += 1
+    x = A.T.astype(np.float64) @ nu.astype(np.float64)
+    return x, nu.astype(np.float64), dict(outer=outer, inner_total=inner_total, resid=resid)
 
 
 def mihs_solve(A, b, lam, family, m, sd, seed, N=200, tol=1e-6, eps_sub=0.1,

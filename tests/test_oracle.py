@@ -536,3 +536,38 @@ def test_quantize_sa_known_values():
     assert dec[0, 0] == 448 * s and dec[1, 1] == 2.0 ** -9 * s and dec[2, 2] == 0.0
     assert dec[3, 3] == 16 * s
     assert abs(dec[129, 130] + 3.0) <= 3.0 * 2.0 ** -4  # 3 mantissa bits
+
+
+# ------------------------------------------------------------ Dual M-IHS
+def test_exact_solve_dual_push_through_identity():
+    """Aᵀ(AAᵀ + λI)⁻¹b = (AᵀA + λI)⁻¹Aᵀb (push-through identity), and the
+    dual solution satisfies ν* = (b − Ax*)/λ (Eq. dual_relation)."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((30, 80)) @ np.diag(np.logspace(0, -2, 80))
+    b = rng.standard_normal(30)
+    lam = 0.05
+    x, nu = o.exact_solve_dual(A, b, lam)
+    xp = np.linalg.lstsq(np.vstack([A, math.sqrt(lam) * np.eye(80)]), np.concatenate([b, np.zeros(80)]),
+                         rcond=None)[0]
+    assert np.linalg.norm(x - xp) <= 1e-10 * np.linalg.norm(xp)
+    assert np.linalg.norm(nu - (b - A @ x) / lam) <= 1e-9 * np.linalg.norm(nu)
+
+
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_dual_mihs_reaches_the_solution(family):
+    """Algorithm 2 on a wide problem (n = 64 ≪ d = 2000) with SAᵀ sketched
+    along d: x = Aᵀν converges to the primal solution of the least squares
+    formulation (not the oracle's own closed form)."""
+    rng = np.random.default_rng(13 + family)
+    n, d, lam = 64, 2000, 1e-3
+    A = rng.standard_normal((n, d)) @ np.diag(np.logspace(0, -1, d)) / math.sqrt(d)
+    b = rng.standard_normal(n)
+    sd = o.stat_dim_of(A, lam)
+    m = int(math.ceil(4 * sd / 4)) * 4 + 4
+    SAt = o.sketch_apply(family, A.T, m, seed=21)
+    x, nu, info = o.dual_mihs(A, b, lam, SAt, sd, N=200, tol=1e-12)
+    # the minimiser of ½‖Ax − b‖² + (λ/2)‖x‖² from LAPACK's least squares
+    xp = np.linalg.lstsq(np.vstack([A, math.sqrt(lam) * np.eye(d)]), np.concatenate([b, np.zeros(d)]),
+                         rcond=None)[0]
+    assert o.rel_error(x, xp) <= 1e-9, info
+    assert info["outer"] < 60
