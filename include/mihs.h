@@ -414,6 +414,48 @@ int mihs_backward_refined(mihs_sketch_t sk, const float* A, int64_t lda,
                           float* dA, int64_t ldda, float* db, double* dlambda,
                           mihs_info* info, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Dual M-IHS (Algorithm 2) for n ≤ d: M-IHS on the dual problem
+ * ν* = argmin ½‖Aᵀν‖² + (λ/2)‖ν‖² − ⟨b, ν⟩ (Eq. intro_dual) with the sketch
+ * taken along the d coordinates, SAᵀ (m × n), and x* = Aᵀν* (Eq.
+ * dual_relation).  Each step: g = b − AAᵀν − λν (two passes over A),
+ * Δν = AAb_Solver(SAᵀ, g, λ, ε_sub), ν⁺ = ν + αΔν + β(ν − ν⁻) with
+ * β = sd/m, α = (1 − β)² (Theorem 1 / Corollary 3 hold for the dual form).
+ * A is n × d row-major (lda ≥ d, a multiple of 4, 16-byte aligned rows),
+ * 1 ≤ n ≤ 2048, n ≤ d.
+ * ---------------------------------------------------------------------- */
+typedef struct mihs_dual_s* mihs_dual_t;
+
+/* Sketch Aᵀ: a d × n transposed copy of A is formed in stream-ordered
+ * scratch, then sketched along its d rows by `family` with m ≤ d rows.  The
+ * handle owns SAᵀ and the workspace of mihs_solve_dual.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_dual_sketch(const float* A, int64_t n, int64_t d, int64_t lda,
+                     int family, int64_t m, uint64_t seed, void* stream,
+                     mihs_dual_t* out);
+/* Recompute SAᵀ for a new A of the handle's shape. */
+int mihs_dual_resketch(mihs_dual_t dk, const float* A, int64_t lda,
+                       uint64_t seed, void* stream);
+/* Copy SAᵀ (m × n) into dst (device, leading dimension ldd ≥ n). */
+int mihs_dual_copy(mihs_dual_t dk, float* dst, int64_t ldd, void* stream);
+int mihs_dual_destroy(mihs_dual_t dk);
+
+/* The dual gradient step on its own: g = b − A(Aᵀν) − λν (n-vectors). */
+int mihs_gradient_dual(const float* A, int64_t n, int64_t d, int64_t lda,
+                       const float* b, const float* nu, double lambda,
+                       float* g, void* stream);
+/* x = Aᵀν (d-vector, 16-byte aligned). */
+int mihs_dual_recover(const float* A, int64_t n, int64_t d, int64_t lda,
+                      const float* nu, float* x, void* stream);
+
+/* Algorithm 2 with the handle's SAᵀ.  nu: DEVICE n-vector, ν¹ on entry if
+ * opts->warm_start (else zeroed), the dual solution on exit; x: optional
+ * DEVICE d-vector receiving Aᵀν.  The stop test is ‖g‖ ≤ tol·‖b‖.  opts,
+ * info and the return value as in mihs_solve (sd ≤ 0: Algorithm 4 on SAᵀ). */
+int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda,
+                    const float* b, double lambda, const mihs_opts* opts,
+                    float* x, float* nu, mihs_info* info, void* stream);
+
 /* Trace of the last solve on this handle: the relative residual
  * ‖g(xⁱ)‖/‖Aᵀb‖ of every gradient step (i = 0, 1, …, at most 1024 entries)
  * into the HOST array host_out[0..cap), the number written in *count.

@@ -93,6 +93,14 @@ def lib() -> ctypes.CDLL:
                               ctypes.POINTER(_Info), _vp]),
         "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
         "mihs_sketch_set_precision": (_int, [_vp, _int, _vp]),
+        "mihs_dual_sketch": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, ctypes.POINTER(_vp)]),
+        "mihs_dual_resketch": (_int, [_vp, _vp, _i64, _u64, _vp]),
+        "mihs_dual_copy": (_int, [_vp, _vp, _i64, _vp]),
+        "mihs_dual_destroy": (_int, [_vp]),
+        "mihs_gradient_dual": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
+        "mihs_dual_recover": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp]),
+        "mihs_solve_dual": (_int, [_vp, _vp, _i64, _vp, _dbl, ctypes.POINTER(_Opts), _vp, _vp,
+                                   ctypes.POINTER(_Info), _vp]),
         "mihs_quantize_sa": (_int, [_vp, _i64, _i64, _i64, _int, _vp, _i64, _vp, _vp]),
         "mihs_aab_solve_q": (_int, [_vp, _int, _vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
         "mihs_gradient_path": (_int, [_vp, _i64, _i64, _i64, _vp, _int, _vp, _vp, _i64, _vp, _i64, _vp]),
@@ -648,3 +656,83 @@ def ridge_solve(A: torch.Tensor, b: torch.Tensor, lam, family="countsketch", m: 
         m = min(n, ((int(4 * sd) + 3) // 4) * 4) if sd > 0 else min(n, d)
     return RidgeSolve.apply(A, b, lam, family, int(m), float(sd), int(seed), float(tol), int(max_outer),
                             float(eps_sub), bool(refine))
+
+
+def gradient_dual(A: torch.Tensor, b: torch.Tensor, nu: torch.Tensor, lam: float, g: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """g = b − A(Aᵀν) − λν (mihs_gradient_dual)."""
+    pa, n, d, lda = _mat(A, "A")
+    if g is None:
+        g = torch.empty(n, dtype=torch.float32, device=A.device)
+    _check(lib().mihs_gradient_dual(pa, n, d, lda, _vec(b, n, "b"), _vec(nu, n, "nu"), float(lam), _vec(g, n, "g"),
+                                    _stream(stream)))
+    return g
+
+
+def dual_recover(A: torch.Tensor, nu: torch.Tensor, x: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """x = Aᵀν (mihs_dual_recover)."""
+    pa, n, d, lda = _mat(A, "A")
+    if x is None:
+        x = torch.empty(d, dtype=torch.float32, device=A.device)
+    _check(lib().mihs_dual_recover(pa, n, d, lda, _vec(nu, n, "nu"), _vec(x, d, "x"), _stream(stream)))
+    return x
+
+
+class DualSketch:
+    """A handle holding SAᵀ (mihs_dual_sketch) for Dual M-IHS solves (n ≤ d)."""
+
+    def __init__(self, A: torch.Tensor, family, m: int, seed: int, stream=None):
+        pa, n, d, lda = _mat(A, "A")
+        h = ctypes.c_void_p()
+        _check(lib().mihs_dual_sketch(pa, n, d, lda, family_id(family), int(m), seed & (2**64 - 1),
+                                      _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n, self.d, self.m = n, d, int(m)
+        self.device = A.device
+
+    def resketch(self, A: torch.Tensor, seed: int, stream=None) -> None:
+        pa, n, d, lda = _mat(A, "A")
+        _check(lib().mihs_dual_resketch(self._h, pa, lda, seed & (2**64 - 1), _stream(stream)))
+
+    def sat(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.m, self.n, dtype=torch.float32, device=self.device)
+        _check(lib().mihs_dual_copy(self._h, out.data_ptr(), self.n, _stream(stream)))
+        return out
+
+    def solve(self, A: torch.Tensor, b: torch.Tensor, lam: float, sd: float, tol: float = 1e-6,
+              max_outer: int = 100, eps_sub: float = 0.1, max_inner: int = 0, nu: torch.Tensor | None = None,
+              x: torch.Tensor | None = None, warm_start: bool = False, want_info: bool = True, stream=None):
+        """Algorithm 2.  Returns (x, nu, SolveInfo or None)."""
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (self.n, self.d):
+            raise ValueError("A does not match the sketch")
+        if nu is None:
+            nu = torch.empty(n, dtype=torch.float32, device=A.device)
+        if x is None:
+            x = torch.empty(d, dtype=torch.float32, device=A.device)
+        o = lib().mihs_default_opts()
+        o.tol, o.max_outer, o.eps_sub = float(tol), int(max_outer), float(eps_sub)
+        o.max_inner, o.sd, o.warm_start = int(max_inner), float(sd), int(bool(warm_start))
+        info = _Info()
+        rc = lib().mihs_solve_dual(self._h, pa, lda, _vec(b, n, "b"), float(lam), ctypes.byref(o), _vec(x, d, "x"),
+                                   _vec(nu, n, "nu"), ctypes.byref(info) if want_info else None, _stream(stream))
+        _check(rc, allow_not_converged=True)
+        return x, nu, (SolveInfo(info.outer_iters, info.inner_iters_total, info.rel_resid, info.status)
+                       if want_info else None)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mihs_dual_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
