@@ -64,8 +64,8 @@ def parse():
                     help="also solve the mixed-precision workload with the fp64 oracle on the host (slow)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
-    ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "gaussian",
-                                            "countsketch", "srht"],
+    ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
+                                            "gaussian", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
 
@@ -636,6 +636,15 @@ def run_mixed(args, dev, ws):
         r = {"value": round(ws / (ms / 1e3), 3), "ms_per_step": round(ms, 2), "status": info.status,
              "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
              "rel_resid": float(f"{info.rel_resid:.3e}")}
+        # per-kernel event times of one more step (host-driven: the library
+        # times each launch on the solve's stream)
+        mihs.timing(True)
+        step()
+        torch.cuda.synchronize()
+        r["kernel_ms"] = {k: round(mihs.timing_read(t)[0], 2) for k, t in
+                          (("sketch", mihs.TIMER_SKETCH), ("apass", mihs.TIMER_APASS),
+                           ("apass_dd", mihs.TIMER_APASS_DD), ("aab", mihs.TIMER_AAB))}
+        mihs.timing(False)
         if xs is not None:
             from oracle import mihs_oracle as o
             r["rel_err_vs_oracle"] = float(f"{o.rel_error(x.cpu().numpy(), xs):.3e}")
@@ -657,7 +666,16 @@ def run_profile_op(args, local):
     x = W.randn((p.d,), seed=5, scale=0.01).to(dev)
     g = torch.empty(p.d, device=dev)
     op = args.profile_op
-    if op in ("aab", "aab-late"):
+    if op == "aab-wide":
+        # AAb_Solver on an SA of the mixed-precision workload's shape (m = 3076,
+        # d = 2048, 25 MB: too large for one cluster, so the grid form runs),
+        # a fixed 200 passes (per-pass latency = ms_per_call / 200)
+        m, d = 3076, 2048
+        SA = W.randn((m, d), 7, scale=1.0 / math.sqrt(m)).to(dev)
+        gw = W.randn((d,), 8).to(dev)
+        delta = torch.empty(d, device=dev)
+        fn = lambda: mihs.aab_solve(SA, gw, 1e-6, 0.0, max_inner=200, delta=delta)
+    elif op in ("aab", "aab-late"):
         SA = mihs.sketch_apply(A, "countsketch", p.m, 3)
         x0 = torch.zeros_like(x)
         if op == "aab-late":  # a gradient from late in a solve (the typical inner solve)

@@ -19,6 +19,7 @@
 // The d-vectors of the recursion (v, d, x) are replicated per block (O(d)
 // work, negligible next to the O(md/CL) products).
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -128,6 +129,14 @@ ClusterPlan plan_cluster(int m, int dp, int sa_type) {
 
 void aab_prepare(int m, int d, int sa_type) { (void)plan_cluster(m, (int)round_up(d, 4), sa_type); }
 
+bool aab_grid_wanted(int m, int d, int sa_type) {
+  if (const char* e = std::getenv("MIHS_AAB_FORM")) {
+    if (std::strcmp(e, "grid") == 0) return true;
+    if (std::strcmp(e, "cluster") == 0) return false;
+  }
+  return plan_cluster(m, (int)round_up(d, 4), sa_type).in_smem == 0;
+}
+
 int launch_aab(const AabLaunch& a, cudaStream_t s) {
   AabParams P = {};
   P.SA = a.SA;
@@ -170,6 +179,11 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   }
   P.sa_scale = a.sa_type == MIHS_SA_FP8E4M3 ? a.sa_scale : nullptr;
   P.scale_ld = (int)((round_up(a.d, 4) + 127) / 128);
+  if (!a.path && a.grid_ws != nullptr && aab_grid_wanted(a.m, a.d, a.sa_type)) {
+    // SA does not fit one cluster's shared memory: spread it over the SMs.
+    const int rc = launch_aab_grid(a, a.grid_ws, s);
+    if (rc != MIHS_ERR_UNSUPPORTED) return rc;
+  }
   const ClusterPlan cp = plan_cluster(a.m, P.dp, a.sa_type);
   if (cp.cl == 0) {
     set_error("aab: no thread-block cluster fits for m=%d d=%d", a.m, a.d);

@@ -218,6 +218,7 @@ struct mihs_sketch_s {
   // λ-path workspace (allocated on the first path solve): split-K partials
   // (P_path × 16 × dp), G and X⁻ (16 × dp each), 16 control blocks and the
   // path's stop counter / flag.
+  void* aab_grid_ws = nullptr;   // global scratch of the single-λ grid AAb kernel (first solve that needs it)
   float* path_partials = nullptr;
   float* path_aab_ws = nullptr;  // global scratch of the cooperative multi-λ AAb kernel
   float* path_g = nullptr;
@@ -256,6 +257,35 @@ void set_sa(AabLaunch& a, const mihs_sketch_s* sk) {
     a.sa_type = MIHS_SA_FP32;
     a.ldsa = sk->dp;
   }
+}
+
+// The grid form of AAb_Solver (SA too large for one cluster's shared memory)
+// needs global scratch: the handle's, allocated on first use; its barrier
+// word is zeroed on the solve's stream before every solve.
+int use_grid_ws(mihs_sketch_s* sk, AabLaunch& a, cudaStream_t s) {
+  if (!aab_grid_wanted(a.m, a.d, a.sa_type)) return MIHS_OK;
+  if (sk->aab_grid_ws == nullptr) {
+    const size_t bytes = aab_grid_ws_bytes(a.d);
+    cudaError_t e = cudaMalloc(&sk->aab_grid_ws, bytes);
+    if (e != cudaSuccess) {
+      sk->aab_grid_ws = nullptr;
+      set_error("AAb grid scratch: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+    }
+  }
+  MIHS_CUDA_TRY(cudaMemsetAsync(sk->aab_grid_ws, 0, kAabGridBarBytes, s));
+  a.grid_ws = sk->aab_grid_ws;
+  return MIHS_OK;
+}
+
+// Row-level calls take the grid form's scratch from the stream-ordered pool.
+int use_grid_scratch(AabLaunch& a, StreamScratch& ws, cudaStream_t s) {
+  if (!aab_grid_wanted(a.m, a.d, a.sa_type)) return MIHS_OK;
+  int rc = ws.alloc(aab_grid_ws_bytes(a.d), s);
+  if (rc) return rc;
+  MIHS_CUDA_TRY(cudaMemsetAsync(ws.p, 0, kAabGridBarBytes, s));
+  a.grid_ws = ws.p;
+  return MIHS_OK;
 }
 
 void drop_graph(mihs_sketch_s::GraphSlot& gs) {
@@ -402,7 +432,10 @@ int mihs_device_status(int* code) {
   if (rc) return rc;
   rc = aab_path_device_error(&ab);
   if (rc) return rc;
-  *code = a ? a : (g ? g : (dd ? dd : (pa ? pa : ab)));
+  int gr = 0;
+  rc = aab_grid_device_error(&gr);
+  if (rc) return rc;
+  *code = a ? a : (g ? g : (dd ? dd : (pa ? pa : (ab ? ab : gr))));
   return MIHS_OK;
 }
 
@@ -531,6 +564,9 @@ int mihs_aab_solve_q(const void* SAq, int sa_prec, const float* scales, int64_t 
   a.max_passes = cap_passes(m, d, max_inner);
   a.delta = delta;
   a.passes = passes;
+  StreamScratch ws;
+  int rc = use_grid_scratch(a, ws, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
   return launch_aab(a, static_cast<cudaStream_t>(stream));
 }
 
@@ -552,6 +588,9 @@ int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa, const fl
   a.max_passes = cap_passes(m, d, max_inner);
   a.delta = delta;
   a.passes = passes;
+  StreamScratch ws;
+  rc = use_grid_scratch(a, ws, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
   return launch_aab(a, static_cast<cudaStream_t>(stream));
 }
 
@@ -576,6 +615,9 @@ int mihs_aab_heavy_ball(const float* SA, int64_t m, int64_t d, int64_t ldsa, con
   a.beta = (float)beta;
   a.x = x;
   a.x_prev = x_prev;
+  StreamScratch ws;
+  rc = use_grid_scratch(a, ws, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
   return launch_aab(a, static_cast<cudaStream_t>(stream));
 }
 
@@ -725,6 +767,7 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
   if (sk->cap) cudaStreamDestroy(sk->cap);
   if (sk->dd_partials) cudaFree(sk->dd_partials);
+  if (sk->aab_grid_ws) cudaFree(sk->aab_grid_ws);
   if (sk->path_partials) cudaFree(sk->path_partials);
   if (sk->SAq) cudaFree(sk->SAq);
   if (sk->path_ctl_host) cudaFreeHost(sk->path_ctl_host);
@@ -831,6 +874,8 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   }
   a.ctl = sk->ctl;
   a.hist = sk->hist;
+  rc = use_grid_ws(sk, a, s);
+  if (rc) return rc;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
   const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs, sk->sa_prec};
   bool graph_ran = false;

@@ -104,8 +104,26 @@ struct AabLaunch {
   int64_t path_ldg, path_ldx;
   int* path_ndone;
   int* path_all_done;
+  // Global scratch of the grid form (aab_grid_ws_bytes(d) bytes, barrier
+  // word zeroed); NULL: the grid form is not used.
+  void* grid_ws;
 };
+// Runs one cluster (aab.cu), or — when SA does not fit one cluster's shared
+// memory and a.grid_ws is given — one grid over the SMs (aab_grid.cu).
 int launch_aab(const AabLaunch& a, cudaStream_t s);
+// Single-λ AAb_Solver as one grid that keeps SA in the shared memory of up to
+// every SM.  `ws` holds aab_grid_ws_bytes(d) bytes whose first
+// kAabGridBarBytes hold the grid barrier word, which must be zero before a
+// solve (it returns to zero after every completed launch).  Returns
+// MIHS_ERR_UNSUPPORTED (nothing launched) when SA does not fit.
+constexpr size_t kAabGridBarBytes = 256;
+size_t aab_grid_ws_bytes(int d);
+int launch_aab_grid(const AabLaunch& a, void* ws, cudaStream_t s);
+int aab_grid_device_error(int* code);
+// True when launch_aab would take the grid form given scratch: SA of m × d
+// does not fit in the shared memory of one cluster (MIHS_AAB_FORM=grid or
+// =cluster overrides).
+bool aab_grid_wanted(int m, int d, int sa_type);
 // λ-path mode with all λ in one cooperative grid that keeps SA in the
 // shared memory of all SMs (aab_path.cu); `ws` holds aab_path_ws_floats(dp)
 // floats.  Returns MIHS_ERR_UNSUPPORTED (nothing launched) when SA or d does

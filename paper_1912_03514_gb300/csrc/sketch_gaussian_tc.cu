@@ -14,6 +14,14 @@
 //   * one thread issues four tcgen05.mma.kind::tf32 (K = 8 each) into a
 //     128×256 fp32 accumulator in tensor memory and commits the operand stage
 //     back to the producers.
+// The blocks that share a tile of S (the same sketch rows and rows of A, one
+// per 256-column tile of A) form one thread-block cluster: block r of the
+// cluster generates only its slice of the tile's rows (a contiguous byte
+// range of the swizzled layout) and pushes it into the other blocks' stage by
+// bulk shared::cta → shared::cluster copies that complete on their `full`
+// barrier, and every MMA commit arrives on the `empty` barrier of every block
+// of the cluster (a stage is refilled once all of them have consumed it).
+// So each element of S is generated once, not once per column tile of A.
 // Rings: 3 operand stages (48 KB) and 2 staging stages (32 KB).  The K range is
 // split across blocks (split-K); each block's accumulator goes to a partial
 // buffer that a small kernel sums in a fixed order and scales by 1/√m.
@@ -73,6 +81,42 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Commit that arrives on the barrier at the same offset in every block of
+// `mask` (the blocks of this cluster).
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+// shared::cluster address of the same location in block `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// Bulk copy of `bytes` (multiple of 16) from this block's shared memory to a
+// block of the cluster; completes `bytes` on the barrier `rbar` there.
+__device__ __forceinline__ void bulk_copy_s2c(uint32_t rdst, uint32_t src, uint32_t bytes, uint32_t rbar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   rdst),
+               "r"(src), "r"(bytes), "r"(rbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -129,6 +173,7 @@ struct GaussTcArgs {
   uint32_t k0, k1;      // Philox key
   float* part;          // [gridDim.z][m][dp]
   int dp;
+  int cn;               // blocks per cluster (= column tiles of A, gridDim.x)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -144,6 +189,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   uint64_t* stg_empty = stg_full + kStg;
   uint64_t* accum = stg_empty + kStg;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile uint32_t* gen_abort = tmem_holder + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * TM;             // first sketch row
@@ -152,10 +198,15 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   const int kb1 = min(a.n, kb0 + a.rows_per_split);
   const int nkb = kb1 > kb0 ? (kb1 - kb0 + TK - 1) / TK : 0;
 
+  const int cn = a.cn;
+  const uint32_t crank = cn > 1 ? cluster_rank() : 0u;
+  // This block's slice of the S tile's rows (contiguous bytes: row g of the
+  // swizzled tile occupies bytes [128g, 128g + 128)).
+  const int g_lo = (int)((TM * crank) / (uint32_t)cn), g_hi = (int)((TM * (crank + 1)) / (uint32_t)cn);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], kGenWarps + kTrWarps);  // one arrival per producer warp
-      mbar_init(&empty[s], 1);                    // MMA commit
+      mbar_init(&full[s], 1 + kTrWarps);  // generator leader (+ peers' bytes), transposer warps
+      mbar_init(&empty[s], cn);           // MMA commits of every block of the cluster
     }
     for (int s = 0; s < kStg; ++s) {
       mbar_init(&stg_full[s], 1);                 // TMA expect_tx arrival
@@ -174,6 +225,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  if (cn > 1) cluster_sync_all();  // every block's barriers initialised before any remote access
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -195,9 +247,19 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
           const uint64_t bd = smem_desc_sw128(sA + kk * 32, 16, 1024);
           mma_tf32(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(&empty[s]);
+        if (cn > 1)
+          mma_commit_mc(&empty[s], (uint16_t)((1u << cn) - 1u));
+        else
+          mma_commit(&empty[s]);
       }
       mma_commit(accum);  // fires when every MMA issued above has completed
+      // Drain: the last rounds' commits of every block of the cluster have
+      // arrived here before this block may exit (its barriers stay valid).
+      for (int kb = nkb > kStages ? nkb - kStages : 0; kb < nkb; ++kb)
+        if (!mbar_wait(&empty[kb % kStages], (uint32_t)(kb / kStages) & 1u, kWaitLimitNs)) {
+          atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -251,25 +313,30 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     }
   } else {
     // ------------------------------------------------------------ S generators
-    // Thread g: tile row g mod 128, 16-byte chunks 2h and 2h + 1 with h = g div 128
-    // (two Philox calls per stage; the generation is ALU-bound, so many warps).
+    // Item e of this block's slice: tile row g_lo + e/8, 16-byte chunk e mod 8
+    // (one Philox call, four consecutive K).  The slice is then pushed to the
+    // other blocks of the cluster by the leader (generator thread 0).
     const int g = threadIdx.x - 64;
-    const int gt = g & (TM - 1);
-    const int h = g >> 7;
-    const int gi = i0 + gt;
+    const int nitems = (g_hi - g_lo) * (TK / 4);
+    const uint32_t slice_off = (uint32_t)g_lo * 128u, slice_bytes = (uint32_t)(g_hi - g_lo) * 128u;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      if (kb >= kStages && !mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs)) {
-        atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
-        break;
+      if (kb >= kStages) {
+        // One thread waits (bounded) and every generator takes its verdict, so
+        // that all of them reach the same named barriers.
+        if (g == 0) *gen_abort = mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs) ? 0u : 1u;
+        named_sync(1, kGenWarps * 32);
+        if (*gen_abort) {
+          if (g == 0) atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
       }
       unsigned char* sS = base + (size_t)s * kStageBytes;
-      unsigned char* row = sS + (gt >> 3) * 1024 + (gt & 7) * 128;
       const int kbase = kb0 + kb * TK;
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * h + cc;
+      for (int e = g; e < nitems; e += kGenWarps * 32) {
+        const int gt = g_lo + (e >> 3), c = e & 7;
+        const int gi = i0 + gt;
         const int j0 = kbase + 4 * c;
         uint4 out = make_uint4(0u, 0u, 0u, 0u);
         if (gi < a.m && j0 < kb1) {
@@ -279,11 +346,19 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
           out = make_uint4(to_tf32(za.x), j0 + 1 < kb1 ? to_tf32(za.y) : 0u,
                            j0 + 2 < kb1 ? to_tf32(zb.x) : 0u, j0 + 3 < kb1 ? to_tf32(zb.y) : 0u);
         }
-        *reinterpret_cast<uint4*>(row + ((c ^ (gt & 7)) << 4)) = out;
+        *reinterpret_cast<uint4*>(sS + (size_t)gt * 128 + ((c ^ (gt & 7)) << 4)) = out;
       }
-      fence_async_shared();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&full[s]);
+      fence_async_shared();            // the slice → visible to the async proxy (MMA, bulk copies)
+      named_sync(1, kGenWarps * 32);   // every generator has written its part
+      if (g == 0) {
+        // This block's stage is complete once the peers' slices have landed.
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(TM * 128) - slice_bytes);
+        const uint32_t src = smem_u32(sS) + slice_off;
+        for (int p = 1; p < cn; ++p) {
+          const uint32_t peer = (crank + (uint32_t)p) % (uint32_t)cn;
+          bulk_copy_s2c(mapa(src, peer), src, slice_bytes, mapa(smem_u32(&full[s]), peer));
+        }
+      }
     }
     if (warp >= 6) goto done;  // warps 2–5 (one per TMEM lane quarter) run the epilogue
     {
@@ -317,6 +392,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
 done:
   tc_fence_before();
   __syncthreads();
+  if (cn > 1) cluster_sync_all();  // no block exits while a peer may still copy into it
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -377,8 +453,43 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   }
   const int tn = (int)((d + TN - 1) / TN), tm = (int)((m + TM - 1) / TM);
   const int64_t kblocks = (n + TK - 1) / TK;
-  int64_t KS = num_sms() / (int64_t)(tn * tm);
-  if (KS < 1) KS = 1;
+  MIHS_CUDA_TRY(cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  // One cluster per (sketch-row tile, K split) holds the tn column tiles.
+  // Clusters that run at once on this GPU (a cluster needs tn SMs of one GPC):
+  int active = 0;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)tn;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)tn, 1, 1);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&active, (void*)gauss_tc_kernel, &cfg) != cudaSuccess || active < 1) {
+      cudaGetLastError();
+      active = num_sms() / tn;
+    }
+  }
+  // K splits: fill whole waves of clusters (at least 8 K-blocks per split).
+  int64_t KS = 1;
+  {
+    double best = 0.0;
+    const int64_t kmax = kblocks / 8 > 1 ? kblocks / 8 : 1;
+    for (int64_t ks = 1; ks <= kmax && ks <= 64; ++ks) {
+      const int64_t cl = (int64_t)tm * ks;
+      const int64_t waves = (cl + active - 1) / active;
+      const double eff = (double)cl / (double)(waves * active);
+      // prefer fewer splits (less partial traffic) unless the waves fill better
+      if (eff > best + 0.02) {
+        best = eff;
+        KS = ks;
+      }
+    }
+  }
   if (KS > kblocks) KS = kblocks;
   const int rows_per_split = (int)(((n + KS - 1) / KS + TK - 1) / TK * TK);
   KS = (n + rows_per_split - 1) / rows_per_split;
@@ -395,9 +506,22 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   args.k1 = (uint32_t)(seed >> 32);
   args.part = static_cast<float*>(scratch.p);
   args.dp = dp;
-  MIHS_CUDA_TRY(cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-  gauss_tc_kernel<<<dim3(tn, tm, (unsigned)KS), kThreads, kSmemBytes, s>>>(tmap, args);
-  MIHS_CHECK_LAUNCH();
+  args.cn = tn;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)tn;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)tn, (unsigned)tm, (unsigned)KS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, gauss_tc_kernel, tmap, args));
+  }
   const long long tot = (long long)m * d;
   gauss_tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
       args.part, (int)KS, (int)m, (int)d, dp, (float)(1.0 / std::sqrt((double)m)), SA, ldsa);

@@ -188,7 +188,10 @@ def _sketch_bound(family, A, m, seed, n):
     return (gamma(ks) + 2.0 ** -10 + 2.0 ** -11 + 16 * U32) * (S @ absA) + 1e-30
 
 
-SKETCH_CASES = [(4096, 256, 256), (3000, 130, 64), (1000, 33, 17), (8192, 1024, 100), (777, 2048, 31)]
+# n, d, m: column tiles of A (256 wide) = 1 … 8 blocks sharing each S tile,
+# one or several sketch-row tiles (128), ragged K splits and widths
+SKETCH_CASES = [(4096, 256, 256), (3000, 130, 64), (1000, 33, 17), (8192, 1024, 100), (777, 2048, 31),
+                (5000, 700, 300), (2049, 1500, 129), (100, 520, 40), (12000, 2048, 260)]
 
 
 @pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
