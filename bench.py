@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
-                                            "gaussian", "countsketch", "srht"],
+                                            "gaussian", "gaussian-bf16", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
 
@@ -610,7 +610,10 @@ def run_mixed(args, dev, ws):
     x = torch.empty(d, dtype=torch.float64, device=dev)
     out = {"workload": f"{p.name}, SNR 40 dB, λ = 1e-6 (sd {p.sd:.1f}, κ(H) ≈ 1e6), Gaussian m = {p.m}, "
                        f"refinement to residual {tol:g}; A = {4 * n * d / 1e9:.1f} GB",
-           "unit": "solves/s", "by_sa_precision": {}}
+           "unit": "solves/s",
+           "sketch_operands": "fp32 SA: tf32 S and A; bf16 / fp8 SA: S·A formed from bf16 S and A "
+                              "(fp32 accumulation), then stored in that precision",
+           "by_sa_precision": {}}
     xs = None
     if args.mixed_oracle:
         from oracle import mihs_oracle as o
@@ -700,6 +703,9 @@ def run_profile_op(args, local):
         skp = mihs.Sketch(q.A, "gaussian", m, seed=3)
         Xp = torch.empty(16, q.d, device=dev)
         fn = lambda: skp.solve_path(q.A, q.b, lams, sds=sds, tol=1e-6, max_outer=100, X=Xp, want_info=False)
+    elif op == "gaussian-bf16":
+        SA = torch.empty(p.m, p.d, device=dev)
+        fn = lambda: mihs.sketch_gaussian_bf16(A, p.m, 3, SA=SA)
     elif op == "backward":
         v = W.randn((p.d,), seed=6, scale=0.01).to(dev)
         fn = lambda: mihs.backward_grads(A, b, x, v)

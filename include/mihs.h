@@ -101,6 +101,18 @@ int mihs_sketch_apply(const float* A, int64_t n, int64_t d, int64_t lda,
                       int family, int64_t m, uint64_t seed,
                       float* SA, int64_t ldsa, void* stream);
 
+/* The Gaussian sketch of mihs_sketch_apply (Lemma 3, case iv) formed from
+ * bf16 operands on the tensor cores: every entry of S and of A is rounded to
+ * bf16 (round to nearest even) and the products are accumulated in fp32,
+ * then scaled by 1/√m.  S is the same Philox/Box–Muller matrix as the fp32
+ * form.  The sketch only preconditions Algorithm 1 (the fixed point is where
+ * the exact gradient vanishes, Section 3.1), so the rounding changes the
+ * rate, not the solution.  Arguments, scratch and errors as
+ * mihs_sketch_apply; UNSUPPORTED when the tensor-core path is unavailable. */
+int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda,
+                              int64_t m, uint64_t seed, float* SA, int64_t ldsa,
+                              void* stream);
+
 /* Gradient step of Algorithm 1: g = Aᵀ(b − Ax) − λx, reading A once.
  *   b (n), x (d) inputs; g (d) output.  λ ≥ 0.
  * Allocates stream-ordered scratch for the split-K partial sums (one d-vector
@@ -199,7 +211,10 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family,
 
 /* Recompute the handle's SA for a new matrix of the same shape (n×d) and/or
  * a new seed, reusing its memory (no allocation of the handle's own buffers;
- * the sketch kernels' stream-ordered scratch as in mihs_sketch_apply).
+ * the sketch kernels' stream-ordered scratch as in mihs_sketch_apply).  A
+ * Gaussian handle whose SA is stored in bf16 or fp8
+ * (mihs_sketch_set_precision) forms S·A from bf16 operands
+ * (mihs_sketch_gaussian_bf16) before quantising it.
  * Errors: INVALID_ARG, CUDA, OOM. */
 int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed,
                   void* stream);

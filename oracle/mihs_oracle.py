@@ -30,6 +30,9 @@ Contents and the passage each follows:
   exact_solve_dual ..... the plain definition through the dual:
                           x* = Aᵀ(AAᵀ + λI)⁻¹b.
   hutchinson_sd ........ Algorithm 4 (inexact Hutchinson estimate of sd).
+  gaussian_sketch_bf16 . the Gaussian sketch from bf16-rounded S and A, summed
+                          exactly (the operand format of the bf16 tensor-core
+                          sketch; a format, not the paper's).
   quantize_sa .......... storage of SA in bf16, or fp8 e4m3 with one scale per
                           128 × 128 tile (a format, not the paper's: the
                           sketch only preconditions, Section 3.1); torch's
@@ -137,6 +140,26 @@ def gaussian_sketch_rows(rows, n: int, m: int, seed: int) -> np.ndarray:
 
 def gaussian_sketch_matrix(m: int, n: int, seed: int) -> np.ndarray:
     return gaussian_sketch_rows(np.arange(m), n, m, seed)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), through torch's CPU
+    cast of the fp32 value; returned as fp64."""
+    import torch
+    t = torch.as_tensor(np.asarray(x, dtype=np.float32))
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def gaussian_sketch_bf16(A: np.ndarray, m: int, seed: int) -> np.ndarray:
+    """The Gaussian sketch formed from bf16 operands (a storage format for
+    the preconditioner, not the paper's: the sketch only preconditions,
+    Section 3.1): SA = (1/√m)·Z̃·Ã with Z̃ the N(0,1) matrix of
+    gaussian_sketch_rows (before the 1/√m) and Ã = A, each entry rounded to
+    bf16, the products summed exactly (fp64)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Z = gaussian_sketch_matrix(m, n, seed) * math.sqrt(m)
+    return (round_bf16(Z) @ round_bf16(A)) / math.sqrt(m)
 
 
 def countsketch_hash(n: int, m: int, seed: int):

@@ -471,6 +471,25 @@ int mihs_sketch_apply(const float* A, int64_t n, int64_t d, int64_t lda, int fam
   return rc;
 }
 
+int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
+                              float* SA, int64_t ldsa, void* stream) {
+  set_error("");
+  int rc = check_matrix(A, n, d, lda, "mihs_sketch_gaussian_bf16");
+  if (rc) return rc;
+  MIHS_ARG(SA != nullptr, "mihs_sketch_gaussian_bf16: null SA");
+  MIHS_ARG(m >= 1 && m <= n, "mihs_sketch_gaussian_bf16: m=%lld outside [1, n]", (long long)m);
+  MIHS_ARG(ldsa >= d, "mihs_sketch_gaussian_bf16: ldsa < d");
+  if (!gaussian_tc_available()) {
+    set_error("mihs_sketch_gaussian_bf16: the tensor-core sketch is unavailable (no cuTensorMapEncodeTiled)");
+    return MIHS_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  timing_begin(kTimerSketch, s);
+  rc = sketch_gaussian_tc(A, n, d, lda, m, seed, SA, ldsa, s, true);
+  timing_end(kTimerSketch, s);
+  return rc;
+}
+
 int mihs_timing(int on) {
   Timing& t = timing_state();
   std::lock_guard<std::mutex> lk(t.mu);
@@ -692,7 +711,12 @@ int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, 
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_resketch");
   if (rc) return rc;
   sk->seed = seed;
-  rc = mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
+  // A handle whose SA is stored quantised forms a Gaussian S·A from bf16
+  // operands too (fp32 accumulation): the sketch only preconditions.
+  if (sk->family == MIHS_GAUSSIAN && sk->sa_prec != MIHS_SA_FP32)
+    rc = mihs_sketch_gaussian_bf16(A, sk->n, sk->d, lda, sk->m, seed, sk->SA, sk->dp, stream);
+  else
+    rc = mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
   if (rc || sk->sa_prec == MIHS_SA_FP32) return rc;
   return launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sk->sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
                             static_cast<cudaStream_t>(stream));

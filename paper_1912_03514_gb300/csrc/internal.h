@@ -141,8 +141,9 @@ int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m
                     uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 // tcgen05 version of the Gaussian sketch (sketch_gaussian_tc.cu).
 bool gaussian_tc_available();
+// bf16 = true: S and A rounded to bf16 (kind::f16 MMAs, fp32 accumulation).
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
-                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s, bool bf16 = false);
 int gauss_tc_device_error(int* code);
 int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                        uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);

@@ -40,9 +40,13 @@ namespace {
 
 constexpr int TM = 128;          // sketch rows per tile (MMA M)
 constexpr int TN = 256;          // columns of A per tile (MMA N)
-constexpr int TK = 32;           // rows of A per stage (4 MMAs of K = 8)
+constexpr int TK = 32;           // rows of A per TMA load (a tf32 stage: 4 MMAs of K = 8)
 constexpr int kStages = 3;       // operand ring
 constexpr int kStg = 2;          // staging ring (TMA → transposers)
+// K rows per operand stage: 32 tf32 or 64 bf16 values fill one 128-byte
+// swizzled row, so both operand types use the same layout and descriptors.
+template <bool BF>
+constexpr int stage_k() { return BF ? 64 : 32; }
 constexpr int kGenWarps = 16;    // S generators (warps 2–17); warps 2–5 then run the epilogue
 constexpr int kTrWarps = 4;      // A transposers (warps 18–21)
 constexpr int kThreads = (2 + kGenWarps + kTrWarps) * 32;  // warp 0: MMA, warp 1: TMA
@@ -63,17 +67,38 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
-                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptors: D f32 (bits 4–5 = 1), A and B both K-major,
+// N/8 at bit 17, M/16 at bit 24; operand format at bits 7–9 / 10–12:
+// kind::tf32 takes tf32 (2), kind::f16 takes bf16 (1).
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) | (0u << 16) |
+                                ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (0u << 16) |
+                                ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
+      : "memory");
+}
+
+// Two fp32 values → one bf16x2 word (round to nearest even); `lo` lands in
+// the low half (the lower K index).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -176,8 +201,13 @@ struct GaussTcArgs {
   int cn;               // blocks per cluster (= column tiles of A, gridDim.x)
 };
 
+// BF = false: tf32 operands (kind::tf32, 32 K per stage); BF = true: S and A
+// rounded to bf16 (kind::f16, 64 K per stage, two TMA loads of 32 rows).
+template <bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a) {
+  constexpr int KT = stage_k<BF>();
+  constexpr int NSLOT = KT / TK;  // TMA loads (staging slots) per operand stage
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms.
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -196,7 +226,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   const int c0 = blockIdx.x * TN;             // first column of A
   const int kb0 = blockIdx.z * a.rows_per_split;
   const int kb1 = min(a.n, kb0 + a.rows_per_split);
-  const int nkb = kb1 > kb0 ? (kb1 - kb0 + TK - 1) / TK : 0;
+  const int nkb = kb1 > kb0 ? (kb1 - kb0 + KT - 1) / KT : 0;
 
   const int cn = a.cn;
   const uint32_t crank = cn > 1 ? cluster_rank() : 0u;
@@ -241,11 +271,15 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
         const uint32_t sS = smem_u32(base + (size_t)s * kStageBytes);
         const uint32_t sA = sS + kSBytes;
 #pragma unroll
-        for (int kk = 0; kk < TK / 8; ++kk) {
-          // Both operands K-major: 8-row atoms of 1024 B; K advances 32 bytes.
+        for (int kk = 0; kk < 4; ++kk) {
+          // Both operands K-major: 8-row atoms of 1024 B; each MMA covers 32
+          // bytes of K (8 tf32 or 16 bf16 values).
           const uint64_t ad = smem_desc_sw128(sS + kk * 32, 16, 1024);
           const uint64_t bd = smem_desc_sw128(sA + kk * 32, 16, 1024);
-          mma_tf32(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+          if constexpr (BF)
+            mma_bf16(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+          else
+            mma_tf32(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
         }
         if (cn > 1)
           mma_commit_mc(&empty[s], (uint16_t)((1u << cn) - 1u));
@@ -265,51 +299,76 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   } else if (warp == 1) {
     // ------------------------------------------------------------ TMA loads of A
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStg;
-        const uint32_t ph = (uint32_t)(kb / kStg) & 1u;
-        if (kb >= kStg && !mbar_wait(&stg_empty[s], ph ^ 1u, kWaitLimitNs)) {
+      // load j covers rows kb0 + 32j … (NSLOT loads per operand stage)
+      for (int j = 0; j < nkb * NSLOT; ++j) {
+        const int s = j % kStg;
+        const uint32_t ph = (uint32_t)(j / kStg) & 1u;
+        if (j >= kStg && !mbar_wait(&stg_empty[s], ph ^ 1u, kWaitLimitNs)) {
           atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
           break;
         }
         mbar_arrive_expect_tx(&stg_full[s], kABytes);
-        tma_load_2d(stg + (size_t)s * kABytes, &tmap_a, c0, kb0 + kb * TK, &stg_full[s]);
+        tma_load_2d(stg + (size_t)s * kABytes, &tmap_a, c0, kb0 + j * TK, &stg_full[s]);
       }
     }
     __syncwarp();
   } else if (warp >= 2 + kGenWarps) {
     // ------------------------------------------------ A transposers: staging → K-major
     const int tt = threadIdx.x - (2 + kGenWarps) * 32;  // 0..127: columns tt, tt + 128
-    for (int kb = 0; kb < nkb; ++kb) {
+    bool stop = false;
+    for (int kb = 0; kb < nkb && !stop; ++kb) {
       const int s = kb % kStages;
-      const int q = kb % kStg;
-      if (!mbar_wait(&stg_full[q], (uint32_t)(kb / kStg) & 1u, kWaitLimitNs) ||
-          (kb >= kStages && !mbar_wait(&empty[s], ((uint32_t)(kb / kStages) & 1u) ^ 1u, kWaitLimitNs))) {
+      if (kb >= kStages && !mbar_wait(&empty[s], ((uint32_t)(kb / kStages) & 1u) ^ 1u, kWaitLimitNs)) {
         atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
         break;
       }
-      const float* src = reinterpret_cast<const float*>(stg + (size_t)q * kABytes);  // [32 rows][256 cols]
       unsigned char* dstA = base + (size_t)s * kStageBytes + kSBytes;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = tt + 128 * h;
-        unsigned char* row = dstA + (c >> 3) * 1024 + (c & 7) * 128;
-#pragma unroll
-        for (int ch = 0; ch < TK / 4; ++ch) {
-          uint4 v;
-          v.x = to_tf32(src[(4 * ch + 0) * TN + c]);
-          v.y = to_tf32(src[(4 * ch + 1) * TN + c]);
-          v.z = to_tf32(src[(4 * ch + 2) * TN + c]);
-          v.w = to_tf32(src[(4 * ch + 3) * TN + c]);
-          *reinterpret_cast<uint4*>(row + ((ch ^ (c & 7)) << 4)) = v;
+      for (int sl = 0; sl < NSLOT; ++sl) {
+        const int j = kb * NSLOT + sl;
+        const int q = j % kStg;
+        if (!mbar_wait(&stg_full[q], (uint32_t)(j / kStg) & 1u, kWaitLimitNs)) {
+          atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
+          stop = true;
+          break;
         }
+        const float* src = reinterpret_cast<const float*>(stg + (size_t)q * kABytes);  // [32 rows][256 cols]
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = tt + 128 * h;
+          unsigned char* row = dstA + (c >> 3) * 1024 + (c & 7) * 128;
+          if constexpr (BF) {
+            // 16-byte chunk ch = 4·sl + cc holds K = 8ch … 8ch + 7 as bf16
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const float* r = src + (size_t)(8 * cc) * TN + c;
+              uint4 v;
+              v.x = pack_bf16x2(r[0 * TN], r[1 * TN]);
+              v.y = pack_bf16x2(r[2 * TN], r[3 * TN]);
+              v.z = pack_bf16x2(r[4 * TN], r[5 * TN]);
+              v.w = pack_bf16x2(r[6 * TN], r[7 * TN]);
+              const int ch = 4 * sl + cc;
+              *reinterpret_cast<uint4*>(row + ((ch ^ (c & 7)) << 4)) = v;
+            }
+          } else {
+#pragma unroll
+            for (int ch = 0; ch < TK / 4; ++ch) {
+              uint4 v;
+              v.x = to_tf32(src[(4 * ch + 0) * TN + c]);
+              v.y = to_tf32(src[(4 * ch + 1) * TN + c]);
+              v.z = to_tf32(src[(4 * ch + 2) * TN + c]);
+              v.w = to_tf32(src[(4 * ch + 3) * TN + c]);
+              *reinterpret_cast<uint4*>(row + ((ch ^ (c & 7)) << 4)) = v;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&stg_empty[q]);  // this warp's reads of the slot are done
       }
+      if (stop) break;
       fence_async_shared();  // generic-proxy writes → visible to the tensor core
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&stg_empty[q]);
-        mbar_arrive(&full[s]);
-      }
+      if (lane == 0) mbar_arrive(&full[s]);
     }
   } else {
     // ------------------------------------------------------------ S generators
@@ -317,7 +376,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     // (one Philox call, four consecutive K).  The slice is then pushed to the
     // other blocks of the cluster by the leader (generator thread 0).
     const int g = threadIdx.x - 64;
-    const int nitems = (g_hi - g_lo) * (TK / 4);
+    const int nitems = (g_hi - g_lo) * 8;
     const uint32_t slice_off = (uint32_t)g_lo * 128u, slice_bytes = (uint32_t)(g_hi - g_lo) * 128u;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages;
@@ -333,18 +392,42 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
         }
       }
       unsigned char* sS = base + (size_t)s * kStageBytes;
-      const int kbase = kb0 + kb * TK;
+      const int kbase = kb0 + kb * KT;
       for (int e = g; e < nitems; e += kGenWarps * 32) {
         const int gt = g_lo + (e >> 3), c = e & 7;
         const int gi = i0 + gt;
-        const int j0 = kbase + 4 * c;
         uint4 out = make_uint4(0u, 0u, 0u, 0u);
-        if (gi < a.m && j0 < kb1) {
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), (uint32_t)gi, kTagGaussian, 0u), a.k0, a.k1);
-          const float2 za = box_muller_fast(w.x, w.y);
-          const float2 zb = box_muller_fast(w.z, w.w);
-          out = make_uint4(to_tf32(za.x), j0 + 1 < kb1 ? to_tf32(za.y) : 0u,
-                           j0 + 2 < kb1 ? to_tf32(zb.x) : 0u, j0 + 3 < kb1 ? to_tf32(zb.y) : 0u);
+        if constexpr (BF) {
+          // chunk c: K = kbase + 8c … + 7, two Philox counters
+          const int j0 = kbase + 8 * c;
+          if (gi < a.m && j0 < kb1) {
+            float z[8];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const uint4 w = philox4x32_10(make_uint4((uint32_t)((j0 >> 2) + hh), (uint32_t)gi, kTagGaussian, 0u),
+                                            a.k0, a.k1);
+              const float2 za = box_muller_fast(w.x, w.y);
+              const float2 zb = box_muller_fast(w.z, w.w);
+              z[4 * hh + 0] = za.x;
+              z[4 * hh + 1] = za.y;
+              z[4 * hh + 2] = zb.x;
+              z[4 * hh + 3] = zb.y;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (j0 + q >= kb1) z[q] = 0.f;
+            out = make_uint4(pack_bf16x2(z[0], z[1]), pack_bf16x2(z[2], z[3]), pack_bf16x2(z[4], z[5]),
+                             pack_bf16x2(z[6], z[7]));
+          }
+        } else {
+          const int j0 = kbase + 4 * c;
+          if (gi < a.m && j0 < kb1) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), (uint32_t)gi, kTagGaussian, 0u), a.k0, a.k1);
+            const float2 za = box_muller_fast(w.x, w.y);
+            const float2 zb = box_muller_fast(w.z, w.w);
+            out = make_uint4(to_tf32(za.x), j0 + 1 < kb1 ? to_tf32(za.y) : 0u,
+                             j0 + 2 < kb1 ? to_tf32(zb.x) : 0u, j0 + 3 < kb1 ? to_tf32(zb.y) : 0u);
+          }
         }
         *reinterpret_cast<uint4*>(sS + (size_t)gt * 128 + ((c ^ (gt & 7)) << 4)) = out;
       }
@@ -433,7 +516,10 @@ EncodeTiledFn encode_fn() {
 bool gaussian_tc_available() { return encode_fn() != nullptr; }
 
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
-                       int64_t ldsa, cudaStream_t s) {
+                       int64_t ldsa, cudaStream_t s, bool bf16) {
+  using KernFn = void (*)(const CUtensorMap, const GaussTcArgs);
+  const KernFn kern = bf16 ? gauss_tc_kernel<true> : gauss_tc_kernel<false>;
+  const int KT = bf16 ? stage_k<true>() : stage_k<false>();
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) {
     set_error("gaussian sketch: cuTensorMapEncodeTiled unavailable");
@@ -452,8 +538,8 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
     return MIHS_ERR_UNSUPPORTED;
   }
   const int tn = (int)((d + TN - 1) / TN), tm = (int)((m + TM - 1) / TM);
-  const int64_t kblocks = (n + TK - 1) / TK;
-  MIHS_CUDA_TRY(cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  const int64_t kblocks = (n + KT - 1) / KT;
+  MIHS_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   // One cluster per (sketch-row tile, K split) holds the tn column tiles.
   // Clusters that run at once on this GPU (a cluster needs tn SMs of one GPC):
   int active = 0;
@@ -469,29 +555,28 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
     cfg.dynamicSmemBytes = kSmemBytes;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&active, (void*)gauss_tc_kernel, &cfg) != cudaSuccess || active < 1) {
+    if (cudaOccupancyMaxActiveClusters(&active, (const void*)kern, &cfg) != cudaSuccess || active < 1) {
       cudaGetLastError();
       active = num_sms() / tn;
     }
   }
-  // K splits: fill whole waves of clusters (at least 8 K-blocks per split).
+  // K splits: minimise waves × (a block's fixed cost + its K blocks), the
+  // fixed cost (barrier set-up, TMEM, pipeline fill, the 128 KB partial
+  // write) counted as 64 K blocks.
   int64_t KS = 1;
   {
-    double best = 0.0;
-    const int64_t kmax = kblocks / 8 > 1 ? kblocks / 8 : 1;
-    for (int64_t ks = 1; ks <= kmax && ks <= 64; ++ks) {
+    double best = 1e300;
+    for (int64_t ks = 1; ks <= kblocks && ks <= 256; ++ks) {
       const int64_t cl = (int64_t)tm * ks;
       const int64_t waves = (cl + active - 1) / active;
-      const double eff = (double)cl / (double)(waves * active);
-      // prefer fewer splits (less partial traffic) unless the waves fill better
-      if (eff > best + 0.02) {
-        best = eff;
+      const double cost = (double)waves * (64.0 + (double)((kblocks + ks - 1) / ks));
+      if (cost < best * 0.999) {
+        best = cost;
         KS = ks;
       }
     }
   }
-  if (KS > kblocks) KS = kblocks;
-  const int rows_per_split = (int)(((n + KS - 1) / KS + TK - 1) / TK * TK);
+  const int rows_per_split = (int)(((n + KS - 1) / KS + KT - 1) / KT * KT);
   KS = (n + rows_per_split - 1) / rows_per_split;
   const int dp = (int)round_up(d, 4);
   StreamScratch scratch;
@@ -520,7 +605,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, gauss_tc_kernel, tmap, args));
+    MIHS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, tmap, args));
   }
   const long long tot = (long long)m * d;
   gauss_tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(

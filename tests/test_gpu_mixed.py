@@ -1,7 +1,9 @@
-"""Parity of the mixed-precision inner solve: the quantised storage of SA
-(bf16, fp8 e4m3 with tile scales) byte for byte against the oracle's
-quantiser, AAb_Solver on the quantised SA against the oracle's Algorithm 5 on
-the decoded SA, and solves with a quantised SA reaching the same solution."""
+"""Parity of the mixed-precision forms: the quantised storage of SA (bf16,
+fp8 e4m3 with tile scales) byte for byte against the oracle's quantiser,
+AAb_Solver on the quantised SA against the oracle's Algorithm 5 on the
+decoded SA, the Gaussian sketch formed from bf16 operands against the
+oracle's sum of the same rounded operands, and solves with a quantised SA
+reaching the same solution."""
 import math
 
 import numpy as np
@@ -11,7 +13,7 @@ import torch
 from oracle import mihs_oracle as o
 from paper_1912_03514_gb300 import mihs
 from paper_1912_03514_gb300 import workloads as W
-from tests._tol import U32
+from tests._tol import U32, gamma
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -134,3 +136,48 @@ def test_quantised_arguments():
         mihs.quantize_sa(SA, 0)  # fp32 is not a quantised format
     with pytest.raises(ValueError):
         mihs.quantize_sa(SA, "fp16")
+
+
+# ------------------------------------------- Gaussian sketch from bf16 operands
+@pytest.mark.parametrize("n,d,m", [(4096, 256, 256), (5000, 700, 300), (2049, 1500, 129), (100, 520, 40),
+                                   (12000, 2048, 260), (777, 33, 17)])
+def test_gaussian_bf16_sketch_matches_oracle(n, d, m):
+    """S·A from bf16-rounded operands on the tensor cores against the
+    oracle's exact sum of the same rounded operands.  The kernel's S comes
+    from fast fp32 transcendentals, so an entry may round to the neighbouring
+    bf16 value (≤ 2⁻⁷ relative); products are exact in fp32, sums carry γ_K,
+    the 1/√m scale 2u."""
+    lda = (d + 3) // 4 * 4
+    A = W.padded_matrix(n, d, lda, seed=n + 7 * d)
+    seed = 0xBF16 + n
+    Ad = A.to(DEV).as_strided((n, d), (lda, 1))
+    SA = mihs.sketch_gaussian_bf16(Ad, m, seed)
+    SA2 = mihs.sketch_gaussian_bf16(Ad, m, seed)
+    torch.cuda.synchronize()
+    An = A[:, :d].numpy().astype(np.float64)
+    ref = o.gaussian_sketch_bf16(An, m, seed)
+    S = np.abs(o.gaussian_sketch_matrix(m, n, seed))
+    bound = (gamma(n + 16) + 2.0 ** -7 + 4 * U32) * (1 + 2.0 ** -7) * (S @ np.abs(o.round_bf16(An))) + 1e-30
+    got = SA.double().cpu().numpy()
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound)}"
+    assert torch.equal(SA, SA2), "not deterministic"
+
+
+def test_gaussian_handle_with_bf16_storage_forms_sa_in_bf16():
+    """A Gaussian handle stored in bf16 re-forms SA from bf16 operands on
+    resketch (the same bytes as the row-level call), and the refined solve
+    on it still reaches 1e-10."""
+    p = W.problem_small()
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam, refine=3, extended=True)
+    with mihs.Sketch(A, "gaussian", p.m, seed=21) as sk:
+        sa32 = sk.sa().clone()
+        sk.set_precision("bf16")
+        sk.resketch(A, 21)
+        sab = sk.sa().clone()
+        x, info = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-13, max_outer=300)
+    assert torch.equal(sab, mihs.sketch_gaussian_bf16(A, p.m, 21))
+    assert not torch.equal(sab, sa32)
+    assert info.converged and o.rel_error(x.cpu().numpy(), xs) <= 1e-10, info

@@ -571,3 +571,38 @@ def test_dual_mihs_reaches_the_solution(family):
                          rcond=None)[0]
     assert o.rel_error(x, xp) <= 1e-9, info
     assert info["outer"] < 60
+
+
+# ------------------------------------------------- bf16-operand Gaussian sketch
+def _bf16_rne_bits(x: float) -> float:
+    """fp32 → bf16 by integer arithmetic on the fp32 bit pattern (round to
+    nearest, ties to even), independent of torch's cast."""
+    u = int(np.array(x, dtype=np.float32).view(np.uint32))
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return float(np.array(u, dtype=np.uint32).view(np.float32))
+
+
+def test_gaussian_sketch_bf16_brute_force():
+    """Entry by entry: Philox counter (⌊j/4⌋, i, tag, 0), the Box–Muller pair
+    of the entry, both operands rounded by bit arithmetic, an exact sum over
+    j and 1/√m — against the oracle's vectorised form.  Integer A is exact in
+    bf16, so a wrong rounding of S, a wrong word pair or a transposed
+    operand shows."""
+    m, n, d, seed = 3, 9, 4, 0x1234ABCD
+    A = W.randint_matrix((n, d), 17, -4, 4).numpy().astype(np.float64)
+    A[0, 0] = 1 + 3 * 2.0 ** -9  # not a bf16 value: rounds up to 1 + 2⁻⁷
+    k0, k1 = o.seed_key(seed)
+    ref = np.zeros((m, d))
+    for i in range(m):
+        for j in range(n):
+            w = o.philox4x32_10(np.uint64(j // 4), np.uint64(i), o.TAG_GAUSSIAN, 0, k0, k1)
+            pa, pb = (w[0], w[1]) if j % 4 < 2 else (w[2], w[3])
+            z = o.box_muller(pa, pb)[j % 2]
+            zb = _bf16_rne_bits(float(z))
+            for c in range(d):
+                ref[i, c] += zb * _bf16_rne_bits(A[j, c])
+    ref /= math.sqrt(m)
+    got = o.gaussian_sketch_bf16(A, m, seed)
+    assert np.allclose(got, ref, rtol=1e-14, atol=1e-14)
+    assert _bf16_rne_bits(1 + 2.0 ** -8) == 1.0 and _bf16_rne_bits(1 + 3 * 2.0 ** -9) == 1 + 2.0 ** -7
+    assert o.round_bf16(np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -9]))[1] == 1 + 2.0 ** -7
