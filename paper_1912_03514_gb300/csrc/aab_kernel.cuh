@@ -152,7 +152,56 @@ __device__ __forceinline__ float fused_sweep(const TS* SAc, long long ldc, int n
     ur[c] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   float rsq = 0.f;
-  for (int i = warp; i < nr; i += kWarps) {
+  int i = warp;
+  if constexpr (CH <= 8) {
+    // Two rows per step (i and i + kWarps): independent loads, dots and
+    // shuffle trees in flight together (the sweep is latency-bound).
+    for (; i + kWarps < nr; i += 2 * kWarps) {
+      const TS* row0 = SAc + (long long)i * ldc;
+      const TS* row1 = row0 + (long long)kWarps * ldc;
+      const float* srow0 = scales != nullptr ? scales + (size_t)((r0 + i) >> 7) * sld : nullptr;
+      const float* srow1 = scales != nullptr ? scales + (size_t)((r0 + i + kWarps) >> 7) * sld : nullptr;
+      float4 a[CH], b[CH];
+      float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int j = 4 * lane + 128 * c;
+        a[c] = j < dp ? load_sa4<TS>(row0, j, d, vec, srow0 != nullptr ? srow0[c] : 1.f)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[c] = j < dp ? load_sa4<TS>(row1, j, d, vec, srow1 != nullptr ? srow1[c] : 1.f)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        s0 = fmaf(a[c].x, vr[c].x, s0);
+        s1 = fmaf(a[c].y, vr[c].y, s1);
+        s0 = fmaf(a[c].z, vr[c].z, s0);
+        s1 = fmaf(a[c].w, vr[c].w, s1);
+        t0 = fmaf(b[c].x, vr[c].x, t0);
+        t1 = fmaf(b[c].y, vr[c].y, t1);
+        t0 = fmaf(b[c].z, vr[c].z, t0);
+        t1 = fmaf(b[c].w, vr[c].w, t1);
+      }
+      float sa_ = s0 + s1, sb_ = t0 + t1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sa_ += __shfl_xor_sync(0xffffffffu, sa_, o);
+        sb_ += __shfl_xor_sync(0xffffffffu, sb_, o);
+      }
+      const float wa = sa_ - theta * p[i], wb = sb_ - theta * p[i + kWarps];
+      rsq = fmaf(wa, wa, rsq);
+      rsq = fmaf(wb, wb, rsq);
+      if (lane == 0) {
+        w[i] = wa;
+        w[i + kWarps] = wb;
+      }
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        ur[c].x = fmaf(b[c].x, wb, fmaf(a[c].x, wa, ur[c].x));
+        ur[c].y = fmaf(b[c].y, wb, fmaf(a[c].y, wa, ur[c].y));
+        ur[c].z = fmaf(b[c].z, wb, fmaf(a[c].z, wa, ur[c].z));
+        ur[c].w = fmaf(b[c].w, wb, fmaf(a[c].w, wa, ur[c].w));
+      }
+    }
+  }
+  for (; i < nr; i += kWarps) {
     const TS* row = SAc + (long long)i * ldc;
     const float* srow = scales != nullptr ? scales + (size_t)((r0 + i) >> 7) * sld : nullptr;
     float4 a[CH];

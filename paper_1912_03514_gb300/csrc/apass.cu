@@ -8,6 +8,8 @@
 // contiguous row range; its warps' partial d-vectors are summed in smem and
 // written as one split-K partial.  A second small kernel sums the partials in
 // a fixed order (deterministic result) and subtracts λx.
+#include <cstdlib>
+
 #include "internal.h"
 
 namespace mihs {
@@ -234,7 +236,14 @@ ApassKernel pick(int64_t d) {
 int apass_num_partials(int64_t n, int64_t d) {
   const ApassKernel k = pick(d);
   const int64_t by_rows = (n + k.rows_per_stage - 1) / k.rows_per_stage;
+  // One block per SM; MIHS_APASS_BLOCKS caps the grid (leaving SMs free for
+  // the inner solves of concurrent solves on other streams).
+  static const int cap = [] {
+    const char* e = std::getenv("MIHS_APASS_BLOCKS");
+    return e != nullptr ? std::atoi(e) : 0;
+  }();
   int64_t P = num_sms();
+  if (cap > 0 && cap < P) P = cap;
   if (P > by_rows) P = by_rows;
   return (int)(P < 1 ? 1 : P);
 }
