@@ -60,11 +60,16 @@ def parse():
     ap.add_argument("--no-backward", action="store_true", help="skip the differentiable-solve leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched λ-path leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (2^21 x 2048)")
+    ap.add_argument("--mixed-tol", type=float, default=3e-14,
+                    help="relative residual the mixed-precision solves refine to")
+    ap.add_argument("--mixed-sample-rows", type=int, default=1 << 17,
+                    help="rows of the same-conditioning sample whose error is checked against the oracle (0: off)")
     ap.add_argument("--mixed-oracle", action="store_true",
                     help="also solve the mixed-precision workload with the fp64 oracle on the host (slow)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
+                                            "aab-wide-bf16",
                                             "gaussian", "gaussian-bf16", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
@@ -415,7 +420,7 @@ def main():
     if not args.no_batched:
         batched = run_batched(args, dev, ws, peaks, peak_src)
 
-    # ---------------- mixed precision: 2²¹ × 2048, κ(H) ≈ 1e6, refined to 1e-10
+    # ---------------- mixed precision: 2²¹ × 2048, κ(H) ≈ 1e6, refined to --mixed-tol
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, dev, ws)
@@ -595,64 +600,101 @@ def run_batched(args, dev, ws, peaks, peak_src):
 def run_mixed(args, dev, ws):
     """2²¹ × 2048, σ_i = 10^(−8(i−1)/2047), λ = 1e-6 (sd ≈ 768, κ(H) ≈ 1e6),
     40 dB SNR, Gaussian sketch with m = 4·sd: compensated-refinement solves to
-    residual 1e-10 with SA stored in fp32, bf16 and fp8 inside AAb_Solver.
-    One step = sketch + refined solve."""
+    a relative residual of --mixed-tol with SA stored in fp32, bf16 and fp8
+    inside AAb_Solver (bf16 / fp8 handles form S·A from bf16 operands).  One
+    step = sketch + refined solve.  The relative error against the oracle is
+    measured on a sample with the same σ profile, λ and sketch size at
+    --mixed-sample-rows rows (the oracle's fp64 Gram of all 2²¹ rows takes
+    minutes on the host; --mixed-oracle does it for the full problem)."""
     import numpy as np
     import torch
 
     from paper_1912_03514_gb300 import mihs
     from paper_1912_03514_gb300 import workloads as W
     n, d, lam = 1 << 21, 2048, 1e-6
+    tol = args.mixed_tol
+    precs = ("fp32", "bf16", "fp8")
+
+    def solve_all(p, A, b, timed):
+        res = {}
+        sk = mihs.Sketch(A, "gaussian", p.m, seed=3)
+        x = torch.empty(d, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        for prec in precs:
+            def step(want_info=False):
+                sk.resketch(A, 3)
+                return sk.solve_refined(A, b, lam, p.sd, tol=tol, max_outer=300, x=x, want_info=want_info)[1]
+            sk.set_precision(prec)
+            try:
+                info = step(want_info=True)
+            except mihs.MihsError as e:  # a quantised SA can stop being an embedding
+                res[prec] = {"status": e.code, "error": str(e).split(":")[0]}
+                continue
+            r = {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
+                 "rel_resid": float(f"{info.rel_resid:.3e}"), "x": x.cpu().numpy().copy()}
+            if timed:
+                torch.cuda.synchronize()
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = max_over_ranks(e0.elapsed_time(e1), ws)
+                r.update({"value": round(ws / (ms / 1e3), 3), "ms_per_step": round(ms, 2)})
+                # per-kernel event times of one more step (host-driven: the
+                # library times each launch on the solve's stream)
+                mihs.timing(True)
+                step()
+                torch.cuda.synchronize()
+                r["kernel_ms"] = {k: round(mihs.timing_read(t)[0], 2) for k, t in
+                                  (("sketch", mihs.TIMER_SKETCH), ("apass", mihs.TIMER_APASS),
+                                   ("apass_dd", mihs.TIMER_APASS_DD), ("aab", mihs.TIMER_AAB))}
+                mihs.timing(False)
+            res[prec] = r
+        sk.close()
+        return res
+
     p = W.make_problem(n, d, W.profile_exponential(d, 8.0), lam, 40.0, seed=1002, device=str(dev), device_rng=True)
-    A, b = p.A, p.b
-    tol = 1e-10
-    sk = mihs.Sketch(A, "gaussian", p.m, seed=3)
-    x = torch.empty(d, dtype=torch.float64, device=dev)
     out = {"workload": f"{p.name}, SNR 40 dB, λ = 1e-6 (sd {p.sd:.1f}, κ(H) ≈ 1e6), Gaussian m = {p.m}, "
-                       f"refinement to residual {tol:g}; A = {4 * n * d / 1e9:.1f} GB",
+                       f"refinement to relative residual {tol:g}; A = {4 * n * d / 1e9:.1f} GB",
            "unit": "solves/s",
            "sketch_operands": "fp32 SA: tf32 S and A; bf16 / fp8 SA: S·A formed from bf16 S and A "
                               "(fp32 accumulation), then stored in that precision",
-           "by_sa_precision": {}}
-    xs = None
+           "by_sa_precision": solve_all(p, p.A, p.b, True)}
     if args.mixed_oracle:
         from oracle import mihs_oracle as o
-        xs = o.exact_solve(A.cpu().numpy(), b.cpu().numpy(), lam, refine=2)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream()
-    for prec in ("fp32", "bf16", "fp8"):
-        def step(want_info=False):
-            sk.resketch(A, 3)
-            return sk.solve_refined(A, b, lam, p.sd, tol=tol, max_outer=300, x=x, want_info=want_info)[1]
-        sk.set_precision(prec)
-        try:
-            info = step(want_info=True)
-        except mihs.MihsError as e:  # a quantised SA can stop being an embedding
-            out["by_sa_precision"][prec] = {"status": e.code, "error": str(e).split(":")[0]}
-            continue
-        torch.cuda.synchronize()
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1), ws)
-        r = {"value": round(ws / (ms / 1e3), 3), "ms_per_step": round(ms, 2), "status": info.status,
-             "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
-             "rel_resid": float(f"{info.rel_resid:.3e}")}
-        # per-kernel event times of one more step (host-driven: the library
-        # times each launch on the solve's stream)
-        mihs.timing(True)
-        step()
-        torch.cuda.synchronize()
-        r["kernel_ms"] = {k: round(mihs.timing_read(t)[0], 2) for k, t in
-                          (("sketch", mihs.TIMER_SKETCH), ("apass", mihs.TIMER_APASS),
-                           ("apass_dd", mihs.TIMER_APASS_DD), ("aab", mihs.TIMER_AAB))}
-        mihs.timing(False)
-        if xs is not None:
-            from oracle import mihs_oracle as o
-            r["rel_err_vs_oracle"] = float(f"{o.rel_error(x.cpu().numpy(), xs):.3e}")
-        out["by_sa_precision"][prec] = r
-    sk.close()
+        xs = o.exact_solve(p.A.cpu().numpy(), p.b.cpu().numpy(), lam, refine=2, dd=True)
+        for r in out["by_sa_precision"].values():
+            if "x" in r:
+                r["rel_err_vs_oracle"] = float(f"{o.rel_error(r['x'], xs):.3e}")
+    for r in out["by_sa_precision"].values():
+        r.pop("x", None)
+    del p
+    torch.cuda.empty_cache()
+    if args.mixed_sample_rows > 0:
+        from oracle import mihs_oracle as o
+        ns = args.mixed_sample_rows
+        q = W.make_problem(ns, d, W.profile_exponential(d, 8.0), lam, 40.0, seed=1012, device=str(dev),
+                           device_rng=True)
+        res = solve_all(q, q.A, q.b, False)
+        # the plain fp32 path (fp32 iterate and gradient, no refinement) on the
+        # same sample: its error floor at κ(H) ≈ 1e6
+        with mihs.Sketch(q.A, "gaussian", q.m, seed=3) as skp:
+            xp, ip = skp.solve(q.A, q.b, lam, q.sd, tol=1e-9, max_outer=150)
+        res["plain_fp32_no_refinement"] = {"status": ip.status, "outer_iters": ip.outer_iters,
+                                           "inner_iters": ip.inner_iters_total,
+                                           "rel_resid": float(f"{ip.rel_resid:.3e}"),
+                                           "x": xp.double().cpu().numpy()}
+        t0 = time.time()
+        xs = o.exact_solve(q.A.cpu().numpy(), q.b.cpu().numpy(), lam, refine=2, dd=True)
+        t_or = time.time() - t0
+        for r in res.values():
+            if "x" in r:
+                r["rel_err_vs_oracle"] = float(f"{o.rel_error(r.pop('x'), xs):.3e}")
+        out["accuracy_sample"] = {
+            "workload": f"{q.name}: the same σ profile, λ, SNR and m = {q.m} on {ns} rows",
+            "oracle": "fp64 Gram + Cholesky, 2 refinement steps with a double-double residual (host C)",
+            "oracle_s": round(t_or, 1), "by_sa_precision": res}
     return out
 
 
@@ -669,15 +711,20 @@ def run_profile_op(args, local):
     x = W.randn((p.d,), seed=5, scale=0.01).to(dev)
     g = torch.empty(p.d, device=dev)
     op = args.profile_op
-    if op == "aab-wide":
+    if op in ("aab-wide", "aab-wide-bf16"):
         # AAb_Solver on an SA of the mixed-precision workload's shape (m = 3076,
-        # d = 2048, 25 MB: too large for one cluster, so the grid form runs),
-        # a fixed 200 passes (per-pass latency = ms_per_call / 200)
+        # d = 2048, 25 MB in fp32, 12.6 MB in bf16: too large for one cluster,
+        # so the grid form runs), a fixed 200 passes (per-pass latency =
+        # ms_per_call / 200)
         m, d = 3076, 2048
         SA = W.randn((m, d), 7, scale=1.0 / math.sqrt(m)).to(dev)
         gw = W.randn((d,), 8).to(dev)
         delta = torch.empty(d, device=dev)
-        fn = lambda: mihs.aab_solve(SA, gw, 1e-6, 0.0, max_inner=200, delta=delta)
+        if op == "aab-wide":
+            fn = lambda: mihs.aab_solve(SA, gw, 1e-6, 0.0, max_inner=200, delta=delta)
+        else:
+            q, sc = mihs.quantize_sa(SA, "bf16")
+            fn = lambda: mihs.aab_solve_q(q, "bf16", sc, d, gw, 1e-6, 0.0, max_inner=200, delta=delta)
     elif op in ("aab", "aab-late"):
         SA = mihs.sketch_apply(A, "countsketch", p.m, 3)
         x0 = torch.zeros_like(x)

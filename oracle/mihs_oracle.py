@@ -17,7 +17,10 @@ Contents and the passage each follows:
                           (iii) SRHT, (iv) Gaussian with entries N(0, 1/m)
                           (proof of Lemma 3), all with E[SᵀS] = I (Section 3.1,
                           text after Algorithm 1).
-  exact_solve .......... the plain definition (Cholesky of AᵀA+λI, fp64).
+  exact_solve .......... the plain definition (Cholesky of AᵀA+λI, fp64),
+                          refined with a residual in extended precision or
+                          in double-double (gradient_dd, plain C in
+                          resid_dd.c: TwoSum/TwoProduct, Ogita–Rump–Oishi 2005).
   svd_solve ............ closed form x* = Σ σᵢ²/(σᵢ²+λ)·(uᵢᵀb/σᵢ)·vᵢ (Eq. tsvdsol).
   stat_dim ............. sd_λ(A) = Σ σᵢ²/(σᵢ²+λ) (Section 1; proof of Lemma 3).
   gradient ............. g = Aᵀ(b − Ax) − λx (Algorithm 1, gradient step).
@@ -57,6 +60,7 @@ the design notes with its justification):
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -261,13 +265,16 @@ def gradient(A, b, x, lam):
     return A.T @ r - lam * x
 
 
-def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16, extended: bool = False):
+def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16, extended: bool = False,
+                dd: bool = False):
     """x* = (AᵀA + λI)⁻¹Aᵀb: fp64 Gram matrix (row blocks summed in order),
     Cholesky, two triangular solves, then `refine` steps of iterative
     refinement x += H⁻¹(Aᵀ(b−Ax) − λx).  With `extended`, the refinement
     residual is formed in numpy's extended precision (np.longdouble: 64-bit
     significand on x86-64, IEEE quad on aarch64), which makes the result
-    accurate to ~κ(H)·u_ext instead of ~κ(H)·u₆₄."""
+    accurate to ~κ(H)·u_ext instead of ~κ(H)·u₆₄; with `dd`, in
+    double-double by gradient_dd (fp32 A and b), which does the same at
+    large sizes where software quad is too slow."""
     n, d = np.shape(A)
     H = np.zeros((d, d))
     Atb = np.zeros(d)
@@ -284,9 +291,38 @@ def exact_solve(A, b, lam, refine: int = 2, row_block: int = 1 << 16, extended: 
 
     x = hsolve(Atb)
     for _ in range(refine):
-        r = gradient_extended(A, b, x, lam, row_block) if extended else gradient_blocked(A, b, x, lam, row_block)
+        if dd:
+            gh, gl = gradient_dd(A, b, x, lam)
+            r = gh + gl
+        elif extended:
+            r = gradient_extended(A, b, x, lam, row_block)
+        else:
+            r = gradient_blocked(A, b, x, lam, row_block)
         x = x + hsolve(np.asarray(r, dtype=np.float64))
     return x
+
+
+def gradient_dd(A, b, x, lam, nthreads: int | None = None):
+    """g = Aᵀ(b − Ax) − λx for fp32 A and b and fp64 x, every product and sum
+    in double-double (Ogita, Rump & Oishi 2005), by the C helper
+    oracle/resid_dd.c.  Returns (hi, lo) fp64 arrays, g = hi + lo."""
+    from oracle import _c
+    A = np.asarray(A)
+    if A.dtype != np.float32:
+        raise TypeError("gradient_dd takes the fp32 data itself")
+    n, d = A.shape
+    if A.strides[1] != 4 or A.strides[0] % 4:
+        A = np.ascontiguousarray(A)
+    lda = A.strides[0] // 4
+    b32 = np.ascontiguousarray(b, dtype=np.float32)
+    x64 = np.ascontiguousarray(x, dtype=np.float64)
+    gh, gl = np.empty(d), np.empty(d)
+    nt = nthreads or max(1, min(os.cpu_count() or 1, 64))
+    rc = _c.lib().oracle_gradient_dd(A.ctypes.data, n, d, lda, b32.ctypes.data, x64.ctypes.data, float(lam),
+                                     int(nt), gh.ctypes.data, gl.ctypes.data)
+    if rc:
+        raise MemoryError("oracle_gradient_dd failed")
+    return gh, gl
 
 
 def gradient_extended(A, b, x, lam, row_block: int = 1 << 14):

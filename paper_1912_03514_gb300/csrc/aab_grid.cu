@@ -70,41 +70,80 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   return v;
 }
 
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier over gridDim.x blocks.  Block 0 adds 2³¹ − (G − 1), the
 // others 1: the word's top bit flips exactly when the last block arrives and
-// the low bits return to their value before the barrier.  Returns false
-// (in every thread of the block) if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* s_ok) {
-  __syncthreads();
+// the low bits return to their value before the barrier.  Each block knows
+// the top bit to wait for from the word's top bit when the launch began
+// (read before its first arrival, so no flip can have happened yet) and the
+// number of barriers it has passed: the arrival is a release reduction with
+// no result to wait for, the wait an acquire load, and no separate fences.
+// Returns false (in every thread of the block) if the wait ran out.
+struct GridBarrier {
+  unsigned int* word;
+  unsigned int expect;  // top bit after the next barrier (thread 0)
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier& gb, int* s_ok) {
+  __syncthreads();  // this block's writes precede thread 0's release
   if (threadIdx.x == 0) {
     const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    __threadfence();
-    const unsigned int old = atomicAdd(bar, add);
+    gb.expect ^= 1u;
+    red_release_add(gb.word, add);
     int ok = 1;
-    if (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) == 0u) {
+    if ((ld_acquire_gpu(gb.word) >> 31) != gb.expect) {
       const uint64_t t0 = global_timer_ns();
       for (uint32_t i = 1;; ++i) {
-        if (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) != 0u) break;
+        if ((ld_acquire_gpu(gb.word) >> 31) == gb.expect) break;
         if ((i & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
           ok = 0;
           break;
         }
       }
     }
-    __threadfence();
     *s_ok = ok;
   }
-  __syncthreads();
+  __syncthreads();  // the other blocks' writes are visible to this block
   return *s_ok != 0;
 }
 
 // Σ_b part[b] over the G blocks in a fixed order (lane l takes b ≡ l mod 32,
 // then a butterfly): the same value in every block.  Called by one warp.
+// All loads are issued before the first add (one L2 round trip for G ≤ 256).
 __device__ __forceinline__ float sum_over_blocks(const float* part, int G) {
   const int lane = threadIdx.x & 31;
   float t = 0.f;
-  for (int b = lane; b < G; b += 32) t += __ldcg(part + b);
+  for (int b0 = lane; b0 < G; b0 += 8 * 32) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int b = b0 + 32 * k;
+      v[k] = b < G ? __ldcg(part + b) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += v[k];
+  }
   return warp_sum(t);
+}
+
+// Σ_{b ≡ q (mod step), b < G} col[b·stride] in order of b, with up to 16
+// loads in flight before the first add.
+__device__ __forceinline__ float strided_sum(const float* col, size_t stride, int q, int step, int G) {
+  float t = 0.f;
+  for (int b0 = q; b0 < G; b0 += 16 * step) {
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int b = b0 + step * k;
+      v[k] = b < G ? __ldcg(col + (size_t)b * stride) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += v[k];
+  }
+  return t;
 }
 
 // One sweep over the block's rows: w_i = SA_i·v − θp_i, ρ² share, and
@@ -262,6 +301,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     return;
   }
 
+  GridBarrier gbar{P.bar, 0u};
+  if (tid == 0) gbar.expect = ld_acquire_gpu(P.bar) >> 31;  // before this block's first arrival
   const int r0 = blk * P.R;
   const int nr = max(0, min(P.m, r0 + P.R) - r0);
   const int c0 = blk * P.cs;
@@ -308,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     xss[j] = 0.f;
   }
   const float theta1 = sqrtf(block_sum(gsq, red));
-  bool alive = grid_barrier(P.bar, s_ok);  // every block has read the control block
+  bool alive = grid_barrier(gbar, s_ok);  // every block has read the control block
   // Every thread waits for its rows (also on the exits below, so that no copy
   // is still landing when the block exits).
   if (!mbar_wait(stage_bar, 0u, kWaitLimitNs)) alive = false;
@@ -361,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     float4 ur[CH];
     float rsq = grid_sweep<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, 0.f, w, P.sa_scale, P.scale_ld, r0, ur);
     block_reduce_store<CH>(ur, rsq, buf, dp, red, P.Upart + (size_t)blk * dp, P.rho2 + blk);
-    alive = grid_barrier(P.bar, s_ok);  // (A) ρ² and U partials
+    alive = grid_barrier(gbar, s_ok);  // (A) ρ² and U partials
     const float lam = P.lambda;
     float rho = 0.f, rhobar = 0.f, c = 0.f, s = 0.f, phi = 0.f, theta = 0.f;
     float t = __int_as_float(0x7f800000);  // +inf
@@ -371,18 +412,21 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
       // ---- after barrier A: U summed over blocks on the owned slice (nsub
       // subsets of blocks per column) and, in warp 0, ρ² — both loads issued
       // before either is waited for.
+      float rv[8];  // warp 0: the ρ² partials, loads issued before the slice's (G ≤ 256)
+      if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) rv[k] = lane + 32 * k < G ? __ldcg(P.rho2 + lane + 32 * k) : 0.f;
+      }
       if (P.cs < kThreads) {
         const int jj = tid % P.cs, q = tid / P.cs;
-        if (q < nsub && jj < ncol) {
-          float u = 0.f;
-#pragma unroll 4
-          for (int b = q; b < G; b += nsub) u += __ldcg(P.Upart + (size_t)b * dp + c0 + jj);
-          buf[q * P.cs + jj] = u;
-        }
+        if (q < nsub && jj < ncol) buf[q * P.cs + jj] = strided_sum(P.Upart + c0 + jj, (size_t)dp, q, nsub, G);
       }
       if (warp == 0) {
-        const float r2 = sum_over_blocks(P.rho2, G);
-        if (lane == 0) scal[2] = r2;
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += rv[k];
+        t = warp_sum(t);
+        if (lane == 0) scal[2] = t;
       }
       __syncthreads();
       rho = sqrtf(scal[2]);
@@ -427,8 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
         if (P.cs < kThreads) {
           for (int q = 0; q < nsub; ++q) u += buf[q * P.cs + jj];
         } else {
-#pragma unroll 4
-          for (int b = 0; b < G; ++b) u += __ldcg(P.Upart + (size_t)b * dp + c0 + jj);
+          u = strided_sum(P.Upart + c0 + jj, (size_t)dp, 0, 1, G);
         }
         const int j = c0 + jj;
         const float z = j < d ? u * inv_rho - rho * v[j] : 0.f;
@@ -437,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
       }
       zpart = block_sum(zpart, red);
       if (tid == 0) __stcg(P.theta2 + blk, zpart);
-      alive = grid_barrier(P.bar, s_ok);  // (B) slices of θv and θ² partials
+      alive = grid_barrier(gbar, s_ok);  // (B) slices of θv and θ² partials
       if (!alive) break;
       // ---- after barrier B: θ² (warp 0) and all of Z, loads issued together
       float4 zr[2];
@@ -465,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
       // ---- ρ p := SA v − θ p (unnormalised in w until ρ is known), ρ², SAᵀw
       rsq = grid_sweep<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, theta, w, P.sa_scale, P.scale_ld, r0, ur);
       block_reduce_store<CH>(ur, rsq, buf, dp, red, P.Upart + (size_t)blk * dp, P.rho2 + blk);
-      alive = grid_barrier(P.bar, s_ok);  // (A)
+      alive = grid_barrier(gbar, s_ok);  // (A)
     }
   }
   if (!alive) {
@@ -550,6 +593,7 @@ GridPlan plan_grid(int m, int dp, int sa_type) {
   }
   const int R = (m + want - 1) / want;
   const int G = (m + R - 1) / R;
+  if (G > 256) return gp;  // the kernel sums block partials with one load per lane and 8 per warp
   const int cs = (int)round_up((dp + G - 1) / G, 4);
   const int pitch = sa_type == MIHS_SA_FP32 ? dp : (int)round_up(dp, 16);
   const GridSmem L = grid_smem_layout(dp, (int)round_up(R, 4), cs, R, pitch, (int)elem_size(sa_type));

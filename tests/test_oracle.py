@@ -606,3 +606,48 @@ def test_gaussian_sketch_bf16_brute_force():
     assert np.allclose(got, ref, rtol=1e-14, atol=1e-14)
     assert _bf16_rne_bits(1 + 2.0 ** -8) == 1.0 and _bf16_rne_bits(1 + 3 * 2.0 ** -9) == 1 + 2.0 ** -7
     assert o.round_bf16(np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -9]))[1] == 1 + 2.0 ** -7
+
+
+# ----------------------------------------------- double-double gradient (C)
+def test_gradient_dd_against_exact_rationals():
+    """Every entry of Aᵀ(b − Ax) − λx in exact rational arithmetic from the
+    same fp32 / fp64 inputs: the double-double result agrees to ~2⁻¹⁰⁰ of
+    the terms' magnitude, on generic data and on a row residual that cancels
+    to far below fp64's resolution of b."""
+    from fractions import Fraction as F
+    rng = np.random.default_rng(5)
+    n, d = 9, 6
+    A = rng.standard_normal((n, d)).astype(np.float32)
+    b = rng.standard_normal(n).astype(np.float32)
+    x = rng.standard_normal(d)
+    lam = 0.37
+    # a row whose residual cancels: b_0 = fp32(A_0·x), x perturbed by 2⁻⁴⁰
+    b[0] = np.float32(A[0].astype(np.float64) @ x)
+    x[1] += 2.0 ** -40
+    gh, gl = o.gradient_dd(A, b, x, lam, nthreads=3)
+    Af = [[F(float(v)) for v in row] for row in A]
+    r = [F(float(b[i])) - sum(Af[i][j] * F(float(x[j])) for j in range(d)) for i in range(n)]
+    for j in range(d):
+        exact = sum(Af[i][j] * r[i] for i in range(n)) - F(lam) * F(float(x[j]))
+        scale = sum(abs(Af[i][j]) * (abs(F(float(b[i]))) + sum(abs(Af[i][k] * F(float(x[k]))) for k in range(d)))
+                    for i in range(n)) + abs(F(lam) * F(float(x[j])))
+        err = abs(F(float(gh[j])) + F(float(gl[j])) - exact)
+        assert err <= scale * F(2) ** -100, (j, float(err), float(scale))
+    # the thread split does not change the result beyond the last bits
+    gh1, gl1 = o.gradient_dd(A, b, x, lam, nthreads=1)
+    assert np.allclose(gh1 + gl1, gh + gl, rtol=0, atol=1e-28 * float(np.max(np.abs(gh))))
+
+
+def test_exact_solve_dd_refinement_on_ill_conditioned_problem():
+    """κ(H) ≈ 1e6: refining with the double-double residual drives the fp64
+    residual of x to rounding level and agrees with the extended-precision
+    refinement."""
+    sigma = W.profile_exponential(128, 8.0)
+    p = W.make_problem(2048, 128, sigma, 1e-6, 40.0, seed=31)
+    A, b = p.A.numpy(), p.b.numpy()
+    x = o.exact_solve(A, b, p.lam, refine=3, dd=True)
+    xe = o.exact_solve(A, b, p.lam, refine=3, extended=True)
+    assert o.rel_error(x, xe) <= 1e-12
+    gh, gl = o.gradient_dd(A, b, x, p.lam)
+    atb = np.abs(A.astype(np.float64)).T @ np.abs(b.astype(np.float64))
+    assert np.linalg.norm(gh + gl) <= 1e-13 * np.linalg.norm(atb)
