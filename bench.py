@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--families", default=",".join(FAMILIES))
     ap.add_argument("--tol", type=float, default=2e-8)
     ap.add_argument("--max-outer", type=int, default=200)
-    ap.add_argument("--n", type=int, default=262144)
-    ap.add_argument("--d", type=int, default=1024)
+    ap.add_argument("--n", "--rows", dest="n", type=int, default=262144)
+    ap.add_argument("--d", "--cols", dest="d", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -100,7 +100,8 @@ def max_over_ranks(v: float, ws: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
