@@ -14,14 +14,15 @@
 //   barrier B θ² = Σ_b θ²_b; v = Z/θ (every block reads all of Z)
 // Every sum over blocks runs in a fixed order, so all blocks compute the same
 // scalars and take the same branches.  The grid barrier is a counter in
-// global memory whose top bit flips once all blocks have arrived (it returns
-// to its starting value after every barrier); each wait is bounded and a wait
-// that runs out stops the solve with MIHS_ERR_TIMEOUT instead of hanging.
+// global memory whose top bit flips once all blocks have arrived
+// (grid_sync.cuh); each wait is bounded and a wait that runs out stops the
+// solve with MIHS_ERR_TIMEOUT instead of hanging.
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 
 #include "aab_kernel.cuh"
+#include "grid_sync.cuh"
 
 namespace mihs {
 
@@ -63,52 +64,6 @@ struct AabGridParams {
   float* Z;            // dp
   unsigned int* bar;   // grid barrier word (0 between launches)
 };
-
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier over gridDim.x blocks.  Block 0 adds 2³¹ − (G − 1), the
-// others 1: the word's top bit flips exactly when the last block arrives and
-// the low bits return to their value before the barrier.  Each block knows
-// the top bit to wait for from the word's top bit when the launch began
-// (read before its first arrival, so no flip can have happened yet) and the
-// number of barriers it has passed: the arrival is a release reduction with
-// no result to wait for, the wait an acquire load, and no separate fences.
-// Returns false (in every thread of the block) if the wait ran out.
-struct GridBarrier {
-  unsigned int* word;
-  unsigned int expect;  // top bit after the next barrier (thread 0)
-};
-
-__device__ __forceinline__ bool grid_barrier(GridBarrier& gb, int* s_ok) {
-  __syncthreads();  // this block's writes precede thread 0's release
-  if (threadIdx.x == 0) {
-    const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    gb.expect ^= 1u;
-    red_release_add(gb.word, add);
-    int ok = 1;
-    if ((ld_acquire_gpu(gb.word) >> 31) != gb.expect) {
-      const uint64_t t0 = global_timer_ns();
-      for (uint32_t i = 1;; ++i) {
-        if ((ld_acquire_gpu(gb.word) >> 31) == gb.expect) break;
-        if ((i & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
-          ok = 0;
-          break;
-        }
-      }
-    }
-    *s_ok = ok;
-  }
-  __syncthreads();  // the other blocks' writes are visible to this block
-  return *s_ok != 0;
-}
 
 // Σ_b part[b] over the G blocks in a fixed order (lane l takes b ≡ l mod 32,
 // then a butterfly): the same value in every block.  Called by one warp.
@@ -302,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
   }
 
   GridBarrier gbar{P.bar, 0u};
-  if (tid == 0) gbar.expect = ld_acquire_gpu(P.bar) >> 31;  // before this block's first arrival
+  if (tid == 0) grid_barrier_init(gbar, P.bar);  // before this block's first arrival
   const int r0 = blk * P.R;
   const int nr = max(0, min(P.m, r0 + P.R) - r0);
   const int c0 = blk * P.cs;

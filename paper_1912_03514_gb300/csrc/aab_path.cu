@@ -17,6 +17,7 @@
 
 #include <mutex>
 
+#include "grid_sync.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -29,6 +30,7 @@ constexpr int kPL = 16;             // λ per launch
 constexpr int kAThreads = 256;      // 8 warps
 constexpr int kAWarps = kAThreads / 32;
 constexpr size_t kAabPathSmemBudget = 220 * 1024;
+constexpr size_t kBarFloats = 64;   // 256 bytes of the scratch hold the grid barrier word
 
 __device__ int g_aab_path_error = 0;
 
@@ -55,6 +57,7 @@ struct AabPathParams {
   float* rho2part;     // blocks × kPL
   float* theta2part;   // blocks × kPL
   float* Z;            // kPL × dp
+  unsigned int* bar;   // grid barrier word (zero before the path solve)
 };
 
 struct AabPathSmem {
@@ -139,8 +142,16 @@ __device__ __forceinline__ void rows16_dots(const float* sa, int pitch, int row0
 __device__ __forceinline__ void sum_over_blocks16(const float* part, int nblk, float* red, float* out) {
   const int tid = threadIdx.x, l = tid & (kPL - 1), q = tid >> 4;
   float t = 0.f;
-#pragma unroll 4
-  for (int b = q; b < nblk; b += 16) t += __ldcg(part + (size_t)b * kPL + l);
+  for (int b0 = q; b0 < nblk; b0 += 16 * 16) {  // every load of a batch before the first add
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int b = b0 + 16 * k;
+      v[k] = b < nblk ? __ldcg(part + (size_t)b * kPL + l) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t += v[k];
+  }
   red[q * kPL + l] = t;
   __syncthreads();
   if (tid < kPL) {
@@ -229,6 +240,10 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
   }
   extern __shared__ __align__(16) float sm[];
   const int blk = blockIdx.x, nblk = gridDim.x, tid = threadIdx.x;
+  __shared__ int s_ok;
+  GridBarrier gbar{P.bar, 0u};
+  if (tid == 0) grid_barrier_init(gbar, P.bar);  // before this block's first arrival
+  bool alive = true;
   const int d = P.d, dp = P.dp, R = P.rows_per_block, pitch = P.pitch, cs = P.cols_per_block;
   const AabPathSmem L = aab_path_layout(R, pitch, dp, cs);
   float* sa = sm + L.sa;
@@ -324,7 +339,8 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
     }
     __syncthreads();
     path_sweep(P, sa, nr, v, p, s_theta, w, rpart, red);
-    grid.sync();  // (A) ρ² and U partials of the first sweep
+    alive = grid_barrier(gbar, &s_ok);  // (A) ρ² and U partials of the first sweep
+    if (alive) {
     sum_over_blocks16(P.rho2part, nblk, red, s_sum);
     if (tid < kPL) {
       const int l = tid;
@@ -376,17 +392,28 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
           const int item = idx % nitems, grp = idx / nitems;
           const int l = item / nq, j = c0 + 4 * (item - l * nq);
           float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-          // written by other blocks in this launch: read through L2, not L1
-#pragma unroll 4
-          for (int b = grp; b < nblk; b += ngrp)
-            for (int q = 0; q < rsub; ++q) {
-              const float4 u4 = __ldcg(reinterpret_cast<const float4*>(
-                  P.Upart + ((size_t)b * kPL + l) * upp + (size_t)q * dp + j));
-              t.x += u4.x;
-              t.y += u4.y;
-              t.z += u4.z;
-              t.w += u4.w;
+          // written by other blocks in this launch: read through L2, not L1;
+          // the (block, row subset) pairs in order, eight loads issued per batch
+          const int nb = nblk > grp ? (nblk - grp + ngrp - 1) / ngrp : 0;
+          const int ne = nb * rsub;
+          for (int e0 = 0; e0 < ne; e0 += 8) {
+            float4 u4[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int e = e0 + k;
+              const int b = grp + (e / rsub) * ngrp, q = e % rsub;
+              u4[k] = e < ne ? __ldcg(reinterpret_cast<const float4*>(P.Upart + ((size_t)b * kPL + l) * upp +
+                                                                      (size_t)q * dp + j))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              t.x += u4[k].x;
+              t.y += u4[k].y;
+              t.z += u4[k].z;
+              t.w += u4[k].w;
+            }
+          }
           float* zs = zsum + (size_t)grp * npairs + l * ncol + (j - c0);
           zs[0] = t.x;
           zs[1] = t.y;
@@ -410,7 +437,8 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
           P.theta2part[(size_t)blk * kPL + tid] = t;
         }
       }
-      grid.sync();  // (B) Z slices and θ² partials visible
+      alive = grid_barrier(gbar, &s_ok);  // (B) Z slices and θ² partials visible
+      if (!alive) break;
       sum_over_blocks16(P.theta2part, nblk, red, s_sum);
       if (tid < kPL) {
         const int l = tid;
@@ -440,7 +468,8 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
       __syncthreads();
       // (A) ρp = SAv − θp, its ρ² and SAᵀ(ρp) in one sweep
       path_sweep(P, sa, nr, v, p, s_theta, w, rpart, red);
-      grid.sync();
+      alive = grid_barrier(gbar, &s_ok);  // (A)
+      if (!alive) break;
       sum_over_blocks16(P.rho2part, nblk, red, s_sum);
       if (tid < kPL) {
         const int l = tid;
@@ -478,8 +507,23 @@ __global__ void __launch_bounds__(kAThreads, 1) aab_path_kernel(const AabPathPar
       if (tid < kPL) s_theta[tid] = 0.f;  // unused until rebuilt
       __syncthreads();
     }
+    }  // alive after the first sweep
   }
-  grid.sync();  // every block has read the control blocks before block 0 writes them
+  // every block has read the control blocks before block 0 writes them
+  if (alive) alive = grid_barrier(gbar, &s_ok);
+  if (!alive) {
+    // A grid barrier ran out: stop every λ of the path with an error.
+    if (tid == 0) {
+      atomicExch(&g_aab_path_error, MIHS_ERR_TIMEOUT);
+      for (int l = 0; l < P.ps.nl; ++l) {
+        P.ctl[l].status = MIHS_ERR_TIMEOUT;
+        P.ctl[l].done = 1;
+      }
+      *P.path_all_done = 1;
+      if (P.cond != 0ull) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
+    }
+    return;
+  }
   // Heavy ball on the owned slice for every λ that took this step.
   for (int i = tid; i < kPL * cs; i += kAThreads) {
     const int l = i / cs, j = c0 + (i - l * cs);
@@ -530,7 +574,7 @@ int aab_path_device_error(int* code) {
 
 size_t aab_path_ws_floats(int dp) {
   const size_t G = (size_t)num_sms();
-  return G * kPL * 1024 + 2 * G * kPL + (size_t)kPL * dp;
+  return kBarFloats + G * kPL * 1024 + 2 * G * kPL + (size_t)kPL * dp;
 }
 
 int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s) {
@@ -577,6 +621,8 @@ int launch_aab_path(const AabLaunch& a, float* ws, cudaStream_t s) {
   P.path_all_done = a.path_all_done;
   P.cond = a.cond;
   const size_t Gmax = (size_t)nsm;
+  P.bar = reinterpret_cast<unsigned int*>(ws);  // first kBarFloats floats: the barrier word
+  ws += kBarFloats;
   P.Upart = ws;
   P.rho2part = ws + Gmax * kPL * 1024;
   P.theta2part = P.rho2part + Gmax * kPL;

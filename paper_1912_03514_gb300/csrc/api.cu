@@ -375,6 +375,18 @@ int build_graph(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
   return rc;
 }
 
+// Whether a path solve on this handle takes the all-λ grid form of
+// AAb_Solver (opt-in, MIHS_PATH_AAB=grid).  Measured on the batched workload
+// (64 matrices × 16 λ, SA up to 16 MB) the one-cluster-per-λ form is twice as
+// fast even where SA does not fit a cluster's shared memory: each λ stops on
+// its own, clusters of different problems run concurrently on four streams,
+// while the grid form keeps every λ until the slowest stops and must not run
+// beside another grid.
+bool path_uses_grid(const mihs_sketch_s* sk) {
+  const char* e = std::getenv("MIHS_PATH_AAB");
+  return e != nullptr && std::strcmp(e, "grid") == 0 && sk->sa_prec == MIHS_SA_FP32 && sk->d <= 1024;
+}
+
 // One outer step of Algorithm 1 for every λ of a path: the shared gradient
 // pass, its reduce, and one AAb_Solver cluster per λ (+ heavy ball).
 int launch_path_step(mihs_sketch_s* sk, const mihs_sketch_s::PathKey& k, const AabLaunch& a, cudaStream_t s) {
@@ -383,13 +395,9 @@ int launch_path_step(mihs_sketch_s* sk, const mihs_sketch_s::PathKey& k, const A
   if (!rc) rc = launch_apass_path_finalize(sk->path_partials, sk->P_path, sk->d, k.X, k.ldx, k.ps, sk->path_g,
                                            sk->dp, all_done, s);
   if (rc) return rc;
-  // One thread-block cluster per λ (default), or all λ in one cooperative
-  // grid with SA spread over the SMs' shared memory (MIHS_PATH_AAB=grid).
-  // Both are latency-bound per pass; measured on GB300 the cluster form was
-  // faster (the grid form pays two grid-wide barriers per pass and keeps
-  // computing every λ until the slowest inner solve ends).
-  const char* env = std::getenv("MIHS_PATH_AAB");
-  if (env != nullptr && std::strcmp(env, "grid") == 0) {
+  // One thread-block cluster per λ, or (opt-in) all λ in one cooperative
+  // grid with SA spread over the SMs' shared memory.
+  if (path_uses_grid(sk)) {
     rc = launch_aab_path(a, sk->path_aab_ws, s);
     if (rc != MIHS_ERR_UNSUPPORTED) return rc;
   }
@@ -1075,6 +1083,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
       ps.alpha[l] = (float)((1.0 - beta) * (1.0 - beta));
     }
     float* Xg = X + (size_t)l0 * ldx;
+    MIHS_CUDA_TRY(cudaMemsetAsync(sk->path_aab_ws, 0, 256, s));  // the grid form's barrier word
     path_init_kernel<<<1, 32, 0, s>>>(sk->path_ctl, sk->path_cnt, nl, opts->max_outer, (float)opts->tol);
     MIHS_CHECK_LAUNCH();
     count_launch();
@@ -1217,12 +1226,12 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
       MIHS_ARG(probs[i].sk != probs[j].sk, "mihs_solve_batched: problems %d and %d share a handle", j, i);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Independent problems run on internal streams forked from and joined back
-  // into the caller's stream: four of them, or one when the path steps use
-  // the cooperative grid form (two such grids must never wait for each
-  // other's blocks, so they are not run concurrently).
+  // into the caller's stream.  Problems whose path steps use the cooperative
+  // grid form all go to stream 0 (two such grids must never wait for each
+  // other's blocks, so they never run concurrently); the others are spread
+  // over streams 1 … 3 (or all four when no problem uses the grid form).
   constexpr int kStreams = 4;
-  const char* env = std::getenv("MIHS_PATH_AAB");
-  const int nstreams = (env != nullptr && std::strcmp(env, "grid") == 0) ? 1 : kStreams;
+  const int nstreams = kStreams;
   static std::mutex mu;
   static std::vector<std::vector<cudaStream_t>> pool;  // per device
   static std::vector<std::vector<cudaEvent_t>> evs;
@@ -1255,10 +1264,23 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
   MIHS_CUDA_TRY(cudaEventRecord(ev[kStreams], s));
   for (int k = 0; k < nstreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kStreams], 0));
   int rc = MIHS_OK;
+  bool any_grid = false;
+  for (int i = 0; i < nprob; ++i) any_grid = any_grid || path_uses_grid(probs[i].sk);
+  int next = 0;
   for (int i = 0; i < nprob && rc == MIHS_OK; ++i) {
     const mihs_problem& q = probs[i];
+    int k;
+    if (path_uses_grid(q.sk)) {
+      k = 0;
+    } else if (any_grid) {
+      k = 1 + next % (nstreams - 1);
+      ++next;
+    } else {
+      k = next % nstreams;
+      ++next;
+    }
     rc = path_enqueue(q.sk, q.A, q.lda, q.b, nlambda, lambdas, sds != nullptr ? sds + (size_t)i * nlambda : nullptr,
-                      opts, q.X, q.ldx, infos != nullptr, st[i % nstreams]);
+                      opts, q.X, q.ldx, infos != nullptr, st[k]);
     if (rc) set_error("mihs_solve_batched: problem %d: %s", i, mihs_last_error());
   }
   for (int k = 0; k < nstreams; ++k) {
