@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-backward", action="store_true", help="skip the differentiable-solve leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched λ-path leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (2^21 x 2048)")
+    ap.add_argument("--no-dual", action="store_true", help="skip the Dual M-IHS leg (2048 x 2^18)")
     ap.add_argument("--mixed-tol", type=float, default=3e-14,
                     help="relative residual the mixed-precision solves refine to")
     ap.add_argument("--mixed-sample-rows", type=int, default=1 << 17,
@@ -426,6 +427,10 @@ def main():
     if not args.no_mixed:
         mixed = run_mixed(args, dev, ws)
 
+    dual = None
+    if not args.no_dual:
+        dual = run_dual(args, dev, ws, peaks, peak_src)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         if A_host is None:
@@ -458,6 +463,7 @@ def main():
             "differentiable": differentiable,
             "batched": batched,
             "mixed": mixed,
+            "dual": dual,
             "not_converged": not_converged or None,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -595,6 +601,75 @@ def run_batched(args, dev, ws, peaks, peak_src):
                                    "peak_source": "derived: 152 SMs × 128 FP32 FMA/clk × 2 flops × 2.07 GHz"}}
     for sk in handles:
         sk.close()
+    return out
+
+
+def run_dual(args, dev, ws, peaks, peak_src):
+    """Dual M-IHS (Algorithm 2) on a wide problem: n = 2048 rows, d = 2¹⁸
+    columns (A = 2.1 GB), σ_i = 1/i, λ = 1e-4 (sd ≈ 147), b = A x0 + ω at
+    40 dB; CountSketch and Gaussian sketches of Aᵀ with m = 4·sd; stop at
+    relative dual residual 1e-6.  One step = sketch + solve + x = Aᵀν.  The
+    roofline is the dual gradient g = b − A(Aᵀν) − λν alone: two passes over A
+    (8nd bytes)."""
+    import numpy as np
+    import torch
+
+    from paper_1912_03514_gb300 import mihs
+    from paper_1912_03514_gb300 import workloads as W
+    n, d, lam = 2048, 1 << 18, 1e-4
+    sigma = 1.0 / np.arange(1, n + 1, dtype=np.float64)
+    q = W.make_problem(d, n, sigma, lam, 40.0, seed=1004, device=str(dev), device_rng=True)
+    A = q.A.t().contiguous()           # n × d with singular values σ
+    del q
+    g = torch.Generator(device=dev).manual_seed(1005)
+    x0 = torch.randn(d, generator=g, device=dev)
+    Ax0 = A @ x0
+    om = torch.randn(n, generator=g, device=dev)
+    b = (Ax0 + om * (Ax0.norm() / om.norm()) / 100.0).contiguous()
+    sd = W.nominal_sd(sigma, lam)
+    m = int(math.ceil(4 * sd / 4)) * 4
+    out = {"workload": f"dual-{n}x{d}-poly1-lam1e-4, SNR 40 dB, m = {m} (4·sd, sd = {sd:.2f}), tol 1e-6; "
+                       f"A = {4 * n * d / 1e9:.2f} GB", "unit": "solves/s", "by_family": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    for fam in ("countsketch", "gaussian"):
+        dk = mihs.DualSketch(A, fam, m, seed=7)
+        x = torch.empty(d, device=dev)
+        nu = torch.empty(n, device=dev)
+
+        def step(want_info=False):
+            dk.resketch(A, 7)
+            return dk.solve(A, b, lam, sd, tol=1e-6, max_outer=200, x=x, nu=nu, want_info=want_info)[2]
+        info = step(want_info=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / 3, ws)
+        out["by_family"][fam] = {"value": round(ws / (ms / 1e3), 3), "ms_per_step": round(ms, 3),
+                                 "status": info.status, "outer_iters": info.outer_iters,
+                                 "inner_iters": info.inner_iters_total, "rel_resid": float(f"{info.rel_resid:.3e}")}
+        dk.close()
+    # the dual gradient's two passes over A, timed alone
+    nu = torch.randn(n, device=dev)
+    gd = torch.empty(n, device=dev)
+    for _ in range(3):
+        mihs.gradient_dual(A, b, nu, lam, g=gd)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        mihs.gradient_dual(A, b, nu, lam, g=gd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 10 / 1e3
+    by = 8.0 * n * d + 4.0 * (3 * n + d)
+    out["gradient_roofline"] = {"bound": "hbm", "kernels": "atnu_kernel + dual_resid_kernel",
+                                "bytes_per_call": by, "avg_call_us": round(t * 1e6, 2),
+                                "achieved": round(by / t / 1e9, 1), "peak": peaks.get("hbm_gbs"),
+                                "unit": "GB/s", "frac": round(by / t / 1e9 / peaks.get("hbm_gbs"), 4)
+                                if peaks.get("hbm_gbs") else None, "peak_source": peak_src}
     return out
 
 

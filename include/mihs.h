@@ -455,11 +455,13 @@ int mihs_dual_resketch(mihs_dual_t dk, const float* A, int64_t lda,
 int mihs_dual_copy(mihs_dual_t dk, float* dst, int64_t ldd, void* stream);
 int mihs_dual_destroy(mihs_dual_t dk);
 
-/* The dual gradient step on its own: g = b − A(Aᵀν) − λν (n-vectors). */
+/* The dual gradient step on its own: g = b − A(Aᵀν) − λν (n-vectors).
+ * Allocates stream-ordered scratch for Aᵀν and its row-split partials. */
 int mihs_gradient_dual(const float* A, int64_t n, int64_t d, int64_t lda,
                        const float* b, const float* nu, double lambda,
                        float* g, void* stream);
-/* x = Aᵀν (d-vector, 16-byte aligned). */
+/* x = Aᵀν (d-vector, 16-byte aligned).  Allocates stream-ordered scratch
+ * for the row-split partials (summed in a fixed order). */
 int mihs_dual_recover(const float* A, int64_t n, int64_t d, int64_t lda,
                       const float* nu, float* x, void* stream);
 

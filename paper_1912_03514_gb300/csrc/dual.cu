@@ -2,7 +2,8 @@
 // dual problem ν* = argmin ½‖Aᵀν‖² + (λ/2)‖ν‖² − ⟨b, ν⟩ (Eq. intro_dual), with
 // the sketch taken along the d coordinates (S·Aᵀ, m × n) and the primal
 // solution recovered as x = Aᵀν (Eq. dual_relation).  Per step:
-//   u = Aᵀν            one pass over A, each block owning a column slice
+//   u = Aᵀν            one pass over A: blocks own a column slice × row split,
+//                      the splits' partials summed in order
 //   g = b − A·u − λν   one pass over A, one block per row
 //   Δν = AAb_Solver(SAᵀ, g, λ, ε_sub), ν⁺ = ν + αΔν + β(ν − ν⁻)   (aab.cu)
 // all inside a CUDA graph WHILE loop that the AAb kernel ends.
@@ -43,56 +44,112 @@ __global__ void transpose_kernel(const float* __restrict__ A, int n, int d, long
   }
 }
 
-// u[j] = Σ_i ν_i A[i][j]: thread owns 4 consecutive columns, rows in order.
-__global__ void __launch_bounds__(kT) atnu_kernel(const float* __restrict__ A, int n, int d, long long lda,
-                                                  const float* __restrict__ nu, float* __restrict__ u,
-                                                  const SolveCtl* __restrict__ ctl) {
+// Partial u over a row split: part[z][j] = Σ_{i in split z} ν_i A[i][j].  A
+// thread owns 4 consecutive columns (one float4 per row, coalesced across the
+// warp) and walks its split's rows in order, eight rows of loads in flight.
+constexpr int kAtnuRows = 256;  // rows per split
+
+__global__ void __launch_bounds__(kT) atnu_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
+                                                          const float* __restrict__ nu, float* __restrict__ part,
+                                                          long long ldp, const SolveCtl* __restrict__ ctl) {
   if (ctl != nullptr && ctl->done) return;
-  extern __shared__ float nus[];
-  for (int i = threadIdx.x; i < n; i += kT) nus[i] = nu[i];
+  __shared__ float nus[kAtnuRows];
+  const int i0 = blockIdx.y * kAtnuRows, i1 = min(n, i0 + kAtnuRows);
+  for (int i = i0 + threadIdx.x; i < i1; i += kT) nus[i - i0] = nu[i];
   __syncthreads();
   const long long c = ((long long)blockIdx.x * kT + threadIdx.x) * 4;
   if (c >= d) return;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float* out = part + (long long)blockIdx.y * ldp + c;
   if (c + 4 <= d) {
-#pragma unroll 4
-    for (int i = 0; i < n; ++i) {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(A + (long long)i * lda + c));
-      const float s = nus[i];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* col = A + c;
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+      float4 a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = __ldg(reinterpret_cast<const float4*>(col + (long long)(i + k) * lda));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float s = nus[i + k - i0];
+        acc.x = fmaf(s, a[k].x, acc.x);
+        acc.y = fmaf(s, a[k].y, acc.y);
+        acc.z = fmaf(s, a[k].z, acc.z);
+        acc.w = fmaf(s, a[k].w, acc.w);
+      }
+    }
+    for (; i < i1; ++i) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(col + (long long)i * lda));
+      const float s = nus[i - i0];
       acc.x = fmaf(s, a.x, acc.x);
       acc.y = fmaf(s, a.y, acc.y);
       acc.z = fmaf(s, a.z, acc.z);
       acc.w = fmaf(s, a.w, acc.w);
     }
-    *reinterpret_cast<float4*>(u + c) = acc;
+    *reinterpret_cast<float4*>(out) = acc;
   } else {
     float t[3] = {0.f, 0.f, 0.f};
-    for (int i = 0; i < n; ++i)
-      for (int k = 0; k < 3 && c + k < d; ++k) t[k] = fmaf(nus[i], A[(long long)i * lda + c + k], t[k]);
-    for (int k = 0; k < 3 && c + k < d; ++k) u[c + k] = t[k];
+    for (int i = i0; i < i1; ++i)
+      for (int k = 0; k < 3 && c + k < d; ++k) t[k] = fmaf(nus[i - i0], A[(long long)i * lda + c + k], t[k]);
+    for (int k = 0; k < 3 && c + k < d; ++k) out[k] = t[k];
   }
 }
 
-// g_i = b_i − A_i·u − λν_i: one block per row, fixed-order block sum.
+// u[j] = Σ_z part[z][j] in split order.
+__global__ void atnu_reduce_kernel(const float* __restrict__ part, int nsplit, long long ldp, int d,
+                                   float* __restrict__ u, const SolveCtl* __restrict__ ctl) {
+  if (ctl != nullptr && ctl->done) return;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  float t = 0.f;
+  for (int z = 0; z < nsplit; ++z) t += part[(long long)z * ldp + j];
+  u[j] = t;
+}
+
+// g_i = b_i − A_i·u − λν_i for kRowsPerBlock rows per block (each load of u
+// serves them all), fixed-order block sums.
+constexpr int kResidRows = 4;
+
 __global__ void __launch_bounds__(kT) dual_resid_kernel(const float* __restrict__ A, int n, int d, long long lda,
                                                         const float* __restrict__ u, const float* __restrict__ b,
                                                         const float* __restrict__ nu, float lam,
                                                         float* __restrict__ g, const SolveCtl* __restrict__ ctl) {
   if (ctl != nullptr && ctl->done) return;
-  __shared__ float red[kT / 32];
-  const int i = blockIdx.x;
-  const float* row = A + (long long)i * lda;
+  __shared__ float red[kResidRows][kT / 32];
+  const int i0 = blockIdx.x * kResidRows;
   const int d4 = d >> 2;
-  float s0 = 0.f, s1 = 0.f;
+  float s0[kResidRows], s1[kResidRows];
+#pragma unroll
+  for (int r = 0; r < kResidRows; ++r) s0[r] = s1[r] = 0.f;
+  const float* rows[kResidRows];
+#pragma unroll
+  for (int r = 0; r < kResidRows; ++r) rows[r] = A + (long long)min(i0 + r, n - 1) * lda;
   for (int k = threadIdx.x; k < d4; k += kT) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(row) + k);
     const float4 v = __ldcg(reinterpret_cast<const float4*>(u) + k);
-    s0 = fmaf(a.x, v.x, fmaf(a.z, v.z, s0));
-    s1 = fmaf(a.y, v.y, fmaf(a.w, v.w, s1));
+#pragma unroll
+    for (int r = 0; r < kResidRows; ++r) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(rows[r]) + k);
+      s0[r] = fmaf(a.x, v.x, fmaf(a.z, v.z, s0[r]));
+      s1[r] = fmaf(a.y, v.y, fmaf(a.w, v.w, s1[r]));
+    }
   }
-  for (int j = 4 * d4 + threadIdx.x; j < d; j += kT) s0 = fmaf(row[j], u[j], s0);
-  const float t = block_sum256(s0 + s1, red);
-  if (threadIdx.x == 0) g[i] = b[i] - t - (nu != nullptr ? lam * nu[i] : 0.f);
+  for (int j = 4 * d4 + threadIdx.x; j < d; j += kT) {
+#pragma unroll
+    for (int r = 0; r < kResidRows; ++r) s0[r] = fmaf(rows[r][j], u[j], s0[r]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < kResidRows; ++r) {
+    const float t = warp_sum(s0[r] + s1[r]);
+    if (lane == 0) red[r][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kResidRows) {
+    const int r = threadIdx.x, i = i0 + r;
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) t += red[r][w];
+    if (i < n) g[i] = b[i] - t - (nu != nullptr ? lam * nu[i] : 0.f);
+  }
 }
 
 __global__ void dual_ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol) {
@@ -116,18 +173,26 @@ __global__ void dual_gnorm0_kernel(SolveCtl* ctl, const float* b, int n) {
   }
 }
 
-int launch_atnu(const float* A, int64_t n, int64_t d, int64_t lda, const float* nu, float* u, const SolveCtl* ctl,
-                cudaStream_t s) {
-  const unsigned blocks = (unsigned)((d + 4 * kT - 1) / (4 * kT));
-  atnu_kernel<<<blocks, kT, sizeof(float) * (size_t)n, s>>>(A, (int)n, (int)d, lda, nu, u, ctl);
+int atnu_num_splits(int64_t n) { return (int)((n + kAtnuRows - 1) / kAtnuRows); }
+
+// u = Aᵀν through row-split partials `part` (atnu_num_splits(n) × round_up(d, 4) floats).
+int launch_atnu(const float* A, int64_t n, int64_t d, int64_t lda, const float* nu, float* u, float* part,
+                const SolveCtl* ctl, cudaStream_t s) {
+  const int ns = atnu_num_splits(n);
+  const long long ldp = round_up(d, 4);
+  const unsigned cblocks = (unsigned)((d + 4 * kT - 1) / (4 * kT));
+  atnu_partial_kernel<<<dim3(cblocks, (unsigned)ns), kT, 0, s>>>(A, (int)n, (int)d, lda, nu, part, ldp, ctl);
   MIHS_CHECK_LAUNCH();
-  count_launch();
+  atnu_reduce_kernel<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(part, ns, ldp, (int)d, u, ctl);
+  MIHS_CHECK_LAUNCH();
+  count_launch(2);
   return MIHS_OK;
 }
 
 int launch_dual_resid(const float* A, int64_t n, int64_t d, int64_t lda, const float* u, const float* b,
                       const float* nu, float lam, float* g, const SolveCtl* ctl, cudaStream_t s) {
-  dual_resid_kernel<<<(unsigned)n, kT, 0, s>>>(A, (int)n, (int)d, lda, u, b, nu, lam, g, ctl);
+  dual_resid_kernel<<<(unsigned)((n + kResidRows - 1) / kResidRows), kT, 0, s>>>(A, (int)n, (int)d, lda, u, b, nu,
+                                                                                 lam, g, ctl);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;
@@ -152,8 +217,10 @@ struct mihs_dual_s {
   uint64_t seed;
   float* SAt = nullptr;   // m × np
   float* u = nullptr;     // d
+  float* upart = nullptr; // atnu_num_splits(n) × round_up(d, 4): row-split partials of Aᵀν
   float* g = nullptr;     // np
   float* nu_prev = nullptr;  // np
+  void* grid_ws = nullptr;   // scratch of the grid form of AAb_Solver (first solve that needs it)
   SolveCtl* ctl = nullptr;
   SolveCtl* ctl_host = nullptr;
   cudaStream_t cap = nullptr;
@@ -190,7 +257,7 @@ int dual_sketch_into(mihs_dual_t dk, const float* A, int64_t lda, uint64_t seed,
 
 // One step of Algorithm 2 (both gradient passes and the AAb + heavy ball).
 int dual_step(mihs_dual_t dk, const mihs_dual_s::Key& k, const AabLaunch& a, cudaStream_t s) {
-  int rc = launch_atnu(k.A, dk->n, dk->d, k.lda, k.nu, dk->u, dk->ctl, s);
+  int rc = launch_atnu(k.A, dk->n, dk->d, k.lda, k.nu, dk->u, dk->upart, dk->ctl, s);
   if (!rc) rc = launch_dual_resid(k.A, dk->n, dk->d, k.lda, dk->u, k.b, k.nu, (float)k.lam, dk->g, dk->ctl, s);
   if (!rc) rc = launch_aab(a, s);
   return rc;
@@ -255,7 +322,8 @@ int mihs_dual_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int fami
   dk->np = round_up(n, 4);
   dk->family = family;
   char* p = nullptr;
-  const size_t fl = (size_t)m * dk->np + (size_t)round_up(d, 4) + 2 * (size_t)dk->np;
+  const size_t fl = (size_t)m * dk->np + (size_t)round_up(d, 4) + 2 * (size_t)dk->np +
+                    (size_t)atnu_num_splits(n) * (size_t)round_up(d, 4);
   cudaError_t e = cudaMalloc(&p, fl * sizeof(float) + sizeof(SolveCtl));
   if (e == cudaSuccess) e = cudaMallocHost(&dk->ctl_host, sizeof(SolveCtl));
   if (e != cudaSuccess) {
@@ -268,7 +336,8 @@ int mihs_dual_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int fami
   dk->u = dk->SAt + (size_t)m * dk->np;
   dk->g = dk->u + round_up(d, 4);
   dk->nu_prev = dk->g + dk->np;
-  dk->ctl = reinterpret_cast<SolveCtl*>(dk->nu_prev + dk->np);
+  dk->upart = dk->nu_prev + dk->np;
+  dk->ctl = reinterpret_cast<SolveCtl*>(dk->upart + (size_t)atnu_num_splits(n) * (size_t)round_up(d, 4));
   rc = dual_sketch_into(dk, A, lda, seed, static_cast<cudaStream_t>(stream));
   if (rc) {
     cudaFree(dk->SAt);
@@ -302,6 +371,7 @@ int mihs_dual_destroy(mihs_dual_t dk) {
   cudaDeviceSynchronize();
   drop_dual_graph(dk);
   if (dk->cap) cudaStreamDestroy(dk->cap);
+  if (dk->grid_ws) cudaFree(dk->grid_ws);
   cudaFree(dk->SAt);
   cudaFreeHost(dk->ctl_host);
   delete dk;
@@ -317,10 +387,10 @@ int mihs_gradient_dual(const float* A, int64_t n, int64_t d, int64_t lda, const 
   MIHS_ARG(lambda >= 0.0 && std::isfinite(lambda), "mihs_gradient_dual: lambda must be finite, >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScratch us;
-  rc = us.alloc(sizeof(float) * (size_t)round_up(d, 4), s);
+  rc = us.alloc(sizeof(float) * (size_t)round_up(d, 4) * (size_t)(1 + atnu_num_splits(n)), s);
   if (rc) return rc;
   float* u = static_cast<float*>(us.p);
-  rc = launch_atnu(A, n, d, lda, nu, u, nullptr, s);
+  rc = launch_atnu(A, n, d, lda, nu, u, u + round_up(d, 4), nullptr, s);
   if (rc) return rc;
   return launch_dual_resid(A, n, d, lda, u, b, nu, (float)lambda, g, nullptr, s);
 }
@@ -331,7 +401,11 @@ int mihs_dual_recover(const float* A, int64_t n, int64_t d, int64_t lda, const f
   if (rc) return rc;
   MIHS_ARG(nu != nullptr && x != nullptr, "mihs_dual_recover: null vector");
   MIHS_ARG((reinterpret_cast<uintptr_t>(x) & 15u) == 0, "mihs_dual_recover: x must be 16-byte aligned");
-  return launch_atnu(A, n, d, lda, nu, x, nullptr, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch ps;
+  const int prc = ps.alloc(sizeof(float) * (size_t)round_up(d, 4) * (size_t)atnu_num_splits(n), s);
+  if (prc) return prc;
+  return launch_atnu(A, n, d, lda, nu, x, static_cast<float*>(ps.p), nullptr, s);
 }
 
 int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda, const float* b, double lambda,
@@ -384,6 +458,19 @@ int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda, const float* b,
   a.x = nu;
   a.x_prev = dk->nu_prev;
   a.ctl = dk->ctl;
+  if (aab_grid_wanted(a.m, a.d, MIHS_SA_FP32)) {  // SAᵀ too large for one cluster: the grid form
+    if (dk->grid_ws == nullptr) {
+      const size_t bytes = aab_grid_ws_bytes(a.d);
+      const cudaError_t e = cudaMalloc(&dk->grid_ws, bytes);
+      if (e != cudaSuccess) {
+        dk->grid_ws = nullptr;
+        set_error("mihs_solve_dual: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+      }
+    }
+    MIHS_CUDA_TRY(cudaMemsetAsync(dk->grid_ws, 0, kAabGridBarBytes, s));
+    a.grid_ws = dk->grid_ws;
+  }
   const mihs_dual_s::Key key = {A, lda, b, nu, lambda, alpha, beta, a.eps, a.max_passes};
   bool graph_ran = false;
   if (!timing_on() && !dk->graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
@@ -412,7 +499,7 @@ int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda, const float* b,
     }
   }
   if (x != nullptr) {  // x = Aᵀν (Eq. dual_relation)
-    rc = launch_atnu(A, n, dk->d, lda, nu, x, nullptr, s);
+    rc = launch_atnu(A, n, dk->d, lda, nu, x, dk->upart, nullptr, s);
     if (rc) return rc;
   }
   if (info == nullptr) return MIHS_OK;
@@ -423,7 +510,7 @@ int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda, const float* b,
   info->inner_iters_total = c.inner_total;
   info->rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
   info->status = c.done ? c.status : MIHS_NOT_CONVERGED;
-  if (graph_ran) count_launch(3ull * (uint64_t)(c.outer + 1));
+  if (graph_ran) count_launch(4ull * (uint64_t)(c.outer + 1));
   return info->status;
 }
 
