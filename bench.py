@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
-                                            "aab-wide-bf16",
+                                            "aab-wide-bf16", "dual-grad",
                                             "gaussian", "gaussian-bf16", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
@@ -787,7 +787,16 @@ def run_profile_op(args, local):
     x = W.randn((p.d,), seed=5, scale=0.01).to(dev)
     g = torch.empty(p.d, device=dev)
     op = args.profile_op
-    if op in ("aab-wide", "aab-wide-bf16"):
+    if op == "dual-grad":
+        # the Dual M-IHS gradient g = b − A(Aᵀν) − λν on a wide 2048 × (n·d/2048)
+        # matrix (as many elements as the n × d workload)
+        nd, dd = 2048, max(1024, args.n * args.d // 2048)
+        Aw = W.randn((nd, dd), 11, scale=1.0 / math.sqrt(dd)).to(dev)
+        bw = W.randn((nd,), 12).to(dev)
+        nu = W.randn((nd,), 13).to(dev)
+        gd = torch.empty(nd, device=dev)
+        fn = lambda: mihs.gradient_dual(Aw, bw, nu, 1e-4, g=gd)
+    elif op in ("aab-wide", "aab-wide-bf16"):
         # AAb_Solver on an SA of the mixed-precision workload's shape (m = 3076,
         # d = 2048, 25 MB in fp32, 12.6 MB in bf16: too large for one cluster,
         # so the grid form runs), a fixed 200 passes (per-pass latency =
