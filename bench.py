@@ -599,6 +599,45 @@ def run_batched(args, dev, ws, peaks, peak_src):
                                    "peak": round(nom_fp32, 1), "unit": "TFLOP/s",
                                    "frac": round(flops / (pa_ms / 1e3) / 1e12 / nom_fp32, 4),
                                    "peak_source": "derived: 152 SMs × 128 FP32 FMA/clk × 2 flops × 2.07 GHz"}}
+    # the plain single-λ form on the same problems: one mihs_solve per
+    # (matrix, λ) on the matrix's handle (same sketch, same tolerance), over
+    # the first 8 matrices
+    nsub = min(8, len(probs))
+    x1 = [torch.empty(q.d, device=dev) for q in probs[:nsub]]
+
+    def plain_pass():
+        for i in range(nsub):
+            q, sk = probs[i], handles[i]
+            sk.resketch(q.A, 100 + i)
+            for l, lam in enumerate(lams):
+                sk.solve(q.A, q.b, lam, sds[i][l], tol=tol, max_outer=100, x=x1[i], want_info=False)
+
+    plain_pass()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = max_over_ranks(e0.elapsed_time(e1), ws)
+
+    def batched_sub():
+        for i in range(nsub):
+            handles[i].resketch(probs[i].A, 100 + i)
+        mihs.solve_batched(entries[:nsub], lams, sds=sds[:nsub], tol=tol, max_outer=100, want_info=False)
+
+    batched_sub()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batched_sub()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = max_over_ranks(e0.elapsed_time(e1), ws)
+    out["plain_single_lambda"] = {
+        "value": round(ws * nsub * len(lams) / (ms_p / 1e3), 2), "unit": "(matrix, λ) solves/s",
+        "batched_same_sample": round(ws * nsub * len(lams) / (ms_b / 1e3), 2),
+        "sample": f"the first {nsub} matrices × {len(lams)} λ: one mihs_solve per (matrix, λ) on the "
+                  f"matrix's handle (same sketch, tol {tol:g}, graph rebuilt per λ), against "
+                  f"mihs_solve_batched on the same {nsub} matrices"}
     for sk in handles:
         sk.close()
     return out
