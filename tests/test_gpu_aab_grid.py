@@ -171,3 +171,39 @@ def test_grid_solves_reach_the_solution(grid_form, family):
     assert o.rel_error(xr.cpu().numpy(), xs) <= 1e-10
     assert o.rel_error(xq.cpu().numpy(), xs) <= 1e-10
     assert mihs.device_status() == 0
+
+
+# ---------------- one cluster reading SA from global memory (L2)
+@pytest.mark.parametrize("m,d,lam,k", [(4096, 1024, 1e-3, 12), (3000, 700, 1e-2, 25), (5000, 512, 0.05, 7)])
+def test_cluster_global_sa_matches_oracle(monkeypatch, m, d, lam, k):
+    """SA too large for one cluster's shared memory, cluster form forced (the
+    form the λ-path solves use for such sketches): its blocks read their rows
+    of SA from global memory every pass; k passes against the oracle's
+    Algorithm 5, repeatable."""
+    monkeypatch.setenv("MIHS_AAB_FORM", "cluster")
+    SA, g = _sa_case(m, d, 11 * m + d)
+    dp = (d + 3) // 4 * 4
+    SAp = torch.zeros(m, dp)
+    SAp[:, :d] = SA
+    SAd = SAp.to(DEV).as_strided((m, d), (dp, 1))
+    SAn, gn = SA.numpy().astype(np.float64), g.numpy().astype(np.float64)
+    amp, ref = _amp(SAn, gn, lam, k)
+    passes = torch.zeros(1, dtype=torch.int32, device=DEV)
+    delta = mihs.aab_solve(SAd, g.to(DEV), lam, eps_sub=0.0, max_inner=k, passes=passes)
+    delta2 = mihs.aab_solve(SAd, g.to(DEV), lam, eps_sub=0.0, max_inner=k)
+    assert int(passes.item()) == min(k, m, d)
+    assert o.rel_error(_np(delta), ref) <= 20 * max(amp, 4 * U32 * math.sqrt(d))
+    assert torch.equal(delta, delta2)
+    assert mihs.device_status() == 0
+
+
+def test_cluster_global_quantised_sa(monkeypatch):
+    monkeypatch.setenv("MIHS_AAB_FORM", "cluster")
+    m, d, lam, k = 8192, 1024, 1e-3, 9
+    SA = W.randn((m, d), 77, scale=1.0 / math.sqrt(m))
+    g = W.randn((d,), 78)
+    q, sc = mihs.quantize_sa(SA.to(DEV), "bf16")
+    SAd = _decoded(q, sc, "bf16", m, d)
+    amp, x64 = _amp(SAd, g.numpy().astype(np.float64), lam, k)
+    delta = mihs.aab_solve_q(q, "bf16", sc, d, g.to(DEV), lam, eps_sub=0.0, max_inner=k)
+    assert o.rel_error(_np(delta), x64) <= 20 * max(amp, 4 * U32 * math.sqrt(d))
