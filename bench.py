@@ -347,6 +347,7 @@ def main():
         sketches[families[0]].solve_refined(A, b, p.lam, p.sd, x=x64[families[0]], **kw_r)
         dd_ms, dd_n = mihs.timing_read(mihs.TIMER_APASS_DD)
         pl_ms, pl_n = mihs.timing_read(mihs.TIMER_APASS)
+        co_ms, co_n = mihs.timing_read(mihs.TIMER_APASS_CORR)
         mihs.timing(False)
         dd_avg_s = dd_ms / 1e3 / max(dd_n, 1)
         refined = {"value": round(ws * len(families) / (ms_r / 1e3), 3), "unit": "solves/s",
@@ -354,6 +355,7 @@ def main():
                    "status": {f: inf_r[f].status for f in families},
                    "outer_iters": {f: inf_r[f].outer_iters for f in families},
                    "switch_tol": 1e-7, "plain_steps": pl_n, "compensated_steps": dd_n,
+                   "correction_steps": co_n,
                    "apass_dd_avg_us": round(dd_avg_s * 1e6, 2),
                    "apass_dd_frac_of_hbm": round(bytes_per_pass / dd_avg_s / 1e9 / peaks["hbm_gbs"], 4)}
 
@@ -763,7 +765,11 @@ def run_mixed(args, dev, ws):
                 torch.cuda.synchronize()
                 r["kernel_ms"] = {k: round(mihs.timing_read(t)[0], 2) for k, t in
                                   (("sketch", mihs.TIMER_SKETCH), ("apass", mihs.TIMER_APASS),
-                                   ("apass_dd", mihs.TIMER_APASS_DD), ("aab", mihs.TIMER_AAB))}
+                                   ("apass_dd", mihs.TIMER_APASS_DD), ("apass_corr", mihs.TIMER_APASS_CORR),
+                                   ("aab", mihs.TIMER_AAB))}
+                r["steps"] = {k: mihs.timing_read(t)[1] for k, t in
+                              (("plain", mihs.TIMER_APASS), ("compensated", mihs.TIMER_APASS_DD),
+                               ("correction", mihs.TIMER_APASS_CORR))}
                 mihs.timing(False)
             res[prec] = r
         sk.close()

@@ -78,7 +78,8 @@ int mihs_device_status(int* code);
  * the records and starts recording CUDA events on the launching stream around
  * every launch of: the gradient A-pass (timer 0), AAb_Solver (timer 1), a
  * sketch call (timer 2), the compensated A-pass (timer 3), the backward
- * gradient pass (timer 4) and the λ-path gradient pass (timer 5).  While it
+ * gradient pass (timer 4), the λ-path gradient pass (timer 5) and the fp32
+ * correction passes of refinement solves (timer 6).  While it
  * is on, solves run their steps as host-driven launches and read the stop
  * state back after each step, so only launches that did work are recorded.
  * mihs_timing(0) stops recording.  mihs_timing_read synchronises on the
@@ -296,11 +297,20 @@ int mihs_solve(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
  * compensated pass over A (double-float sums: TwoProduct/TwoSum in fp32
  * pairs, fp64 partial sums), while SA, AAb_Solver and its stop test stay
  * fp32 (the sketch only preconditions; the fixed point of the iteration is
- * where the gradient vanishes).  For targets below the fp32 floor
- * (relative error ~1e-6 and beyond).  x is a DEVICE double array (x¹ on
- * entry if warm_start).  The first refined solve on a handle allocates its
- * workspace (double-float partials, fp64 previous iterate) with cudaMalloc.
- * Same arguments, semantics and errors as mihs_solve otherwise. */
+ * where the gradient vanishes).  Between compensated passes ("refreshes" at
+ * x_ref), steps may take g(x) = g(x_ref) − (AᵀA + λI)(x − x_ref) with the
+ * product from the plain fp32 pass: its rounding is relative to
+ * ‖x − x_ref‖, not to ‖x‖; a refresh follows when that gradient stops
+ * falling, after 8 such steps, or before the solve may stop (only a
+ * compensated gradient ends a solve), and the corrections are switched off
+ * for the rest of the solve once a refresh cycle gains less than 4×
+ * (ill-conditioned problems; environment MIHS_REFINE_CORR=0 switches them
+ * off from the start).  For targets below the fp32 floor (relative error
+ * ~1e-6 and beyond).  x is a DEVICE double array (x¹ on entry if
+ * warm_start).  The first refined solve on a handle allocates its workspace
+ * (double-float partials, fp64 previous iterate, reference point and
+ * gradient) with cudaMalloc.  Same arguments, semantics and errors as
+ * mihs_solve otherwise. */
 int mihs_solve_refined(mihs_sketch_t sk, const float* A, int64_t lda, const float* b,
                        double lambda, const mihs_opts* opts, double* x,
                        mihs_info* info, void* stream);

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
 
   // Control block: every block reads it before the first grid barrier; block
   // 0 writes it only after that barrier.
-  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1;
+  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1, refresh = 1, corr = 0;
   float tol = 0.f, gnorm0 = 0.f, switch_tol = 0.f;
   if (ctl != nullptr) {
     done = ctl->done;
@@ -250,6 +250,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     gnorm0 = ctl->gnorm0;
     phase = ctl->phase;
     switch_tol = ctl->switch_tol;
+    refresh = ctl->refresh;
+    corr = ctl->corr;
   }
   if (done) {  // the same in every block: nothing has written it in this launch
     if (P.cond != 0ull && blk == 0 && tid == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, 0u);
@@ -325,15 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     const float g0 = g0known ? gnorm0 : theta1;
     if (P.hist != nullptr && blk == 0 && tid == 0 && outer < kHistCap) P.hist[outer] = theta1;
     const bool bad = !(theta1 <= 3.0e38f);
-    const bool conv = tol > 0.f && theta1 <= tol * g0;
+    // A refinement correction's gradient is approximate: it never stops the solve.
+    const bool correction = phase == 1 && corr && !refresh;
+    const bool conv = tol > 0.f && theta1 <= tol * g0 && !correction;
     const bool capped = outer >= max_outer;
-    if (phase == 0 && blk == 0 && tid == 0) {  // refinement: switch to the compensated gradient
-      const float gmin = ctl->gmin;
-      const int stall = theta1 < gmin ? 0 : ctl->stall + 1;
-      if (theta1 < gmin) ctl->gmin = theta1;
-      ctl->stall = stall;
-      if (theta1 <= switch_tol * g0 || stall >= 3) ctl->phase = 1;
-    }
+    if (blk == 0 && tid == 0) refine_step_update(ctl, phase, refresh, corr, theta1, g0, tol, switch_tol);
     if (bad || conv || capped) {
       if (blk == 0 && tid == 0) {
         ctl->gnorm = theta1;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
 
   // Solve-mode control block: read everything before the first barrier; only
   // rank 0 writes it, after the last barrier.
-  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1;
+  int done = 0, outer = 0, max_outer = 0, g0known = 0, phase = 1, refresh = 1, corr = 0;
   float tol = 0.f, gnorm0 = 0.f, switch_tol = 0.f;
   if (ctl_ != nullptr) {
     done = ctl_->done;
@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     gnorm0 = ctl_->gnorm0;
     phase = ctl_->phase;
     switch_tol = ctl_->switch_tol;
+    refresh = ctl_->refresh;
+    corr = ctl_->corr;
   }
   cluster.sync();  // every block is running before any DSMEM access
   if (done) {
@@ -352,19 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const float g0 = g0known ? gnorm0 : theta1;
     if (hist_ != nullptr && rank == 0 && tid == 0 && outer < kHistCap) hist_[outer] = theta1;
     const bool bad = !(theta1 <= 3.0e38f);
-    const bool conv = tol > 0.f && theta1 <= tol * g0;
+    // A refinement correction's gradient is approximate: it never stops the solve.
+    const bool correction = phase == 1 && corr && !refresh;
+    const bool conv = tol > 0.f && theta1 <= tol * g0 && !correction;
     const bool capped = outer >= max_outer;
-    // Refinement solves: from the next step on the compensated gradient, once
-    // the plain residual is below switch_tol or has set no new minimum for
-    // three steps (it has reached its fp32 floor, which for a generic
-    // right-hand side can lie above switch_tol).
-    if (phase == 0 && rank == 0 && tid == 0) {
-      const float gmin = ctl_->gmin;
-      const int stall = theta1 < gmin ? 0 : ctl_->stall + 1;
-      if (theta1 < gmin) ctl_->gmin = theta1;
-      ctl_->stall = stall;
-      if (theta1 <= switch_tol * g0 || stall >= 3) ctl_->phase = 1;
-    }
+    if (rank == 0 && tid == 0) refine_step_update(ctl_, phase, refresh, corr, theta1, g0, tol, switch_tol);
     if (bad || conv || capped) {
       if (rank == 0 && tid == 0) {
         ctl_->gnorm = theta1;

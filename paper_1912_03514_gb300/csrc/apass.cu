@@ -40,7 +40,7 @@ apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
                      SolveCtl* __restrict__ ctl, int gate) {
   constexpr int NC = kConsumerWarps, R = NC * RW;
   constexpr bool XS = CH > 8;  // wide rows: keep x in smem instead of registers
-  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;  // uniform
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl_gate(ctl) != gate))) return;  // uniform
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
@@ -190,8 +190,9 @@ apass_partial_kernel(const float* __restrict__ A, int n, int d, long long lda,
 __global__ void __launch_bounds__(256)
 apass_finalize_kernel(const float* __restrict__ partials, int P, int d, int dpad,
                       const float* __restrict__ x, float lambda, const float* __restrict__ rhs,
-                      float* __restrict__ g, const SolveCtl* __restrict__ ctl, int gate) {
-  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
+                      float* __restrict__ g, const SolveCtl* __restrict__ ctl, int gate,
+                      const double* __restrict__ base64) {
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl_gate(ctl) != gate))) return;
   __shared__ float red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -206,7 +207,8 @@ apass_finalize_kernel(const float* __restrict__ partials, int P, int d, int dpad
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += red[k][lane];
     if (rhs != nullptr) t += rhs[j];
-    g[j] = t - (x != nullptr ? lambda * x[j] : 0.f);
+    t -= (x != nullptr ? lambda * x[j] : 0.f);
+    g[j] = base64 != nullptr ? (float)(base64[j] + (double)t) : t;
   }
 }
 
@@ -265,9 +267,11 @@ int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda, cons
   long long lda64 = lda;
   void* args[] = {(void*)&A, &n32, &d32, &lda64, (void*)&b, (void*)&x,
                   (void*)&partials, &dp32, (void*)&rows_per_cta, &stages, (void*)&ctl, &gate};
-  timing_begin(kTimerApass, s);
+  // refinement corrections (gate 2) are timed apart from plain gradients
+  const int timer = gate == 2 ? kTimerApassCorr : kTimerApass;
+  timing_begin(timer, s);
   MIHS_CUDA_TRY(cudaLaunchKernel(k.fn, dim3(P), dim3(kThreads), args, smem, s));
-  timing_end(kTimerApass, s);
+  timing_end(timer, s);
   count_launch();
   return MIHS_OK;
 }
@@ -282,10 +286,10 @@ int apass_device_error(int* code) {
 
 int launch_apass_finalize(const float* partials, int P, int64_t d, const float* x,
                           float lambda, float* g, const SolveCtl* ctl, cudaStream_t s, int gate,
-                          const float* rhs) {
+                          const float* rhs, const double* base64) {
   const int64_t dpad = apass_dpad(d);
   apass_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)dpad,
-                                                                   x, lambda, rhs, g, ctl, gate);
+                                                                   x, lambda, rhs, g, ctl, gate, base64);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

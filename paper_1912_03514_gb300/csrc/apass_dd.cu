@@ -80,7 +80,7 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
                 int stages, SolveCtl* __restrict__ ctl, int gate) {
   constexpr int NC = DdCfg<CH>::NC, R = NC;
   constexpr int kThreads = DdCfg<CH>::kThreads;
-  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;  // uniform
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl_gate(ctl) != gate))) return;  // uniform
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(256)
 apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int dpad,
                          const double* __restrict__ x, double lambda, double* __restrict__ g64,
                          float* __restrict__ g32, const SolveCtl* __restrict__ ctl, int gate,
-                         const float* __restrict__ rhs) {
-  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl->phase != gate))) return;
+                         const float* __restrict__ rhs, double* __restrict__ xref) {
+  if (ctl != nullptr && (ctl->done || (gate >= 0 && ctl_gate(ctl) != gate))) return;
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -276,6 +276,7 @@ apass_dd_finalize_kernel(const float2* __restrict__ partials, int P, int d, int 
     if (x != nullptr) t -= lambda * x[j];
     if (g64 != nullptr) g64[j] = t;
     if (g32 != nullptr) g32[j] = (float)t;
+    if (xref != nullptr) xref[j] = x[j];  // the point this gradient was taken at
   }
 }
 
@@ -344,9 +345,9 @@ int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const flo
 
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
                              double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate,
-                             const float* rhs) {
+                             const float* rhs, double* xref) {
   apass_dd_finalize_kernel<<<(unsigned)((d + 31) / 32), 256, 0, s>>>(partials, P, (int)d, (int)apass_dpad(d), x,
-                                                                     lambda, g64, g32, ctl, gate, rhs);
+                                                                     lambda, g64, g32, ctl, gate, rhs, xref);
   MIHS_CHECK_LAUNCH();
   count_launch();
   return MIHS_OK;

@@ -81,7 +81,7 @@ void timing_end(int which, cudaStream_t s) {
 
 namespace {
 
-__global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int phase, float switch_tol) {
+__global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int phase, float switch_tol, int corr) {
   SolveCtl c = {};
   c.max_outer = max_outer;
   c.tol = tol;
@@ -90,7 +90,19 @@ __global__ void ctl_init_kernel(SolveCtl* ctl, int max_outer, float tol, int pha
   c.switch_tol = switch_tol;
   c.gmin = 3.0e38f;
   c.stall = 0;
+  c.corr = corr;
+  c.refresh = 1;
+  c.since = 0;
+  c.gref = 3.0e38f;
   *ctl = c;
+}
+
+// δ = x − x_ref in fp32 for the correction step of a refinement solve.
+__global__ void refine_delta_kernel(const double* __restrict__ x, const double* __restrict__ xref,
+                                    float* __restrict__ delta, int d, const SolveCtl* __restrict__ ctl) {
+  if (ctl->done || ctl_gate(ctl) != 2) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) delta[j] = (float)(x[j] - xref[j]);
 }
 
 // λ-path control blocks: one per λ (plain solves), the stop counter cleared.
@@ -188,6 +200,9 @@ struct mihs_sketch_s {
   double* x_prev64 = nullptr;
   float* x32_shadow = nullptr;
   float* bw32 = nullptr;  // 2·dp: fp32 roundings of x and v for refined backward solves
+  double* gref64 = nullptr;  // dp: the compensated gradient at the last refresh
+  double* xref64 = nullptr;  // dp: the point it was taken at
+  float* delta32 = nullptr;  // dp: x − x_ref for the fp32 correction pass
   int P_dd = 0;
   double last_sd = 0; // sd estimated by the last solve that was given sd ≤ 0
   SolveCtl* ctl;
@@ -304,16 +319,28 @@ int launch_step(mihs_sketch_s* sk, const mihs_sketch_s::Key& key, const AabLaunc
                 cudaStream_t s, int phase = -1) {
   int rc = MIHS_OK;
   if (refined) {
-    if (phase != 1) {
+    // gate 0: plain fp32 pass at the fp32 shadow of x (phase 0)
+    if (phase < 0 || phase == 0) {
       rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, sk->x32_shadow, sk->partials, sk->ctl, s, 0);
       if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, sk->x32_shadow, (float)key.lam, sk->g,
                                           sk->ctl, s, 0, key.rhs);
     }
-    if (!rc && phase != 0) {
-      rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const double*>(key.x),
-                           sk->dd_partials, sk->ctl, s, 1);
-      if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, static_cast<const double*>(key.x),
-                                             key.lam, nullptr, sk->g, sk->ctl, s, 1, key.rhs);
+    // gate 1: compensated refresh at x, kept with x as (g_ref, x_ref)
+    if (!rc && (phase < 0 || phase == 1)) {
+      const double* x64 = static_cast<const double*>(key.x);
+      rc = launch_apass_dd(key.A, sk->n, sk->d, key.lda, key.b, x64, sk->dd_partials, sk->ctl, s, 1);
+      if (!rc) rc = launch_apass_dd_finalize(sk->dd_partials, sk->P_dd, sk->d, x64, key.lam, sk->gref64, sk->g,
+                                             sk->ctl, s, 1, key.rhs, sk->xref64);
+    }
+    // gate 2: g = g_ref − H(x − x_ref), H·δ by the fp32 pass with b = 0
+    if (!rc && (phase < 0 || phase == 2)) {
+      refine_delta_kernel<<<(unsigned)((sk->d + 255) / 256), 256, 0, s>>>(
+          static_cast<const double*>(key.x), sk->xref64, sk->delta32, (int)sk->d, sk->ctl);
+      MIHS_CHECK_LAUNCH();
+      count_launch();
+      rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, nullptr, sk->delta32, sk->partials, sk->ctl, s, 2);
+      if (!rc) rc = launch_apass_finalize(sk->partials, sk->P, sk->d, sk->delta32, (float)key.lam, sk->g,
+                                          sk->ctl, s, 2, nullptr, sk->gref64);
     }
   } else {
     rc = launch_apass_partial(key.A, sk->n, sk->d, key.lda, key.b, static_cast<const float*>(key.x),
@@ -827,8 +854,8 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   if (refined && sk->dd_partials == nullptr) {
     sk->P_dd = apass_dd_num_partials(n, d);
     char* p = nullptr;
-    const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + sizeof(double) * (size_t)sk->dp +
-                         3 * sizeof(float) * (size_t)sk->dp;
+    const size_t bytes = sizeof(float2) * (size_t)sk->P_dd * sk->dp + 3 * sizeof(double) * (size_t)sk->dp +
+                         4 * sizeof(float) * (size_t)sk->dp;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       set_error("mihs_solve_refined: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -836,8 +863,11 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
     }
     sk->dd_partials = reinterpret_cast<float2*>(p);
     sk->x_prev64 = reinterpret_cast<double*>(p + sizeof(float2) * (size_t)sk->P_dd * sk->dp);
-    sk->x32_shadow = reinterpret_cast<float*>(sk->x_prev64 + sk->dp);
+    sk->gref64 = sk->x_prev64 + sk->dp;
+    sk->xref64 = sk->gref64 + sk->dp;
+    sk->x32_shadow = reinterpret_cast<float*>(sk->xref64 + sk->dp);
     sk->bw32 = sk->x32_shadow + sk->dp;
+    sk->delta32 = sk->bw32 + 2 * sk->dp;
   }
   // sd ≤ 0: estimate it from SA (Algorithm 4 with the paper's T = 2,
   // ε_tr = 0.5); an over-estimate only slows the rate (Remark after
@@ -860,7 +890,14 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   // compensated pass once the relative residual is below 1e-7 or stops
   // improving (the fp32 floor); plain solves never switch.
   const float switch_tol = refined ? 1e-7f : 0.f;
-  ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol, refined ? 0 : 1, switch_tol);
+  // Refinement corrections (fp32 passes between compensated refreshes) are on
+  // unless MIHS_REFINE_CORR=0.
+  static const bool corr_on = [] {
+    const char* e = std::getenv("MIHS_REFINE_CORR");
+    return e == nullptr || std::strcmp(e, "0") != 0;
+  }();
+  ctl_init_kernel<<<1, 1, 0, s>>>(sk->ctl, opts->max_outer, (float)opts->tol, refined ? 0 : 1, switch_tol,
+                                  refined && corr_on ? 1 : 0);
   MIHS_CHECK_LAUNCH();
   count_launch();
   if (opts->warm_start) {
@@ -930,7 +967,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
     // fired (ctl->done).  With per-kernel timing on, the control block is
     // read back after every step so that only working launches are timed.
     const bool poll = timing_on();
-    int phase = poll && refined ? 0 : -1;
+    int phase = poll && refined ? 0 : -1;  // the gate of the next step, when the host knows it
     for (int it = 0; it <= opts->max_outer; ++it) {
       rc = launch_step(sk, key, a, refined, s, phase);
       if (rc) return rc;
@@ -938,7 +975,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
         MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ctl_host, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
         MIHS_CUDA_TRY(cudaStreamSynchronize(s));
         if (sk->ctl_host->done) break;
-        if (refined) phase = sk->ctl_host->phase;
+        if (refined) phase = ctl_gate(sk->ctl_host);
       }
     }
   }
@@ -950,7 +987,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   info->inner_iters_total = c.inner_total;
   info->rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
   info->status = c.done ? c.status : MIHS_NOT_CONVERGED;
-  if (graph_ran) count_launch((refined ? 5ull : 3ull) * (uint64_t)(c.outer + 1));
+  if (graph_ran) count_launch((refined ? 8ull : 3ull) * (uint64_t)(c.outer + 1));
   return info->status;
 }
 

@@ -68,7 +68,63 @@ struct SolveCtl {
   float switch_tol;  // switch to phase 1 once ‖g‖ ≤ switch_tol·‖Aᵀb‖ ...
   float gmin;        // ... or once ‖g‖ has set no new minimum (gmin) for
   int stall;         //     three steps (stall counts them)
+  // Refinement (phase 1): a compensated refresh fixes g(x_ref); the steps
+  // after it take g(x) = g(x_ref) − H(x − x_ref) from an fp32 pass.
+  int corr;          // corrections enabled (cleared when a cycle gains < 4×)
+  int refresh;       // the next gradient is a compensated refresh
+  int since;         // correction steps since the last refresh
+  float gref;        // ‖g‖ at the last refresh
 };
+
+// Bookkeeping of one outer step of a refinement solve, by the one thread
+// that writes the control block, once the step's ‖g‖ (θ₁) is known; phase,
+// refresh and corr are the control block's values when the step began.
+//   phase 0: plain fp32 steps until ‖g‖ ≤ switch_tol·g0 or no new minimum
+//            for three steps (the fp32 floor), then phase 1 with a refresh.
+//   phase 1, corrections on: after a refresh, fp32 corrections until ‖g‖
+//            has set no new minimum for two steps (the correction's own
+//            rounding floor, ∝ ‖x − x_ref‖; the heavy ball's residual is not
+//            monotone), reaches the tolerance (only a refresh may stop the
+//            solve) or 10 steps; corrections are turned off for good once a
+//            whole cycle gained less than 4×.  gmin / stall track the cycle.
+__device__ __forceinline__ void refine_step_update(SolveCtl* c, int phase, int refresh, int corr, float theta1,
+                                                   float g0, float tol, float switch_tol) {
+  if (phase == 0) {
+    const float gmin = c->gmin;
+    const int stall = theta1 < gmin ? 0 : c->stall + 1;
+    if (theta1 < gmin) c->gmin = theta1;
+    c->stall = stall;
+    if (theta1 <= switch_tol * g0 || stall >= 3) {
+      c->phase = 1;
+      c->refresh = 1;
+    }
+  } else if (corr) {
+    if (refresh) {
+      const int on = (c->gref < 3.0e38f && theta1 > 0.25f * c->gref) ? 0 : 1;
+      c->corr = on;
+      c->gref = theta1;
+      c->since = 0;
+      c->gmin = theta1;
+      c->stall = 0;
+      c->refresh = on ? 0 : 1;
+    } else {
+      const int since = c->since + 1;
+      c->since = since;
+      const float gmin = c->gmin;
+      const int stall = theta1 < gmin ? 0 : c->stall + 1;
+      if (theta1 < gmin) c->gmin = theta1;
+      c->stall = stall;
+      if ((tol > 0.f && theta1 <= tol * g0) || stall >= 2 || since >= 10) c->refresh = 1;
+    }
+  }
+}
+
+// Which gradient a step of a refinement solve computes: 0 the plain fp32
+// pass (phase 0), 1 a compensated refresh, 2 an fp32 correction from the
+// last refresh.  Kernels launched with gate k run only when this is k.
+__host__ __device__ inline int ctl_gate(const SolveCtl* c) {
+  return c->phase == 0 ? 0 : (c->refresh ? 1 : 2);
+}
 
 // ------------------------------------------------------------- device side
 __device__ __forceinline__ float warp_sum(float v) {

@@ -23,11 +23,12 @@ int launch_apass_partial(const float* A, int64_t n, int64_t d, int64_t lda,
                          SolveCtl* ctl, cudaStream_t s, int gate = -1);
 // Reads and clears the library-wide device error word (synchronises).
 int apass_device_error(int* code);
-// g[j] = rhs[j] + Σ_p partials[p][j] − λ·x[j] in a fixed order (rhs may be null).
+// g[j] = rhs[j] + Σ_p partials[p][j] − λ·x[j] in a fixed order (rhs may be
+// null); with base64, g[j] = fp32(base64[j] + that) (refinement corrections).
 int launch_apass_finalize(const float* partials, int P, int64_t d,
                           const float* x, float lambda, float* g,
                           const SolveCtl* ctl, cudaStream_t s, int gate = -1,
-                          const float* rhs = nullptr);
+                          const float* rhs = nullptr, const double* base64 = nullptr);
 
 // ---- λ-path gradient (apass_path.cu) ---------------------------------------
 // Per-λ scalars of a path solve (passed by value to the kernels).
@@ -66,10 +67,11 @@ int apass_dd_num_partials(int64_t n, int64_t d);
 int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, const double* x,
                     float2* partials, SolveCtl* ctl, cudaStream_t s, int gate = -1);
 // g64[j] = rhs[j] + Σ_p (hi + lo) − λ·x[j] in fp64 (rhs may be null); g32
-// (optional) its fp32 rounding.  b of launch_apass_dd may be null (taken as 0).
+// (optional) its fp32 rounding; xref (optional) receives x.  b of
+// launch_apass_dd may be null (taken as 0).
 int launch_apass_dd_finalize(const float2* partials, int P, int64_t d, const double* x, double lambda,
                              double* g64, float* g32, const SolveCtl* ctl, cudaStream_t s, int gate = -1,
-                             const float* rhs = nullptr);
+                             const float* rhs = nullptr, double* xref = nullptr);
 int apass_dd_device_error(int* code);
 
 // ---- AAb_Solver (aab.cu) --------------------------------------------------
@@ -156,7 +158,8 @@ int estimate_sd(const float* SA, int64_t m, int64_t d, int64_t ldsa, double lamb
                 uint64_t seed, double* sd_out, cudaStream_t s);
 
 // ---- per-kernel event timing (api.cu) -------------------------------------
-enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kTimerBackward = 4, kTimerApassPath = 5, kNumTimers = 6 };
+enum TimerId { kTimerApass = 0, kTimerAab = 1, kTimerSketch = 2, kTimerApassDd = 3, kTimerBackward = 4, kTimerApassPath = 5,
+               kTimerApassCorr = 6, kNumTimers = 7 };
 bool timing_on();
 void timing_begin(int which, cudaStream_t s);
 void timing_end(int which, cudaStream_t s);

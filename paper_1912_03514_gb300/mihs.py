@@ -161,7 +161,8 @@ def launch_count() -> int:
     return int(lib().mihs_launch_count())
 
 
-TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD, TIMER_BACKWARD, TIMER_APASS_PATH = 0, 1, 2, 3, 4, 5
+TIMER_APASS, TIMER_AAB, TIMER_SKETCH, TIMER_APASS_DD, TIMER_BACKWARD, TIMER_APASS_PATH, TIMER_APASS_CORR = \
+    0, 1, 2, 3, 4, 5, 6
 
 
 def timing(on: bool) -> None:

@@ -65,6 +65,7 @@ def test_refined_solve_switches_phase_once():
             xt, it = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12, max_outer=200)
             _, n_plain = mihs.timing_read(mihs.TIMER_APASS)
             _, n_dd = mihs.timing_read(mihs.TIMER_APASS_DD)
+            _, n_corr = mihs.timing_read(mihs.TIMER_APASS_CORR)
         finally:
             mihs.timing(False)
         hist = np.asarray(sk.history(), dtype=np.float64)
@@ -72,7 +73,8 @@ def test_refined_solve_switches_phase_once():
     assert torch.equal(xg, xt)
     assert ig.outer_iters == it.outer_iters
     assert n_plain >= 1 and n_dd >= 1
-    assert n_plain + n_dd == it.outer_iters + 1  # one gradient per step plus the final stop test
+    # one gradient per step plus the final stop test (which is a refresh)
+    assert n_plain + n_dd + n_corr == it.outer_iters + 1
     # the switch came at the first step whose plain residual was ≤ 1e-7·‖Aᵀb‖
     # or had set no new minimum for three steps
     gmin, stall, k_exp = np.inf, 0, None
@@ -122,3 +124,30 @@ def test_solve_with_estimated_sd():
     with mihs.Sketch(A, "gaussian", p.m, seed=5) as sk:
         x, info = sk.solve(A, b, p.lam, 0.0, tol=1e-6, max_outer=300)
     assert info.converged and o.rel_error(x.cpu().double().numpy(), xs) <= 1e-5
+
+
+def test_refinement_corrections_between_refreshes():
+    """κ(H) ≈ 1e4 (the 262144×1024 workload's conditioning at a size the
+    oracle refines quickly): after the compensated refresh, fp32 corrections
+    g(x_ref) − H(x − x_ref) carry most refinement steps, the solve still ends
+    on a compensated gradient and reaches 1e-10 of the exact solution."""
+    n, d = 32768, 256
+    sigma = 1.0 / np.arange(1, d + 1, dtype=np.float64)
+    p = W.make_problem(n, d, sigma, 1e-4, 40.0, seed=23)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam, refine=3, extended=True)
+    with mihs.Sketch(A, "countsketch", p.m, seed=14) as sk:
+        xg, ig = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12, max_outer=300)
+        mihs.timing(True)
+        try:
+            xt, it = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12, max_outer=300)
+            _, n_plain = mihs.timing_read(mihs.TIMER_APASS)
+            _, n_dd = mihs.timing_read(mihs.TIMER_APASS_DD)
+            _, n_corr = mihs.timing_read(mihs.TIMER_APASS_CORR)
+        finally:
+            mihs.timing(False)
+    assert ig.converged and it.converged, (ig, it)
+    assert torch.equal(xg, xt)  # graph (gated launches) and host-driven steps agree
+    assert n_plain + n_dd + n_corr == it.outer_iters + 1
+    assert n_corr > n_dd >= 1, (n_plain, n_dd, n_corr)
+    assert o.rel_error(xg.cpu().numpy(), xs) <= 1e-10
