@@ -244,6 +244,36 @@ def test_solve_small_problem_matches_exact(family):
     assert o.certify(p.A.numpy(), p.b.numpy(), _np(x), p.lam) >= np.linalg.norm(_np(x) - xs) * (1 - 1e-6)
 
 
+# n, d, decades, λ (m = 4·sd rounded up to 4, at most n): tiny, ragged widths
+# (not multiples of 4 or 128), one column, m close to n, and wide sketches
+# (SA too large for one cluster: the grid form of AAb_Solver runs)
+SOLVE_EDGE = [(64, 3, 1.0, 1e-2), (1000, 129, 2.0, 1e-3), (5000, 1, 0.0, 0.1),
+              (120, 50, 3.0, 1e-3), (20000, 777, 2.0, 1e-3), (8192, 2048, 2.0, 5e-2)]
+
+
+@pytest.mark.parametrize("n,d,decades,lam", SOLVE_EDGE)
+@pytest.mark.parametrize("family", ["gaussian", "countsketch", "srht"])
+def test_solve_edge_shapes_match_exact(n, d, decades, lam, family):
+    sigma = W.profile_exponential(d, decades) if d > 1 else np.ones(1)
+    m = int(min(n, math.ceil(4 * W.nominal_sd(sigma, lam) / 4) * 4))
+    p = W.make_problem(n, d, sigma, lam, 30.0, seed=n + d, m=m)
+    dp = (d + 3) // 4 * 4
+    Ap = torch.zeros(n, dp)
+    Ap[:, :d] = p.A
+    A = Ap.to(DEV).as_strided((n, d), (dp, 1))
+    b = p.b.to(DEV)
+    sd = min(W.nominal_sd(sigma, lam), 0.9 * m)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), lam, refine=2, dd=True)
+    with mihs.Sketch(A, family, m, seed=77) as sk:
+        x, info = sk.solve(A, b, lam, sd, tol=1e-6, max_outer=400)
+        xr, ir = sk.solve_refined(A, b, lam, sd, tol=1e-12, max_outer=400)
+    assert info.converged and ir.converged, (info, ir)
+    # residual 1e-6 bounds the error by κ(H)·1e-6 (κ(H) up to ≈ 1e3 here)
+    kappa = (sigma.max() ** 2 + lam) / (sigma.min() ** 2 + lam)
+    assert o.rel_error(_np(x), xs) <= max(1e-5, 2e-6 * kappa)
+    assert o.rel_error(xr.cpu().numpy(), xs) <= 1e-9
+
+
 def test_solve_history_matches_info():
     p = W.problem_scaled(20000, 300, seed=8)
     A, b = p.A.to(DEV), p.b.to(DEV)
