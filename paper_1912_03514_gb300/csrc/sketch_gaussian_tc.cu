@@ -30,6 +30,7 @@
 #include <cuda.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.h"
@@ -41,21 +42,30 @@ namespace {
 constexpr int TM = 128;          // sketch rows per tile (MMA M)
 constexpr int TN = 256;          // columns of A per tile (MMA N)
 constexpr int TK = 32;           // rows of A per TMA load (a tf32 stage: 4 MMAs of K = 8)
-constexpr int kStages = 3;       // operand ring
-constexpr int kStg = 2;          // staging ring (TMA → transposers)
-// K rows per operand stage: 32 tf32 or 64 bf16 values fill one 128-byte
-// swizzled row, so both operand types use the same layout and descriptors.
-template <bool BF>
-constexpr int stage_k() { return BF ? 64 : 32; }
 constexpr int kGenWarps = 16;    // S generators (warps 2–17); warps 2–5 then run the epilogue
 constexpr int kTrWarps = 4;      // A transposers (warps 18–21)
 constexpr int kThreads = (2 + kGenWarps + kTrWarps) * 32;  // warp 0: MMA, warp 1: TMA
-constexpr uint32_t kSBytes = TM * TK * 4;       // 16 KB
-constexpr uint32_t kABytes = TK * TN * 4;       // 32 KB
-constexpr uint32_t kStageBytes = kSBytes + kABytes;
-constexpr size_t kSmemBytes =
-    (size_t)kStages * kStageBytes + (size_t)kStg * kABytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kSBytes = TM * TK * 4;       // one 128-row S tile: 16 KB
+constexpr uint32_t kABytes = TK * TN * 4;       // one 32-row fp32 A tile: 32 KB
+
+// Shape of one kernel variant.  BF: bf16 operands (64 K per 128-byte
+// swizzled row) or tf32 (32 K), so both use the same layout and descriptors.
+// MT: sketch-row tiles per block (two TMEM accumulators of 256 columns when
+// MT = 2, so that each staged and transposed A tile feeds twice the MMA
+// work — the kernel is bound by shared-memory traffic, not by the MMA).
+// Operand ring and staging ring (TMA → transposers) depths fill ≤ 227 KB.
+template <bool BF, int MT>
+struct TcCfg {
+  static constexpr int KT = BF ? 64 : 32;        // K rows per operand stage
+  static constexpr int NSLOT = KT / TK;          // 32-row TMA loads per stage
+  static constexpr uint32_t SBytes = MT * kSBytes;
+  static constexpr uint32_t StageBytes = SBytes + kABytes;
+  static constexpr int NSTAGE = MT == 1 ? (BF ? 2 : 3) : 2;
+  static constexpr int NSTG = MT == 1 ? (BF ? 4 : 2) : 3;
+  static constexpr uint32_t TmemCols = 256u * MT;
+  static constexpr size_t Smem = (size_t)NSTAGE * StageBytes + (size_t)NSTG * kABytes + 1024 /*align*/ +
+                                 256 /*barriers*/;
+};
 
 __device__ int g_gauss_tc_error = 0;
 
@@ -203,26 +213,32 @@ struct GaussTcArgs {
 
 // BF = false: tf32 operands (kind::tf32, 32 K per stage); BF = true: S and A
 // rounded to bf16 (kind::f16, 64 K per stage, two TMA loads of 32 rows).
-template <bool BF>
+// MT sketch-row tiles of 128 per block, one TMEM accumulator each.
+template <bool BF, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
 gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a) {
-  constexpr int KT = stage_k<BF>();
-  constexpr int NSLOT = KT / TK;  // TMA loads (staging slots) per operand stage
+  using C = TcCfg<BF, MT>;
+  constexpr int KT = C::KT;
+  constexpr int NSLOT = C::NSLOT;  // TMA loads (staging slots) per operand stage
+  constexpr int NSTAGE = C::NSTAGE;
+  constexpr int NSTG = C::NSTG;
+  constexpr uint32_t kStageBytes = C::StageBytes;
+  constexpr int MROWS = MT * TM;   // sketch rows of the block
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment for the 128-byte swizzle atoms.
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char* stg = base + (size_t)kStages * kStageBytes;           // staging ring
-  uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)kStg * kABytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* stg_full = empty + kStages;
-  uint64_t* stg_empty = stg_full + kStg;
-  uint64_t* accum = stg_empty + kStg;
+  unsigned char* stg = base + (size_t)NSTAGE * kStageBytes;           // staging ring
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)NSTG * kABytes);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* stg_full = empty + NSTAGE;
+  uint64_t* stg_empty = stg_full + NSTG;
+  uint64_t* accum = stg_empty + NSTG;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accum + 1);
   volatile uint32_t* gen_abort = tmem_holder + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.y * TM;             // first sketch row
+  const int i0 = blockIdx.y * MROWS;          // first sketch row
   const int c0 = blockIdx.x * TN;             // first column of A
   const int kb0 = blockIdx.z * a.rows_per_split;
   const int kb1 = min(a.n, kb0 + a.rows_per_split);
@@ -230,15 +246,15 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
 
   const int cn = a.cn;
   const uint32_t crank = cn > 1 ? cluster_rank() : 0u;
-  // This block's slice of the S tile's rows (contiguous bytes: row g of the
-  // swizzled tile occupies bytes [128g, 128g + 128)).
-  const int g_lo = (int)((TM * crank) / (uint32_t)cn), g_hi = (int)((TM * (crank + 1)) / (uint32_t)cn);
+  // This block's slice of the stage's S rows (contiguous bytes: row g of the
+  // MT stacked swizzled tiles occupies bytes [128g, 128g + 128)).
+  const int g_lo = (int)((MROWS * crank) / (uint32_t)cn), g_hi = (int)((MROWS * (crank + 1)) / (uint32_t)cn);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1 + kTrWarps);  // generator leader (+ peers' bytes), transposer warps
       mbar_init(&empty[s], cn);           // MMA commits of every block of the cluster
     }
-    for (int s = 0; s < kStg; ++s) {
+    for (int s = 0; s < NSTG; ++s) {
       mbar_init(&stg_full[s], 1);                 // TMA expect_tx arrival
       mbar_init(&stg_empty[s], kTrWarps);
     }
@@ -247,7 +263,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                 "r"(kTmemCols)
+                 "r"(C::TmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -261,25 +277,29 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        const int s = kb % NSTAGE;
+        const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
         if (!mbar_wait(&full[s], ph, kWaitLimitNs)) {
           atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
           break;
         }
         tc_fence_after();
         const uint32_t sS = smem_u32(base + (size_t)s * kStageBytes);
-        const uint32_t sA = sS + kSBytes;
+        const uint32_t sA = sS + C::SBytes;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           // Both operands K-major: 8-row atoms of 1024 B; each MMA covers 32
-          // bytes of K (8 tf32 or 16 bf16 values).
-          const uint64_t ad = smem_desc_sw128(sS + kk * 32, 16, 1024);
+          // bytes of K (8 tf32 or 16 bf16 values).  Tile t of S (rows
+          // 128t … 128t + 127) accumulates into TMEM columns 256t ….
           const uint64_t bd = smem_desc_sw128(sA + kk * 32, 16, 1024);
-          if constexpr (BF)
-            mma_bf16(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
-          else
-            mma_tf32(tmem, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+          for (int t = 0; t < MT; ++t) {
+            const uint64_t ad = smem_desc_sw128(sS + t * kSBytes + kk * 32, 16, 1024);
+            if constexpr (BF)
+              mma_bf16(tmem + 256u * t, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+            else
+              mma_tf32(tmem + 256u * t, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+          }
         }
         if (cn > 1)
           mma_commit_mc(&empty[s], (uint16_t)((1u << cn) - 1u));
@@ -289,8 +309,8 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
       mma_commit(accum);  // fires when every MMA issued above has completed
       // Drain: the last rounds' commits of every block of the cluster have
       // arrived here before this block may exit (its barriers stay valid).
-      for (int kb = nkb > kStages ? nkb - kStages : 0; kb < nkb; ++kb)
-        if (!mbar_wait(&empty[kb % kStages], (uint32_t)(kb / kStages) & 1u, kWaitLimitNs)) {
+      for (int kb = nkb > NSTAGE ? nkb - NSTAGE : 0; kb < nkb; ++kb)
+        if (!mbar_wait(&empty[kb % NSTAGE], (uint32_t)(kb / NSTAGE) & 1u, kWaitLimitNs)) {
           atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
           break;
         }
@@ -301,9 +321,9 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     if (lane == 0) {
       // load j covers rows kb0 + 32j … (NSLOT loads per operand stage)
       for (int j = 0; j < nkb * NSLOT; ++j) {
-        const int s = j % kStg;
-        const uint32_t ph = (uint32_t)(j / kStg) & 1u;
-        if (j >= kStg && !mbar_wait(&stg_empty[s], ph ^ 1u, kWaitLimitNs)) {
+        const int s = j % NSTG;
+        const uint32_t ph = (uint32_t)(j / NSTG) & 1u;
+        if (j >= NSTG && !mbar_wait(&stg_empty[s], ph ^ 1u, kWaitLimitNs)) {
           atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
           break;
         }
@@ -317,17 +337,17 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     const int tt = threadIdx.x - (2 + kGenWarps) * 32;  // 0..127: columns tt, tt + 128
     bool stop = false;
     for (int kb = 0; kb < nkb && !stop; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((uint32_t)(kb / kStages) & 1u) ^ 1u, kWaitLimitNs)) {
+      const int s = kb % NSTAGE;
+      if (kb >= NSTAGE && !mbar_wait(&empty[s], ((uint32_t)(kb / NSTAGE) & 1u) ^ 1u, kWaitLimitNs)) {
         atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
         break;
       }
-      unsigned char* dstA = base + (size_t)s * kStageBytes + kSBytes;
+      unsigned char* dstA = base + (size_t)s * kStageBytes + C::SBytes;
 #pragma unroll
       for (int sl = 0; sl < NSLOT; ++sl) {
         const int j = kb * NSLOT + sl;
-        const int q = j % kStg;
-        if (!mbar_wait(&stg_full[q], (uint32_t)(j / kStg) & 1u, kWaitLimitNs)) {
+        const int q = j % NSTG;
+        if (!mbar_wait(&stg_full[q], (uint32_t)(j / NSTG) & 1u, kWaitLimitNs)) {
           atomicExch(&g_gauss_tc_error, MIHS_ERR_TIMEOUT);
           stop = true;
           break;
@@ -379,9 +399,9 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     const int nitems = (g_hi - g_lo) * 8;
     const uint32_t slice_off = (uint32_t)g_lo * 128u, slice_bytes = (uint32_t)(g_hi - g_lo) * 128u;
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      if (kb >= kStages) {
+      const int s = kb % NSTAGE;
+      const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
+      if (kb >= NSTAGE) {
         // One thread waits (bounded) and every generator takes its verdict, so
         // that all of them reach the same named barriers.
         if (g == 0) *gen_abort = mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs) ? 0u : 1u;
@@ -435,7 +455,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
       named_sync(1, kGenWarps * 32);   // every generator has written its part
       if (g == 0) {
         // This block's stage is complete once the peers' slices have landed.
-        mbar_arrive_expect_tx(&full[s], (uint32_t)(TM * 128) - slice_bytes);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(MROWS * 128) - slice_bytes);
         const uint32_t src = smem_u32(sS) + slice_off;
         for (int p = 1; p < cn; ++p) {
           const uint32_t peer = (crank + (uint32_t)p) % (uint32_t)cn;
@@ -451,11 +471,13 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
     tc_fence_after();
     const int qw = warp & 3;                 // TMEM lanes 32·qw … 32·qw + 31
     const int row_local = 32 * qw + lane;
-    const int grow = i0 + row_local;
+#pragma unroll 1
+    for (int t = 0; t < MT; ++t) {          // tile t: TMEM columns 256t …
+    const int grow = i0 + TM * t + row_local;
     float* dst = a.part + ((size_t)blockIdx.z * a.m + (size_t)(grow < a.m ? grow : 0)) * a.dp;
     for (int cc = 0; cc < TN; cc += 32) {
       float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)cc, v);
+      tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(256 * t + cc), v);
       if (grow < a.m) {
         const int col = c0 + cc;
         const bool have = ok && nkb > 0;
@@ -471,6 +493,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
       }
     }
     }
+    }
   }
 done:
   tc_fence_before();
@@ -478,7 +501,7 @@ done:
   if (cn > 1) cluster_sync_all();  // no block exits while a peer may still copy into it
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TmemCols) : "memory");
   }
 }
 
@@ -518,8 +541,20 @@ bool gaussian_tc_available() { return encode_fn() != nullptr; }
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
                        int64_t ldsa, cudaStream_t s, bool bf16) {
   using KernFn = void (*)(const CUtensorMap, const GaussTcArgs);
-  const KernFn kern = bf16 ? gauss_tc_kernel<true> : gauss_tc_kernel<false>;
-  const int KT = bf16 ? stage_k<true>() : stage_k<false>();
+  // Two 128-row sketch tiles per block whenever there are two to share the
+  // staged A tiles (MIHS_GAUSSIAN_MT=1 keeps one).
+  static const bool force_mt1 = [] {
+    const char* e = std::getenv("MIHS_GAUSSIAN_MT");
+    return e != nullptr && std::atoi(e) == 1;
+  }();
+  const int tm = (int)((m + TM - 1) / TM);
+  const int MT = (tm >= 2 && !force_mt1) ? 2 : 1;
+  const KernFn kern = bf16 ? (MT == 2 ? gauss_tc_kernel<true, 2> : gauss_tc_kernel<true, 1>)
+                           : (MT == 2 ? gauss_tc_kernel<false, 2> : gauss_tc_kernel<false, 1>);
+  const size_t kSmemBytes = bf16 ? (MT == 2 ? TcCfg<true, 2>::Smem : TcCfg<true, 1>::Smem)
+                                 : (MT == 2 ? TcCfg<false, 2>::Smem : TcCfg<false, 1>::Smem);
+  const int KT = bf16 ? TcCfg<true, 1>::KT : TcCfg<false, 1>::KT;
+  const int tmb = (tm + MT - 1) / MT;  // blocks along the sketch rows
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) {
     set_error("gaussian sketch: cuTensorMapEncodeTiled unavailable");
@@ -537,7 +572,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
     set_error("gaussian sketch: cuTensorMapEncodeTiled failed (%d)", (int)r);
     return MIHS_ERR_UNSUPPORTED;
   }
-  const int tn = (int)((d + TN - 1) / TN), tm = (int)((m + TM - 1) / TM);
+  const int tn = (int)((d + TN - 1) / TN);
   const int64_t kblocks = (n + KT - 1) / KT;
   MIHS_CUDA_TRY(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   // One cluster per (sketch-row tile, K split) holds the tn column tiles.
@@ -567,7 +602,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   {
     double best = 1e300;
     for (int64_t ks = 1; ks <= kblocks && ks <= 256; ++ks) {
-      const int64_t cl = (int64_t)tm * ks;
+      const int64_t cl = (int64_t)tmb * ks;
       const int64_t waves = (cl + active - 1) / active;
       const double cost = (double)waves * (64.0 + (double)((kblocks + ks - 1) / ks));
       if (cost < best * 0.999) {
@@ -599,7 +634,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
     attr[0].val.clusterDim.x = (unsigned)tn;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)tn, (unsigned)tm, (unsigned)KS);
+    cfg.gridDim = dim3((unsigned)tn, (unsigned)tmb, (unsigned)KS);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = kSmemBytes;
     cfg.stream = s;
