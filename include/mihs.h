@@ -154,8 +154,15 @@ int mihs_gradient_noalloc(const float* A, int64_t n, int64_t d, int64_t lda,
  *   passes: optional DEVICE int* receiving the number of loop passes.
  * Any ldsa ≥ d is accepted when SA fits in the cluster's shared memory
  * (m·d ≲ 800K); larger SA must have 16-byte aligned rows (ldsa % 4 == 0).
- * Runs as one thread-block cluster; allocates nothing.
- * Errors: INVALID_ARG (λ ≤ 0, eps_sub < 0, sizes), CUDA. */
+ * Runs as one thread-block cluster with SA in its shared memory; an SA too
+ * large for that runs as one cooperative grid of up to one block per SM with
+ * SA spread over their shared memory, whose scratch (one d-vector per SM,
+ * about 1.2 MB at d = 2048) comes from the stream-ordered pool and is freed
+ * on the same stream (the environment variable MIHS_AAB_FORM=cluster keeps
+ * one cluster reading SA from L2 instead).  Grid-form calls on different
+ * streams should not overlap: two grids that wait for each other's blocks
+ * end with MIHS_ERR_TIMEOUT after 2 s.
+ * Errors: INVALID_ARG (λ ≤ 0, eps_sub < 0, sizes), CUDA, OOM, TIMEOUT. */
 int mihs_aab_solve(const float* SA, int64_t m, int64_t d, int64_t ldsa,
                    const float* g, double lambda, double eps_sub, int max_inner,
                    float* delta, int* passes, void* stream);

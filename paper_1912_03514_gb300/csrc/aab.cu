@@ -17,7 +17,10 @@
 //     from partials summed in a fixed order, so all blocks take the same
 //     branch and the result is deterministic.
 // The d-vectors of the recursion (v, d, x) are replicated per block (O(d)
-// work, negligible next to the O(md/CL) products).
+// work, negligible next to the O(md/CL) products).  When SA is too large for
+// the shared memory of 16 blocks, launch_aab hands a single-λ solve that has
+// scratch to the grid form (aab_grid.cu); otherwise the cluster's blocks
+// read their rows of SA from global memory (L2) on every pass.
 #include <cstdlib>
 #include <cstring>
 #include <map>
