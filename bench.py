@@ -69,6 +69,9 @@ def parse():
                     help="also solve the mixed-precision workload with the fp64 oracle on the host (slow)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the per-family solves of a step one after another on one stream")
+    ap.add_argument("--aab", default="",
+                    help="form of AAb_Solver in the step's solves: auto, cluster, grid or grid:<blocks> "
+                         "(default: grid:24 when the solves share the GPU on concurrent streams, else auto)")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
                                             "aab-wide-bf16", "dual-grad",
                                             "gaussian", "gaussian-bf16", "countsketch", "srht"],
@@ -226,6 +229,13 @@ def main():
     n, d, m = p.n, p.d, p.m
     seed = 0x5EED0000 + rank
     sketches = {f: mihs.Sketch(A, f, m, seed) for f in families}
+    # Concurrent solves: a 24-block grid AAb starts on whichever SMs the other
+    # streams' gradient passes leave free; a 16-block cluster needs one GPU
+    # processing cluster with 16 free SMs and waits for it.
+    aab = args.aab or ("auto" if args.sequential or len(families) == 1 else "grid:24")
+    aab_form, _, aab_blocks = aab.partition(":")
+    for sk in sketches.values():
+        sk.set_aab(aab_form, int(aab_blocks or 0))
     xs = {f: torch.empty(d, dtype=torch.float32, device=dev) for f in families}
     kw = dict(tol=args.tol, max_outer=args.max_outer, eps_sub=0.1)
 
@@ -393,7 +403,7 @@ def main():
                 streams[f].wait_event(ev)
                 with torch.cuda.stream(streams[f]):
                     mihs.solve(A_pin, b_pin, p.lam, f, m, p.sd, seed=seed, out=outs[f],
-                               want_info=False, **kw)
+                               want_info=False, aab=aab, **kw)
             for f in families:
                 main_stream.wait_stream(streams[f])
 
@@ -454,6 +464,7 @@ def main():
                        "stop": "‖Aᵀ(b−Ax)−λx‖ ≤ tol·‖Aᵀb‖", "eps_sub": 0.1,
                        "families": families, "l2": "inputs larger than L2 (A = %.2f GB)" % (4 * n * d / 1e9),
                        "streams": "sequential" if args.sequential else "one CUDA stream per family (independent solves run concurrently)",
+                       "aab": aab,
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "gpu_launches": launches_per_step * args.steps,
             "per_family_ms": per_family,

@@ -248,6 +248,28 @@ int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream);
  * (Algorithm 4) keeps using the fp32 SA.  Errors: INVALID_ARG, OOM, CUDA. */
 int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream);
 
+/* Form of the inner solver (AAb_Solver, Algorithm 5) in a handle's solves
+ * (mihs_solve, mihs_solve_refined, mihs_backward*):
+ *   MIHS_AAB_AUTO     one thread-block cluster holding SA in its distributed
+ *                     shared memory when it fits, else one cooperative grid
+ *                     holding SA in the shared memory of up to every SM;
+ *   MIHS_AAB_CLUSTER  always one cluster (SA read from L2 when it does not
+ *                     fit);
+ *   MIHS_AAB_GRID     one cooperative grid of `grid_blocks` blocks (0: one per
+ *                     SM, at most m), raised to the fewest that hold SA in
+ *                     shared memory; the cluster form when the grid cannot be
+ *                     made resident.
+ * The cluster form is the faster one for a solve that has the GPU to itself.
+ * A small grid (about 24 blocks) is the better choice when several solves
+ * share the GPU on concurrent streams: its blocks start on any free SMs,
+ * while a 16-block cluster waits until one GPU processing cluster has 16
+ * free SMs.  Results agree to fp32 rounding (the summation order differs).
+ * λ-paths, batched and dual solves and the row-level mihs_aab_* calls keep
+ * MIHS_AAB_AUTO.  Not to be called while a solve on the handle is in
+ * flight.  Errors: INVALID_ARG (unknown form, grid_blocks < 0). */
+enum { MIHS_AAB_AUTO = 0, MIHS_AAB_CLUSTER = 1, MIHS_AAB_GRID = 2 };
+int mihs_sketch_set_aab(mihs_sketch_t sk, int form, int grid_blocks);
+
 /* Release a handle (synchronises the device first).  NULL is a no-op. */
 int mihs_sketch_destroy(mihs_sketch_t sk);
 

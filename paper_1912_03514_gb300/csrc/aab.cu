@@ -132,7 +132,9 @@ ClusterPlan plan_cluster(int m, int dp, int sa_type) {
 
 void aab_prepare(int m, int d, int sa_type) { (void)plan_cluster(m, (int)round_up(d, 4), sa_type); }
 
-bool aab_grid_wanted(int m, int d, int sa_type) {
+bool aab_grid_wanted(int m, int d, int sa_type, int form) {
+  if (form == MIHS_AAB_GRID) return true;
+  if (form == MIHS_AAB_CLUSTER) return false;
   if (const char* e = std::getenv("MIHS_AAB_FORM")) {
     if (std::strcmp(e, "grid") == 0) return true;
     if (std::strcmp(e, "cluster") == 0) return false;
@@ -182,8 +184,9 @@ int launch_aab(const AabLaunch& a, cudaStream_t s) {
   }
   P.sa_scale = a.sa_type == MIHS_SA_FP8E4M3 ? a.sa_scale : nullptr;
   P.scale_ld = (int)((round_up(a.d, 4) + 127) / 128);
-  if (!a.path && a.grid_ws != nullptr && aab_grid_wanted(a.m, a.d, a.sa_type)) {
-    // SA does not fit one cluster's shared memory: spread it over the SMs.
+  if (!a.path && a.grid_ws != nullptr && aab_grid_wanted(a.m, a.d, a.sa_type, a.aab_form)) {
+    // SA does not fit one cluster's shared memory (or the caller asked for
+    // the grid form): spread it over the SMs.
     const int rc = launch_aab_grid(a, a.grid_ws, s);
     if (rc != MIHS_ERR_UNSUPPORTED) return rc;
   }

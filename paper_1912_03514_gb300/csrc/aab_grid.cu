@@ -17,6 +17,7 @@
 // global memory whose top bit flips once all blocks have arrived
 // (grid_sync.cuh); each wait is bounded and a wait that runs out stops the
 // solve with MIHS_ERR_TIMEOUT instead of hanging.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -534,30 +535,39 @@ struct GridPlan {
   size_t smem = 0;
 };
 
-// Rows per block so that SA is spread over at most one block per SM, and the
-// launch that holds it; G = 0 when it does not fit.
-GridPlan plan_grid(int m, int dp, int sa_type) {
+// Rows per block so that SA is spread over `blocks` blocks (0: one per SM),
+// raised to the fewest blocks whose row slices fit in shared memory, and the
+// launch that holds it; G = 0 when SA does not fit even one block per SM.
+GridPlan plan_grid(int m, int dp, int sa_type, int blocks) {
   GridPlan gp;
   const int nsm = num_sms();
   int want = nsm;
-  if (const char* e = std::getenv("MIHS_AAB_GRID_BLOCKS")) {
+  if (blocks > 0) {
+    want = blocks;
+  } else if (const char* e = std::getenv("MIHS_AAB_GRID_BLOCKS")) {
     const int v = std::atoi(e);
-    if (v > 0 && v < want) want = v;
+    if (v > 0) want = v;
   }
-  const int R = (m + want - 1) / want;
-  const int G = (m + R - 1) / R;
-  if (G > 256) return gp;  // the kernel sums block partials with one load per lane and 8 per warp
-  const int cs = (int)round_up((dp + G - 1) / G, 4);
+  if (want > nsm) want = nsm;
   const int pitch = sa_type == MIHS_SA_FP32 ? dp : (int)round_up(dp, 16);
-  const GridSmem L = grid_smem_layout(dp, (int)round_up(R, 4), cs, R, pitch, (int)elem_size(sa_type));
-  if (L.total > kSmemBudget + 16 * 1024) return gp;
-  gp.G = G;
-  gp.R = R;
-  gp.Rpad = (int)round_up(R, 4);
-  gp.cs = cs;
-  gp.pitch = pitch;
-  gp.smem = L.total;
-  return gp;
+  for (;; want = std::min(nsm, want + (want < 8 ? 1 : want / 8))) {
+    const int R = (m + want - 1) / want;
+    const int G = (m + R - 1) / R;
+    if (G > 256) return gp;  // the kernel sums block partials with one load per lane and 8 per warp
+    const int cs = (int)round_up((dp + G - 1) / G, 4);
+    const GridSmem L = grid_smem_layout(dp, (int)round_up(R, 4), cs, R, pitch, (int)elem_size(sa_type));
+    if (L.total > kSmemBudget + 16 * 1024) {
+      if (want >= nsm) return gp;
+      continue;
+    }
+    gp.G = G;
+    gp.R = R;
+    gp.Rpad = (int)round_up(R, 4);
+    gp.cs = cs;
+    gp.pitch = pitch;
+    gp.smem = L.total;
+    return gp;
+  }
 }
 
 std::mutex g_grid_mu;
@@ -586,7 +596,7 @@ int launch_aab_grid(const AabLaunch& a, void* ws, cudaStream_t s) {
   const bool vec = (reinterpret_cast<uintptr_t>(a.SA) & 15u) == 0 &&
                    (a.sa_type != MIHS_SA_FP32 || a.ldsa % 4 == 0);
   if (a.sa_type != MIHS_SA_FP32 && (!vec || a.ldsa < round_up(dp, 16))) return MIHS_ERR_UNSUPPORTED;
-  const GridPlan gp = plan_grid(a.m, dp, a.sa_type);
+  const GridPlan gp = plan_grid(a.m, dp, a.sa_type, a.grid_blocks);
   if (gp.G == 0) return MIHS_ERR_UNSUPPORTED;
   const GridFn fn = grid_kernel(dp, a.sa_type);
   {

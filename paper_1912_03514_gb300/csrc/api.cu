@@ -218,8 +218,10 @@ struct mihs_sketch_s {
     double lam, alpha, beta; float eps; int max_passes;
     const float* rhs;  // adjoint solves: g = rhs − AᵀAx − λx (b null)
     int sa_prec;       // storage of SA read by AAb_Solver
+    int aab_form, aab_blocks;
     bool operator==(const Key& o) const {
       return A == o.A && lda == o.lda && b == o.b && x == o.x && rhs == o.rhs && sa_prec == o.sa_prec &&
+             aab_form == o.aab_form && aab_blocks == o.aab_blocks &&
              lam == o.lam &&
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
@@ -234,6 +236,8 @@ struct mihs_sketch_s {
   // (P_path × 16 × dp), G and X⁻ (16 × dp each), 16 control blocks and the
   // path's stop counter / flag.
   void* aab_grid_ws = nullptr;   // global scratch of the single-λ grid AAb kernel (first solve that needs it)
+  int aab_form = MIHS_AAB_AUTO;  // form of AAb_Solver in single-λ solves (mihs_sketch_set_aab)
+  int aab_grid_blocks = 0;
   float* path_partials = nullptr;
   float* path_aab_ws = nullptr;  // global scratch of the cooperative multi-λ AAb kernel
   float* path_g = nullptr;
@@ -274,11 +278,14 @@ void set_sa(AabLaunch& a, const mihs_sketch_s* sk) {
   }
 }
 
-// The grid form of AAb_Solver (SA too large for one cluster's shared memory)
-// needs global scratch: the handle's, allocated on first use; its barrier
-// word is zeroed on the solve's stream before every solve.
+// The grid form of AAb_Solver (SA too large for one cluster's shared memory,
+// or asked for by mihs_sketch_set_aab) needs global scratch: the handle's,
+// allocated on first use; its barrier word is zeroed on the solve's stream
+// before every solve.
 int use_grid_ws(mihs_sketch_s* sk, AabLaunch& a, cudaStream_t s) {
-  if (!aab_grid_wanted(a.m, a.d, a.sa_type)) return MIHS_OK;
+  a.aab_form = sk->aab_form;
+  a.grid_blocks = sk->aab_grid_blocks;
+  if (!aab_grid_wanted(a.m, a.d, a.sa_type, a.aab_form)) return MIHS_OK;
   if (sk->aab_grid_ws == nullptr) {
     const size_t bytes = aab_grid_ws_bytes(a.d);
     cudaError_t e = cudaMalloc(&sk->aab_grid_ws, bytes);
@@ -781,6 +788,17 @@ int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream) {
                             static_cast<cudaStream_t>(stream));
 }
 
+int mihs_sketch_set_aab(mihs_sketch_t sk, int form, int grid_blocks) {
+  set_error("");
+  MIHS_ARG(sk != nullptr, "mihs_sketch_set_aab: null handle");
+  MIHS_ARG(form == MIHS_AAB_AUTO || form == MIHS_AAB_CLUSTER || form == MIHS_AAB_GRID,
+           "mihs_sketch_set_aab: unknown form %d", form);
+  MIHS_ARG(grid_blocks >= 0, "mihs_sketch_set_aab: grid_blocks %d < 0", grid_blocks);
+  sk->aab_form = form;
+  sk->aab_grid_blocks = form == MIHS_AAB_GRID ? grid_blocks : 0;
+  return MIHS_OK;
+}
+
 int mihs_sketch_info(mihs_sketch_t sk, const float** SA, int64_t* m, int64_t* d, int64_t* n,
                      int* family) {
   MIHS_ARG(sk != nullptr, "mihs_sketch_info: null handle");
@@ -946,7 +964,9 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   rc = use_grid_ws(sk, a, s);
   if (rc) return rc;
   // Algorithm 1: up to max_outer momentum steps, each after a gradient.
-  const mihs_sketch_s::Key key = {A, lda, b, xv, lambda, alpha, beta, a.eps, a.max_passes, rhs, sk->sa_prec};
+  const mihs_sketch_s::Key key = {A,         lda,         b,          xv,           lambda,
+                                  alpha,     beta,        a.eps,      a.max_passes, rhs,
+                                  sk->sa_prec, sk->aab_form, sk->aab_grid_blocks};
   bool graph_ran = false;
   mihs_sketch_s::GraphSlot& gs = sk->slots[(refined ? 1 : 0) + (rhs != nullptr ? 2 : 0)];
   if (!timing_on() && !gs.failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {

@@ -109,6 +109,8 @@ struct AabLaunch {
   // Global scratch of the grid form (aab_grid_ws_bytes(d) bytes, barrier
   // word zeroed); NULL: the grid form is not used.
   void* grid_ws;
+  int aab_form;     // MIHS_AAB_AUTO / _CLUSTER / _GRID
+  int grid_blocks;  // grid form: blocks wanted (0: one per SM, at most m)
 };
 // Runs one cluster (aab.cu), or — when SA does not fit one cluster's shared
 // memory and a.grid_ws is given — one grid over the SMs (aab_grid.cu).
@@ -122,10 +124,11 @@ constexpr size_t kAabGridBarBytes = 256;
 size_t aab_grid_ws_bytes(int d);
 int launch_aab_grid(const AabLaunch& a, void* ws, cudaStream_t s);
 int aab_grid_device_error(int* code);
-// True when launch_aab would take the grid form given scratch: SA of m × d
-// does not fit in the shared memory of one cluster (MIHS_AAB_FORM=grid or
-// =cluster overrides).
-bool aab_grid_wanted(int m, int d, int sa_type);
+// True when launch_aab would take the grid form given scratch: `form` is
+// MIHS_AAB_GRID, or MIHS_AAB_AUTO and SA of m × d does not fit in the shared
+// memory of one cluster (for AUTO, MIHS_AAB_FORM=grid or =cluster in the
+// environment overrides).
+bool aab_grid_wanted(int m, int d, int sa_type, int form = 0);
 // λ-path mode with all λ in one cooperative grid that keeps SA in the
 // shared memory of all SMs (aab_path.cu); `ws` holds aab_path_ws_floats(dp)
 // floats.  Returns MIHS_ERR_UNSUPPORTED (nothing launched) when SA or d does

@@ -20,6 +20,8 @@ from . import _build
 GAUSSIAN, COUNTSKETCH, SRHT = 0, 1, 2
 SA_FP32, SA_BF16, SA_FP8 = 0, 1, 2
 SA_PRECISIONS = {"fp32": SA_FP32, "bf16": SA_BF16, "fp8": SA_FP8}
+AAB_AUTO, AAB_CLUSTER, AAB_GRID = 0, 1, 2
+AAB_FORMS = {"auto": AAB_AUTO, "cluster": AAB_CLUSTER, "grid": AAB_GRID}
 FAMILIES = {"gaussian": GAUSSIAN, "countsketch": COUNTSKETCH, "srht": SRHT}
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC, UNSUPPORTED = -1, -2, -3, -4, -5, -6
@@ -94,6 +96,7 @@ def lib() -> ctypes.CDLL:
                               ctypes.POINTER(_Info), _vp]),
         "mihs_backward_grads": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
         "mihs_sketch_set_precision": (_int, [_vp, _int, _vp]),
+        "mihs_sketch_set_aab": (_int, [_vp, _int, _int]),
         "mihs_dual_sketch": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, ctypes.POINTER(_vp)]),
         "mihs_dual_resketch": (_int, [_vp, _vp, _i64, _u64, _vp]),
         "mihs_dual_copy": (_int, [_vp, _vp, _i64, _vp]),
@@ -435,6 +438,12 @@ class Sketch:
         """Storage of SA inside AAb_Solver: 'fp32', 'bf16' or 'fp8' (mihs_sketch_set_precision)."""
         _check(lib().mihs_sketch_set_precision(self._h, _prec(prec), _stream(stream)))
 
+    def set_aab(self, form="auto", grid_blocks=0) -> None:
+        """Form of AAb_Solver in this handle's solves: 'auto', 'cluster' or 'grid'
+        with `grid_blocks` blocks (0: one per SM) (mihs_sketch_set_aab)."""
+        f = AAB_FORMS[form] if isinstance(form, str) else int(form)
+        _check(lib().mihs_sketch_set_aab(self._h, f, int(grid_blocks)))
+
     def sa(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.m, self.d, dtype=torch.float32, device=self.device)
         _check(lib().mihs_sketch_copy(self._h, out.data_ptr(), self.d, _stream(stream)))
@@ -594,14 +603,16 @@ _HANDLES: dict = {}
 
 
 def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: float, seed: int = 0,
-          out: torch.Tensor | None = None, **kw):
+          out: torch.Tensor | None = None, aab: str = "auto", **kw):
     """Sketch A then run Algorithm 1: the one-call form.
 
     A and b may live on the GPU or on the host (ideally pinned).  Host inputs
     are copied to the current CUDA device and x is copied back (into `out`
     when given), which makes this the end-to-end form of the solver.  One
     sketch handle per (device, n, d, m, family) is kept and reused, so
-    repeated calls allocate nothing new.  Returns (x, SolveInfo or None).
+    repeated calls allocate nothing new.  `aab` is the form of AAb_Solver,
+    "auto", "cluster", "grid" or "grid:<blocks>" (Sketch.set_aab).
+    Returns (x, SolveInfo or None).
     """
     host = not A.is_cuda
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -614,6 +625,8 @@ def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: floa
         sk = _HANDLES[key] = Sketch(A, family, m, seed)
     else:
         sk.resketch(A, seed)
+    form, _, blocks = aab.partition(":")
+    sk.set_aab(form, int(blocks or 0))
     x, info = sk.solve(A, b, lam, sd, **kw)
     if host:
         if out is None:

@@ -207,3 +207,40 @@ def test_cluster_global_quantised_sa(monkeypatch):
     amp, x64 = _amp(SAd, g.numpy().astype(np.float64), lam, k)
     delta = mihs.aab_solve_q(q, "bf16", sc, d, g.to(DEV), lam, eps_sub=0.0, max_inner=k)
     assert o.rel_error(_np(delta), x64) <= 20 * max(amp, 4 * U32 * math.sqrt(d))
+
+
+# ---------------- the form chosen per handle (mihs_sketch_set_aab)
+@pytest.mark.parametrize("shape", ["small", "scaled"])
+def test_handle_aab_form_reaches_the_solution(shape):
+    """Every form of AAb_Solver a handle can be set to, inside the device-side
+    loop of Algorithm 1: the cluster form, the grid form over all SMs, and
+    small grids whose requested block count is too few to hold SA in shared
+    memory (raised to the fewest that do).  Plain solves reach 1e-5 and
+    refined solves 1e-10 of the exact solution; a repeated solve on the same
+    form gives the same bytes, and switching forms rebuilds the solve graph."""
+    p = W.problem_small() if shape == "small" else W.problem_scaled(16384, 512, seed=41)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam, refine=3, extended=True)
+    forms = [("auto", 0), ("cluster", 0), ("grid", 0), ("grid", 1), ("grid", 3), ("grid", 24), ("auto", 0)]
+    with mihs.Sketch(A, "gaussian", p.m, seed=13) as sk:
+        for form, blocks in forms:
+            sk.set_aab(form, blocks)
+            x, info = sk.solve(A, b, p.lam, p.sd, tol=1e-6, max_outer=200)
+            x2, _ = sk.solve(A, b, p.lam, p.sd, tol=1e-6, max_outer=200)
+            xr, ir = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-13, max_outer=300)
+            assert info.converged and ir.converged, (form, blocks, info, ir)
+            assert o.rel_error(_np(x), xs) <= 1e-5, (form, blocks)
+            assert torch.equal(x, x2), (form, blocks)
+            assert o.rel_error(xr.cpu().numpy(), xs) <= 1e-10, (form, blocks)
+    assert mihs.device_status() == 0
+
+
+def test_handle_aab_form_arguments():
+    p = W.problem_small()
+    with mihs.Sketch(p.A.to(DEV), "gaussian", p.m, seed=13) as sk:
+        for bad in [(3, 0), (-1, 0), (2, -5)]:
+            with pytest.raises(mihs.MihsError):
+                sk.set_aab(*bad)
+        sk.set_aab("grid", 10_000)  # more blocks than SMs: one per SM
+        x, info = sk.solve(p.A.to(DEV), p.b.to(DEV), p.lam, p.sd, tol=1e-6, max_outer=200)
+    assert info.converged

@@ -58,4 +58,5 @@ def test_host_side_argument_checks(L):
     o = L.mihs_default_opts()
     assert L.mihs_solve(None, FAKE, 4, FAKE, 1.0, ctypes.byref(o), FAKE, None, None) == EINVAL
     assert b"lambda" in L.mihs_last_error() or b"null" in L.mihs_last_error()
+    assert L.mihs_sketch_set_aab(None, 0, 0) == EINVAL
     assert L.mihs_sketch_destroy(None) == 0
