@@ -263,10 +263,15 @@ int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream);
  * A small grid (about 24 blocks) is the better choice when several solves
  * share the GPU on concurrent streams: its blocks start on any free SMs,
  * while a 16-block cluster waits until one GPU processing cluster has 16
- * free SMs.  Results agree to fp32 rounding (the summation order differs).
- * λ-paths, batched and dual solves and the row-level mihs_aab_* calls keep
- * MIHS_AAB_AUTO.  Not to be called while a solve on the handle is in
- * flight.  Errors: INVALID_ARG (unknown form, grid_blocks < 0). */
+ * free SMs.  Grids of handles solving on concurrent streams never wait for
+ * one another while their block counts sum to at most the number of SMs
+ * (the other kernels' blocks end by themselves and free their SMs); beyond
+ * that, a grid barrier that stalls ends the solve with MIHS_ERR_TIMEOUT
+ * after 2 s rather than hanging.  Results agree to fp32 rounding (the
+ * summation order differs).  λ-paths, batched and dual solves and the
+ * row-level mihs_aab_* calls keep MIHS_AAB_AUTO.  Not to be called while a
+ * solve on the handle is in flight.
+ * Errors: INVALID_ARG (unknown form, grid_blocks < 0). */
 enum { MIHS_AAB_AUTO = 0, MIHS_AAB_CLUSTER = 1, MIHS_AAB_GRID = 2 };
 int mihs_sketch_set_aab(mihs_sketch_t sk, int form, int grid_blocks);
 
