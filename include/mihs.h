@@ -74,6 +74,21 @@ uint64_t mihs_launch_count(void);
  * the current device. */
 int mihs_device_status(int* code);
 
+/* Failure-detection self-test of those bounded waits: one kernel runs the
+ * library's own wait on a condition that nothing satisfies, with a limit of
+ * limit_ns (10⁶ … 10¹⁰ ns) instead of 2 s, and *status receives what the
+ * waiting kernel reported — MIHS_ERR_TIMEOUT when the wait ran out (the
+ * expected outcome), MIHS_OK if the condition was somehow met.
+ *   which 0: an mbarrier expecting one arrival that never comes (the wait of
+ *            the bulk-copy rings of the gradient passes, the AAb staging copy
+ *            and the tensor-core sketch pipeline);
+ *   which 1: a grid barrier of two blocks, one of which leaves without
+ *            arriving (the barrier of the grid forms of AAb_Solver).
+ * Nothing faults: the kernel returns, the device stays usable and the
+ * device error word of mihs_device_status is left alone.  Synchronises
+ * `stream`.  Errors: INVALID_ARG, CUDA, OOM. */
+int mihs_selftest_wait(int which, int64_t limit_ns, int* status, void* stream);
+
 /* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
  * the records and starts recording CUDA events on the launching stream around
  * every launch of: the gradient A-pass (timer 0), AAb_Solver (timer 1), a

@@ -8,7 +8,7 @@
 // reads the top bit before its first arrival (no flip can have happened yet,
 // since a flip needs this block's arrival) and toggles its expectation per
 // barrier; arrival is a release reduction (nothing to wait for), the wait an
-// acquire load.  A wait that runs out (2 s) returns false so that the kernel
+// acquire load.  A wait that runs out (2 s by default) returns false so that the kernel
 // can stop with an error instead of hanging; the word is then inconsistent
 // and must be zeroed before the next launch.
 #pragma once
@@ -39,8 +39,8 @@ __device__ __forceinline__ void grid_barrier_init(GridBarrier& gb, unsigned int*
 }
 
 // Every thread of every block calls it; returns false in every thread of the
-// block if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(GridBarrier& gb, int* s_ok) {
+// block if the wait ran out (after limit_ns).
+__device__ __forceinline__ bool grid_barrier(GridBarrier& gb, int* s_ok, uint64_t limit_ns = kWaitLimitNs) {
   __syncthreads();  // this block's writes precede thread 0's release
   if (threadIdx.x == 0) {
     const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
@@ -51,7 +51,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier& gb, int* s_ok) {
       const uint64_t t0 = global_timer_ns();
       for (uint32_t i = 1;; ++i) {
         if ((ld_acquire_gpu(gb.word) >> 31) == gb.expect) break;
-        if ((i & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+        if ((i & 63u) == 0 && global_timer_ns() - t0 > limit_ns) {
           ok = 0;
           break;
         }

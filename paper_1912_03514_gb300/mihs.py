@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
         "mihs_last_error": (ctypes.c_char_p, []),
         "mihs_launch_count": (_u64, []),
         "mihs_device_status": (_int, [ctypes.POINTER(_int)]),
+        "mihs_selftest_wait": (_int, [_int, _i64, ctypes.POINTER(_int), _vp]),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_sketch_gaussian_bf16": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
         "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
@@ -158,6 +159,16 @@ def device_status() -> int:
     c = _int()
     _check(lib().mihs_device_status(ctypes.byref(c)))
     return c.value
+
+
+def selftest_wait(which: int, limit_s: float = 0.05, stream=None) -> int:
+    """Runs one of the library's bounded waits on a condition nothing
+    satisfies (0: mbarrier, 1: grid barrier) with a limit of limit_s seconds;
+    returns the status its kernel reported (TIMEOUT expected)
+    (mihs_selftest_wait)."""
+    st = _int()
+    _check(lib().mihs_selftest_wait(int(which), int(limit_s * 1e9), ctypes.byref(st), _stream(stream)))
+    return st.value
 
 
 def launch_count() -> int:

@@ -59,4 +59,8 @@ def test_host_side_argument_checks(L):
     assert L.mihs_solve(None, FAKE, 4, FAKE, 1.0, ctypes.byref(o), FAKE, None, None) == EINVAL
     assert b"lambda" in L.mihs_last_error() or b"null" in L.mihs_last_error()
     assert L.mihs_sketch_set_aab(None, 0, 0) == EINVAL
+    st = ctypes.c_int()
+    assert L.mihs_selftest_wait(2, 50_000_000, ctypes.byref(st), None) == EINVAL  # which
+    assert L.mihs_selftest_wait(0, 10, ctypes.byref(st), None) == EINVAL  # limit below 1 ms
+    assert L.mihs_selftest_wait(0, 50_000_000, None, None) == EINVAL
     assert L.mihs_sketch_destroy(None) == 0
