@@ -89,6 +89,17 @@ int mihs_device_status(int* code);
  * `stream`.  Errors: INVALID_ARG, CUDA, OOM. */
 int mihs_selftest_wait(int which, int64_t limit_ns, int* status, void* stream);
 
+/* Host → device copy of `bytes` bytes for the end-to-end forms: when `src`
+ * is pinned host memory mapped into the device's address space (memory from
+ * cudaHostAlloc / cudaHostRegister under unified addressing) and both
+ * pointers are 16-byte aligned, the SMs load it directly over the CPU–GPU
+ * link (NVLink-C2C on Grace systems); otherwise, and for the last bytes not
+ * filling 16, cudaMemcpyAsync.  dst: DEVICE memory.  Asynchronous on
+ * `stream`; src must stay valid and unchanged until the copy has run.
+ * Errors: INVALID_ARG (null pointers, bytes < 0, dst not device memory),
+ * CUDA. */
+int mihs_copy_to_device(void* dst, const void* src, int64_t bytes, void* stream);
+
 /* Per-kernel timing (profiling aid, off by default).  mihs_timing(1) clears
  * the records and starts recording CUDA events on the launching stream around
  * every launch of: the gradient A-pass (timer 0), AAb_Solver (timer 1), a

@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
         "mihs_launch_count": (_u64, []),
         "mihs_device_status": (_int, [ctypes.POINTER(_int)]),
         "mihs_selftest_wait": (_int, [_int, _i64, ctypes.POINTER(_int), _vp]),
+        "mihs_copy_to_device": (_int, [_vp, _vp, _i64, _vp]),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_sketch_gaussian_bf16": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
         "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
@@ -169,6 +170,19 @@ def selftest_wait(which: int, limit_s: float = 0.05, stream=None) -> int:
     st = _int()
     _check(lib().mihs_selftest_wait(int(which), int(limit_s * 1e9), ctypes.byref(st), _stream(stream)))
     return st.value
+
+
+def copy_to_device(dst: torch.Tensor, src: torch.Tensor, stream=None) -> torch.Tensor:
+    """dst ← src for a contiguous host tensor src and a contiguous CUDA
+    tensor dst of the same dtype and size (mihs_copy_to_device: the SMs read
+    pinned host memory directly)."""
+    if src.is_cuda or not dst.is_cuda or src.dtype != dst.dtype or src.numel() != dst.numel():
+        raise ValueError("copy_to_device: host src and CUDA dst of one dtype and size")
+    if not (src.is_contiguous() and dst.is_contiguous()):
+        raise ValueError("copy_to_device: contiguous tensors only")
+    _check(lib().mihs_copy_to_device(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(),
+                                     _stream(stream)))
+    return dst
 
 
 def launch_count() -> int:
@@ -611,6 +625,22 @@ class Sketch:
 
 
 _HANDLES: dict = {}
+_IN_FLIGHT: list = []  # (event, host tensors) of host → device copies not known to have run
+
+
+def _to_device(t: torch.Tensor, dev) -> torch.Tensor:
+    """Host tensor → new CUDA tensor on the current stream by
+    mihs_copy_to_device (pinned memory is read by the SMs); the host tensor
+    is kept alive until the copy has run."""
+    t = t.contiguous()
+    out = torch.empty(t.shape, dtype=t.dtype, device=dev)
+    copy_to_device(out, t)
+    ev = torch.cuda.Event()
+    ev.record()
+    while _IN_FLIGHT and _IN_FLIGHT[0][0].query():
+        _IN_FLIGHT.pop(0)
+    _IN_FLIGHT.append((ev, t))
+    return out
 
 
 def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: float, seed: int = 0,
@@ -618,8 +648,9 @@ def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: floa
     """Sketch A then run Algorithm 1: the one-call form.
 
     A and b may live on the GPU or on the host (ideally pinned).  Host inputs
-    are copied to the current CUDA device and x is copied back (into `out`
-    when given), which makes this the end-to-end form of the solver.  One
+    are copied to the current CUDA device (mihs_copy_to_device) and x is
+    copied back (into `out` when given), which makes this the end-to-end
+    form of the solver.  One
     sketch handle per (device, n, d, m, family) is kept and reused, so
     repeated calls allocate nothing new.  `aab` is the form of AAb_Solver,
     "auto", "cluster", "grid" or "grid:<blocks>" (Sketch.set_aab).
@@ -628,8 +659,8 @@ def solve(A: torch.Tensor, b: torch.Tensor, lam: float, family, m: int, sd: floa
     host = not A.is_cuda
     dev = torch.device("cuda", torch.cuda.current_device())
     if host:
-        A = A.to(dev, non_blocking=True)
-        b = b.to(dev, non_blocking=True)
+        A = _to_device(A, dev)
+        b = _to_device(b, dev)
     key = (A.device.index, A.shape[0], A.shape[1], int(m), family_id(family))
     sk = _HANDLES.get(key)
     if sk is None:

@@ -63,4 +63,7 @@ def test_host_side_argument_checks(L):
     assert L.mihs_selftest_wait(2, 50_000_000, ctypes.byref(st), None) == EINVAL  # which
     assert L.mihs_selftest_wait(0, 10, ctypes.byref(st), None) == EINVAL  # limit below 1 ms
     assert L.mihs_selftest_wait(0, 50_000_000, None, None) == EINVAL
+    assert L.mihs_copy_to_device(FAKE, FAKE, -1, None) == EINVAL
+    assert L.mihs_copy_to_device(None, FAKE, 16, None) == EINVAL
+    assert L.mihs_copy_to_device(FAKE, FAKE, 0, None) == 0  # nothing to copy
     assert L.mihs_sketch_destroy(None) == 0
