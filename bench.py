@@ -243,7 +243,8 @@ def main():
     streams = {f: (main_stream if args.sequential else torch.cuda.Stream()) for f in families}
 
     def step(want_info=False):
-        # The solves of one step are independent problems: each runs on its
+        # The solves of one step (one per sketch family, same A and b) are
+        # independent of one another: each runs on its
         # own stream (so one solve's latency-bound inner solver overlaps
         # another's bandwidth-bound gradient pass), joined back to the main
         # stream at the end of the step.
