@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--aab", default="",
                     help="form of AAb_Solver in the step's solves: auto, cluster, grid or grid:<blocks> "
                          "(default: grid:24 when the solves share the GPU on concurrent streams, else auto)")
+    ap.add_argument("--aab-refined", default="auto",
+                    help="form of AAb_Solver in the refined leg's solves (same values as --aab)")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
                                             "aab-wide-bf16", "dual-grad",
                                             "gaussian", "gaussian-bf16", "countsketch", "srht"],
@@ -328,6 +330,11 @@ def main():
     if not args.no_refined:
         x64 = {f: torch.empty(d, dtype=torch.float64, device=dev) for f in families}
         kw_r = dict(tol=args.refined_tol, max_outer=args.max_outer, eps_sub=0.1)
+        # Measured on this step: the one-cluster inner solver is the faster
+        # form here (the grid form is the faster one in the plain step).
+        form_r, _, blocks_r = args.aab_refined.partition(":")
+        for sk in sketches.values():
+            sk.set_aab(form_r, int(blocks_r or 0))
 
         def step_refined(want_info=False):
             infos_r = {}
@@ -366,9 +373,11 @@ def main():
                    "status": {f: inf_r[f].status for f in families},
                    "outer_iters": {f: inf_r[f].outer_iters for f in families},
                    "switch_tol": 1e-7, "plain_steps": pl_n, "compensated_steps": dd_n,
-                   "correction_steps": co_n,
+                   "correction_steps": co_n, "aab": args.aab_refined,
                    "apass_dd_avg_us": round(dd_avg_s * 1e6, 2),
                    "apass_dd_frac_of_hbm": round(bytes_per_pass / dd_avg_s / 1e9 / peaks["hbm_gbs"], 4)}
+        for sk in sketches.values():
+            sk.set_aab(aab_form, int(aab_blocks or 0))
 
     # ---------------- accuracy vs the oracle's exact solution
     accuracy = None
