@@ -466,8 +466,11 @@ class Sketch:
     def set_aab(self, form="auto", grid_blocks=0) -> None:
         """Form of AAb_Solver in this handle's solves: 'auto', 'cluster' or 'grid'
         with `grid_blocks` blocks (0: one per SM) (mihs_sketch_set_aab)."""
-        f = AAB_FORMS[form] if isinstance(form, str) else int(form)
-        _check(lib().mihs_sketch_set_aab(self._h, f, int(grid_blocks)))
+        if isinstance(form, str):
+            if form not in AAB_FORMS:
+                raise ValueError(f"unknown AAb_Solver form {form!r}: one of {sorted(AAB_FORMS)}")
+            form = AAB_FORMS[form]
+        _check(lib().mihs_sketch_set_aab(self._h, int(form), int(grid_blocks)))
 
     def sa(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.m, self.d, dtype=torch.float32, device=self.device)

@@ -241,6 +241,8 @@ def test_handle_aab_form_arguments():
         for bad in [(3, 0), (-1, 0), (2, -5)]:
             with pytest.raises(mihs.MihsError):
                 sk.set_aab(*bad)
+        with pytest.raises(ValueError):
+            sk.set_aab("persistent")
         sk.set_aab("grid", 10_000)  # more blocks than SMs: one per SM
         x, info = sk.solve(p.A.to(DEV), p.b.to(DEV), p.lam, p.sd, tol=1e-6, max_outer=200)
     assert info.converged
