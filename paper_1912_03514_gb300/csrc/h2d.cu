@@ -57,7 +57,7 @@ int mihs_copy_to_device(void* dst, const void* src, int64_t bytes, void* stream)
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0;
   const void* dsrc = as.type == cudaMemoryTypeHost ? as.devicePointer : nullptr;
   if (dsrc == nullptr || !aligned || dsrc != src) {
-    MIHS_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyHostToDevice, s));
+    MIHS_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, s));
     return MIHS_OK;
   }
   const size_t n16 = (size_t)bytes / 16, tail = (size_t)bytes % 16;
@@ -71,6 +71,6 @@ int mihs_copy_to_device(void* dst, const void* src, int64_t bytes, void* stream)
   }
   if (tail > 0)
     MIHS_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + n16 * 16, static_cast<const char*>(src) + n16 * 16, tail,
-                                  cudaMemcpyHostToDevice, s));
+                                  cudaMemcpyDefault, s));
   return MIHS_OK;
 }
