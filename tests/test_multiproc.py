@@ -60,3 +60,23 @@ def test_reference_arm_under_torchrun_prints_one_line():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_single_process_rotates_pieces():
+    """One process, several steps: the first step times every piece of the
+    oracle's work and later steps re-time one piece each; the line carries
+    the contract's keys."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "6", "--warmup", "2",
+           "--rows", "4096", "--cols", "64"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    out = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["n_gpus"] == 1 and out["steps"] == 6 and out["value"] > 0
+    assert out["cpu_baseline"]["value"] == out["value"] and out["e2e"]["value"] == out["value"]
+    assert "re-timed" in out["cpu_baseline"]["sample"]
