@@ -703,7 +703,12 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, i
   MIHS_ARG(family >= MIHS_GAUSSIAN && family <= MIHS_SRHT, "mihs_sketch: unknown family %d", family);
   mihs_sketch_s* h = new (std::nothrow) mihs_sketch_s();
   if (!h) return MIHS_ERR_OOM;
-  MIHS_CUDA_TRY(cudaGetDevice(&h->device));
+  const cudaError_t ed = cudaGetDevice(&h->device);
+  if (ed != cudaSuccess) {
+    delete h;
+    set_error("mihs_sketch: cudaGetDevice: %s", cudaGetErrorString(ed));
+    return MIHS_ERR_CUDA;
+  }
   h->n = n;
   h->d = d;
   h->m = m;
@@ -734,8 +739,13 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, i
     return MIHS_ERR_CUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (h->dp != d) cudaMemsetAsync(h->SA, 0, sizeof(float) * (size_t)m * h->dp, s);
-  rc = mihs_sketch_apply(A, n, d, lda, family, m, seed, h->SA, h->dp, stream);
+  e = h->dp != d ? cudaMemsetAsync(h->SA, 0, sizeof(float) * (size_t)m * h->dp, s) : cudaSuccess;
+  if (e != cudaSuccess) {
+    set_error("mihs_sketch: cudaMemsetAsync: %s", cudaGetErrorString(e));
+    rc = MIHS_ERR_CUDA;
+  } else {
+    rc = mihs_sketch_apply(A, n, d, lda, family, m, seed, h->SA, h->dp, stream);
+  }
   if (rc) {
     cudaStreamSynchronize(s);
     cudaFreeHost(h->ctl_host);

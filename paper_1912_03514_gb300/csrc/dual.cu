@@ -315,7 +315,10 @@ int mihs_dual_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int fami
   MIHS_ARG(family >= MIHS_GAUSSIAN && family <= MIHS_SRHT, "mihs_dual_sketch: unknown family %d", family);
   MIHS_ARG(m >= 1 && m <= d, "mihs_dual_sketch: m=%lld must be in [1, d]", (long long)m);
   mihs_dual_t dk = new (std::nothrow) mihs_dual_s();
-  MIHS_ARG(dk != nullptr, "mihs_dual_sketch: out of host memory");
+  if (dk == nullptr) {
+    set_error("mihs_dual_sketch: out of host memory");
+    return MIHS_ERR_OOM;
+  }
   dk->n = n;
   dk->d = d;
   dk->m = m;
@@ -340,6 +343,7 @@ int mihs_dual_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int fami
   dk->ctl = reinterpret_cast<SolveCtl*>(dk->upart + (size_t)atnu_num_splits(n) * (size_t)round_up(d, 4));
   rc = dual_sketch_into(dk, A, lda, seed, static_cast<cudaStream_t>(stream));
   if (rc) {
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));  // nothing of this handle still in flight
     cudaFree(dk->SAt);
     cudaFreeHost(dk->ctl_host);
     delete dk;
