@@ -67,3 +67,25 @@ def test_host_side_argument_checks(L):
     assert L.mihs_copy_to_device(None, FAKE, 16, None) == EINVAL
     assert L.mihs_copy_to_device(FAKE, FAKE, 0, None) == 0  # nothing to copy
     assert L.mihs_sketch_destroy(None) == 0
+
+
+def test_binding_rejects_host_tensors_before_any_cuda_call():
+    """The binding marshals arguments only: it refuses what the C ABI could
+    not take (host tensors, wrong dtype or layout) before calling into the
+    library, so no CPU path can stand in for the kernels."""
+    import torch
+    A = torch.zeros(16, 4)
+    v4, v16 = torch.zeros(4), torch.zeros(16)
+    with pytest.raises(ValueError):
+        mihs.gradient(A, v16, v4, 1.0)
+    with pytest.raises(ValueError):
+        mihs._mat(torch.zeros(16, 4, dtype=torch.float64), "A")
+    with pytest.raises(ValueError):
+        mihs._mat(torch.zeros(4, 16).t(), "A")  # column stride 4
+    with pytest.raises(ValueError):
+        mihs._vec(torch.zeros(8)[::2], 4, "x")  # not contiguous
+    with pytest.raises(ValueError):
+        mihs.copy_to_device(torch.zeros(4), torch.zeros(4))  # destination on the host
+    with pytest.raises(ValueError):
+        mihs._prec("fp4")
+    assert mihs.family_id("srht") == 2 and mihs.AAB_FORMS["grid"] == 2
