@@ -139,6 +139,20 @@ def test_sketch_rows_equal_full_product(family):
     assert np.allclose(SA, S @ A.astype(np.float64), rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("family", [o.GAUSSIAN, o.COUNTSKETCH, o.SRHT])
+def test_sketch_rows_in_any_order_are_rows_of_the_full_sketch(family):
+    """The row-sampled form (used for sampled checks at full size) returns
+    exactly the requested rows of S·A, in the order asked, repeats allowed."""
+    n, d, m = 257, 5, 16
+    A = W.randn((n, d), 8).numpy().astype(np.float64)
+    S = {o.GAUSSIAN: o.gaussian_sketch_matrix, o.COUNTSKETCH: o.countsketch_matrix,
+         o.SRHT: o.srht_matrix}[family](m, n, 31)
+    rows = [11, 0, 15, 3, 11]
+    got = o.sketch_rows(family, rows, A, m, 31)
+    want = np.stack([sum(S[i, j] * A[j] for j in range(n)) for i in rows])  # brute force
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
 # ----------------------------------------------------------- ridge solution
 def _small(n=400, d=40, lam=1e-2, seed=0):
     rng = np.random.default_rng(seed)
@@ -651,3 +665,38 @@ def test_exact_solve_dd_refinement_on_ill_conditioned_problem():
     gh, gl = o.gradient_dd(A, b, x, p.lam)
     atb = np.abs(A.astype(np.float64)).T @ np.abs(b.astype(np.float64))
     assert np.linalg.norm(gh + gl) <= 1e-13 * np.linalg.norm(atb)
+
+
+def test_gradient_blocked_is_blocking_independent_and_brute_force():
+    rng = np.random.default_rng(5)
+    n, d, lam = 37, 6, 0.3
+    A, b, x = rng.standard_normal((n, d)), rng.standard_normal(n), rng.standard_normal(d)
+    want = np.zeros(d)
+    for i in range(n):  # row by row: a_i (b_i − a_i·x)
+        want += A[i] * (b[i] - sum(A[i, j] * x[j] for j in range(d)))
+    want -= lam * x
+    for blk in (1, 5, 36, 37, 1000):
+        assert np.allclose(o.gradient_blocked(A, b, x, lam, row_block=blk), want, rtol=1e-13, atol=1e-13)
+
+
+def test_characteristic_roots_vieta_and_underdamped_modulus():
+    """Roots of the heavy-ball characteristic polynomial (proof of Theorem 1):
+    their sum is the trace 1 + β − αμ and their product β; when they are
+    complex both have modulus √β."""
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        beta = rng.uniform(0.01, 0.9)
+        alpha = rng.uniform(0.05, 2.0)
+        mu = rng.uniform(0.0, 3.0, size=7)
+        r1, r2 = o.characteristic_roots(mu, alpha, beta)
+        assert np.allclose(r1 + r2, 1 + beta - alpha * mu, atol=1e-12)
+        assert np.allclose(r1 * r2, beta, atol=1e-12)
+        cplx = (1 + beta - alpha * mu) ** 2 < 4 * beta
+        assert np.allclose(np.abs(r1[cplx]), math.sqrt(beta)) and np.allclose(np.abs(r2[cplx]), math.sqrt(beta))
+
+
+def test_corollary3_iteration_count_closed_form():
+    """With β = 1/4 the rate √β is 1/2, so η = 2⁻¹⁰ needs exactly 10 steps;
+    with β = 1/100, η = 1e-6 needs 6."""
+    assert math.isclose(o.corollary3_iters(2.0 ** -10, 0.25), 10.0, rel_tol=1e-12)
+    assert math.isclose(o.corollary3_iters(1e-6, 0.01), 6.0, rel_tol=1e-12)
