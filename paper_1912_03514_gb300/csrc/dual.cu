@@ -7,6 +7,7 @@
 //   g = b − A·u − λν   one pass over A, one block per row
 //   Δν = AAb_Solver(SAᵀ, g, λ, ε_sub), ν⁺ = ν + αΔν + β(ν − ν⁻)   (aab.cu)
 // all inside a CUDA graph WHILE loop that the AAb kernel ends.
+#include <cfloat>
 #include <cmath>
 #include <cstdlib>
 
@@ -388,7 +389,7 @@ int mihs_gradient_dual(const float* A, int64_t n, int64_t d, int64_t lda, const 
   int rc = check_dual(A, n, d, lda, "mihs_gradient_dual");
   if (rc) return rc;
   MIHS_ARG(b != nullptr && nu != nullptr && g != nullptr, "mihs_gradient_dual: null vector");
-  MIHS_ARG(lambda >= 0.0 && std::isfinite(lambda), "mihs_gradient_dual: lambda must be finite, >= 0");
+  MIHS_ARG(lambda >= 0.0 && lambda <= (double)FLT_MAX, "mihs_gradient_dual: lambda must be in [0, FLT_MAX]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScratch us;
   rc = us.alloc(sizeof(float) * (size_t)round_up(d, 4) * (size_t)(1 + atnu_num_splits(n)), s);
@@ -420,7 +421,7 @@ int mihs_solve_dual(mihs_dual_t dk, const float* A, int64_t lda, const float* b,
   if (rc) return rc;
   MIHS_ARG(b != nullptr && nu != nullptr, "mihs_solve_dual: null b or nu");
   MIHS_ARG(x == nullptr || (reinterpret_cast<uintptr_t>(x) & 15u) == 0, "mihs_solve_dual: x must be 16-byte aligned");
-  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve_dual: lambda must be > 0");
+  MIHS_ARG(lambda > 0.0 && lambda <= (double)FLT_MAX, "mihs_solve_dual: lambda must be in (0, FLT_MAX]");
   MIHS_ARG(opts->sd < (double)dk->m, "mihs_solve_dual: sd=%g must be < m", opts->sd);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve_dual: bad max_outer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

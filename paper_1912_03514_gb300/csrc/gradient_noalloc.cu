@@ -3,17 +3,23 @@
 // a cudaMallocAsync buffer.
 //
 // This is for callers that cannot allocate device memory at the time they
-// call: code running while a CUDA graph is being captured with a strict
-// capture mode, code inside an allocator callback or a custom memory pool
-// that must not recurse into the allocator, or processes whose memory budget
-// is fixed up front.  The array (1.25 MiB) is reserved on every GPU where the
-// library's device code is loaded and is held until the process exits.
+// call: code inside an allocator callback or a custom memory pool that must
+// not recurse into the allocator, code that may only allocate at start-up,
+// or processes whose memory budget is fixed up front.  The array (1.25 MiB)
+// is reserved on every GPU where the library's device code is loaded and is
+// held until the process exits.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents.  Nothing in it needs to start at zero: each launch writes every
 // partial row it later reads.  Calls whose kernels overlap on the GPU (two
 // streams, or two host threads) race on the array and must be serialised by
 // the caller.
+//
+// The device address of the array is looked up on the first call on each
+// device and cached for the life of the process; a cudaDeviceReset of that
+// device invalidates it (the module, and with it the array, is reloaded at a
+// new address), so the entry point must not be called after such a reset.
+#include <cfloat>
 #include <mutex>
 
 #include "internal.h"
@@ -70,7 +76,8 @@ extern "C" int mihs_gradient_noalloc(const float* A, int64_t n, int64_t d, int64
            (long long)lda);
   MIHS_ARG((reinterpret_cast<uintptr_t>(A) & 15u) == 0,
            "mihs_gradient_noalloc: matrix pointer must be 16-byte aligned");
-  MIHS_ARG(lambda >= 0.0 && lambda < 1e300, "mihs_gradient_noalloc: lambda must be finite, >= 0");
+  MIHS_ARG(lambda >= 0.0 && lambda <= (double)FLT_MAX,
+           "mihs_gradient_noalloc: lambda must be in [0, FLT_MAX] (the kernel computes in fp32)");
   const int P = apass_num_partials(n, d);
   const size_t need = (size_t)P * (size_t)apass_dpad(d);
   if (need > kNoAllocFloats) {
