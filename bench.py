@@ -34,11 +34,15 @@ sys.path.insert(0, ROOT)
 FAMILIES = ["gaussian", "countsketch", "srht"]
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one A-pass
-# launch from the ncu capture summarised in
-# profiles/apass_partial_kernel_ridge-65536x1024.md (65536×1024).  Traffic is
-# one read of A plus O(d) vectors, so it scales with the rows processed.
-APASS_NCU = {"n": 65536, "d": 1024, "bytes": 268.741120e6 + 3.547392e6}
+# launch, taken by ncu on the 65536×1024 case of this kernel.  Traffic is one
+# read of A plus O(d) vectors, so it scales with the rows processed.
+APASS_NCU = {"n": 65536, "d": 1024, "bytes": 268737536 + 3024896}
 METRIC = "ridge solves/s at stated rel. error"
+# The oracle's sample, identical in the cpu_baseline leg and the reference
+# arm: rows of each dense SA timed (scaled to m) and M-IHS iterations per
+# solve (the steps at the rate √(sd/m) = 1/2 from residual 1 to 2e-8).
+ORACLE_ROWS = 2
+ORACLE_ITERS = 25
 
 
 def parse():
@@ -59,6 +63,8 @@ def parse():
     ap.add_argument("--refined-tol", type=float, default=1e-10)
     ap.add_argument("--no-backward", action="store_true", help="skip the differentiable-solve leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched λ-path leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 leg")
+    ap.add_argument("--oracle-sample", default="", help=argparse.SUPPRESS)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (2^21 x 2048)")
     ap.add_argument("--no-dual", action="store_true", help="skip the Dual M-IHS leg (2048 x 2^18)")
     ap.add_argument("--mixed-tol", type=float, default=3e-14,
@@ -214,19 +220,70 @@ class OracleTimer:
         for part in self.parts:
             self.measure(part)
 
-    def value(self, iters_per_family):
+    def value(self, iters=None):
+        iters = ORACLE_ITERS if iters is None else iters
         t_it = self.t[("iter", None)]
-        total = sum(self.t[("sketch", f)] + (iters_per_family[f] + 1) * t_it for f in self.families)
+        total = sum(self.t[("sketch", f)] + (iters + 1) * t_it for f in self.families)
         return len(self.families) / total
 
-    def sample(self, iters_per_family):
+    def sample(self, iters=None):
+        iters = ORACLE_ITERS if iters is None else iters
         return (f"oracle (numpy fp64) on the full {self.p.n}x{self.p.d} problem: {self.rows} rows of SA per "
-                f"dense family scaled to m={self.p.m}, full CountSketch SA, one M-IHS iteration scaled to "
-                f"the iteration counts {iters_per_family}")
+                f"dense family scaled to m={self.p.m}, the full CountSketch SA, one M-IHS iteration "
+                f"scaled to {iters} iterations + 1 gradient per family")
 
     def detail(self):
         return {"sketch_s": {f: round(self.t[("sketch", f)], 3) for f in self.families},
                 "iter_s": round(self.t[("iter", None)], 4)}
+
+
+def oracle_one_core(A_host, b_host, families):
+    """The same oracle sample in a fresh interpreter whose BLAS and OpenMP
+    pools have one thread, pinned to one core; A and b reach it through a
+    temporary .npy file."""
+    import tempfile
+
+    import numpy as np
+    tmpdir = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    with tempfile.TemporaryDirectory(dir=tmpdir) as td:
+        np.save(os.path.join(td, "A.npy"), A_host.numpy())
+        np.save(os.path.join(td, "b.npy"), b_host.numpy())
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = "1"
+        env.pop("RANK", None)
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", td, "--families", ",".join(families)]
+        try:
+            r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+            line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
+            return json.loads(line)
+        except Exception as e:  # reported, not fatal: the all-core number stands
+            return {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+
+
+def run_oracle_sample(args):
+    """Child of oracle_one_core: the oracle sample on one core."""
+    import numpy as np
+    import torch
+
+    from paper_1912_03514_gb300 import workloads as W
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+    A = torch.from_numpy(np.load(os.path.join(args.oracle_sample, "A.npy")))
+    b = torch.from_numpy(np.load(os.path.join(args.oracle_sample, "b.npy")))
+    n, d = A.shape
+    sigma = W.profile_polynomial(d, 1.0)
+    lam = 1e-4
+    sd = W.nominal_sd(sigma, lam)
+    p = W.RidgeProblem(name=f"ridge-{n}x{d}", A=A, b=b, lam=lam, sd=sd, m=min(n, W.round_up(4 * sd, 4)),
+                       x0=None, sigma=sigma, meta={})
+    families = [f for f in args.families.split(",") if f]
+    ot = OracleTimer(A, b, p, families, rows=ORACLE_ROWS)
+    ot.measure_all()
+    print(json.dumps({"value": round(ot.value(), 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                      "sample": "the same sample on one core", "detail": ot.detail()}), flush=True)
 
 
 # ------------------------------------------------------------------ main
@@ -238,6 +295,8 @@ def main():
 
     from paper_1912_03514_gb300 import workloads as W
 
+    if args.oracle_sample:
+        return run_oracle_sample(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank, families)
     if args.profile_op:
@@ -454,6 +513,11 @@ def main():
                "h2d_bytes_per_step": len(families) * 4 * (n * d + n),
                "d2h_bytes_per_step": len(families) * 4 * d}
 
+    # ---------------- the 4096 × 256 problem (L2-resident, latency-bound)
+    small = None
+    if not args.no_small:
+        small = run_small(args, dev, ws)
+
     # ---------------- differentiable solve: forward + adjoint backward
     differentiable = None
     if not args.no_backward:
@@ -477,11 +541,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         if A_host is None:
             A_host, b_host = A.cpu(), b.cpu()
-        iters = {f: infos[f].outer_iters for f in families}
-        ot = OracleTimer(A_host, b_host, p, families, rows=3)  # ≈ 20 s of host work at 262144×1024
+        ot = OracleTimer(A_host, b_host, p, families, rows=ORACLE_ROWS)
         ot.measure_all()
-        cpu = {"value": round(ot.value(iters), 5), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": ot.sample(iters), "detail": ot.detail()}
+        cpu = {"value": round(ot.value(), 5), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": ot.sample(), "detail": ot.detail(),
+               "one_core": oracle_one_core(A_host, b_host, families)}
 
     if rank == 0:
         out = {
@@ -503,6 +567,7 @@ def main():
                           "aab_launches": aab_n, "sketch_total": round(sk_ms, 4)},
             "roofline": roofline,
             "accuracy": accuracy,
+            "small": small,
             "refined": refined,
             "differentiable": differentiable,
             "batched": batched,
@@ -517,6 +582,62 @@ def main():
         print(json.dumps(out), flush=True)
     for sk in sketches.values():
         sk.close()
+
+
+def run_small(args, dev, ws):
+    """The 4096 × 256 problem (σ_i = 10^(−4(i−1)/255), λ with sd = 64, 30 dB
+    SNR, Gaussian sketch m = 256, stop at relative residual 1e-6): A is 4 MB
+    and stays in L2, so this measures latency, not bandwidth.  One step =
+    sketch + solve on one stream; the oracle's whole CPU solve (sketch +
+    Algorithm 1 in fp64) is timed beside it on the host cores."""
+    import torch
+
+    from oracle import mihs_oracle as o
+    from paper_1912_03514_gb300 import mihs
+    from paper_1912_03514_gb300 import workloads as W
+    p = W.problem_small(device=str(dev))
+    tol = 1e-6
+    x = torch.empty(p.d, device=dev)
+    sk = mihs.Sketch(p.A, "gaussian", p.m, seed=3)
+
+    def step(want_info=False):
+        sk.resketch(p.A, 3)
+        return sk.solve(p.A, p.b, p.lam, p.sd, tol=tol, max_outer=200, x=x, want_info=want_info)[1]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    info = step(want_info=True)
+    nsteps = 200
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nsteps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / nsteps, ws)
+    sk.close()
+    out = {"workload": f"{p.name}: 4096×256, σ_i = 10^(−4(i−1)/255), λ = {p.lam:.6g} (sd = 64), 30 dB SNR, "
+                       f"Gaussian m = {p.m}, stop at relative residual {tol:g}; A = 4 MB (L2-resident)",
+           "value": round(ws / (ms / 1e3), 2), "unit": "solves/s", "ms_per_step": round(ms, 4), "steps": nsteps,
+           "status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
+           "rel_resid": float(f"{info.rel_resid:.3e}")}
+    if int(os.environ.get("RANK", "0")) == 0:
+        An, bn = p.A.cpu().numpy(), p.b.cpu().numpy()
+        xs = o.exact_solve(An, bn, p.lam)
+        out["rel_err_vs_oracle"] = float(f"{o.rel_error(x.cpu().double().numpy(), xs):.3e}")
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 3 or time.perf_counter() - t0 < 3.0:
+            xo, io = o.mihs_solve(An, bn, p.lam, o.GAUSSIAN, p.m, p.sd, 3, N=200, tol=tol)
+            reps += 1
+        t_o = (time.perf_counter() - t0) / reps
+        out["oracle_cpu"] = {"value": round(1.0 / t_o, 3), "unit": "solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": f"the whole solve (sketch + Algorithm 1, fp64), "
+                                                         f"{reps} runs", "outer_iters": io["outer"],
+                             "rel_err_vs_exact": float(f"{o.rel_error(xo, xs):.3e}")}
+    return out
 
 
 def run_differentiable(args, dev, ws, peaks, peak_src):
@@ -584,27 +705,37 @@ def run_batched(args, dev, ws, peaks, peak_src):
     """64 matrices (n log-uniform in [8192, 262144], d in {64 … 1024}, σ_i =
     10^(−r(i−1)/(d−1)), r ~ U[2, 6]) × one 16-value λ path in [1e-6, 1e-1]:
     per matrix a Gaussian sketch with m = 4·sd(λ_min), then the whole path
-    (mihs_solve_batched: one fused gradient pass per step for all 16 λ).
-    One step = sketch + path solve for all 64 matrices; value = (matrix, λ)
-    solves per second."""
+    (mihs_solve_batched: one fused gradient pass per step for all 16 λ) to a
+    relative residual of 1e-7, then compensated refinement
+    (mihs_refine_batched) of the λ whose κ(AᵀA + λI) = (σ₁² + λ)/λ exceeds
+    5e3 (σ₁ = 1 by construction), where no fp32 residual certifies a relative
+    error of 1e-5.  One step = sketch + path solve + refinement for all 64
+    matrices; value = (matrix, λ) solves per second.  The error of every
+    (matrix, λ) against the oracle's x*(λ) is measured on a sample of
+    matrices, for this form and for one plain solve per (matrix, λ)."""
     import numpy as np
     import torch
 
     from paper_1912_03514_gb300 import mihs
     from paper_1912_03514_gb300 import workloads as W
     probs, lams, sds = W.batch_lambda_path(device=str(dev), device_rng=True)
-    tol = 1e-6
+    tol, tol_ref, kappa_fp32 = 1e-7, 1e-10, 5e3
+    tols = [tol_ref if (1.0 + lam) / lam > kappa_fp32 else 0.0 for lam in lams]
     handles = [mihs.Sketch(q.A, "gaussian", q.m, seed=100 + i) for i, q in enumerate(probs)]
     Xs = [torch.empty(len(lams), q.d, device=dev) for q in probs]
     entries = [(sk, q.A, q.b, X) for sk, q, X in zip(handles, probs, Xs)]
 
-    def step(want_info=False):
-        for i, (sk, q) in enumerate(zip(handles, probs)):
+    def step(want_info=False, sub=None):
+        ent = entries if sub is None else entries[:sub]
+        for i, (sk, q) in enumerate(zip(handles[:len(ent)], probs)):
             sk.resketch(q.A, 100 + i)
-        return mihs.solve_batched(entries, lams, sds=sds, tol=tol, max_outer=100, want_info=want_info)
+        sd_ = sds[:len(ent)]
+        inf = mihs.solve_batched(ent, lams, sds=sd_, tol=tol, max_outer=200, want_info=want_info)
+        rinf = mihs.refine_batched(ent, lams, tols, sds=sd_, max_outer=200, want_info=want_info)
+        return inf, rinf
 
     step()
-    infos = step(want_info=True)
+    infos, rinfos = step(want_info=True)
     steps = 2
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -619,7 +750,7 @@ def run_batched(args, dev, ws, peaks, peak_src):
     mihs.timing(True)
     for i, (sk, q) in enumerate(zip(handles, probs)):
         sk.resketch(q.A, 100 + i)
-    mihs.solve_batched(entries, lams, sds=sds, tol=tol, max_outer=100, want_info=False)
+    mihs.solve_batched(entries, lams, sds=sds, tol=tol, max_outer=200, want_info=False)
     sk_ms, _ = mihs.timing_read(mihs.TIMER_SKETCH)
     pa_ms, pa_n = mihs.timing_read(mihs.TIMER_APASS_PATH)
     aab_ms, aab_n = mihs.timing_read(mihs.TIMER_AAB)
@@ -629,34 +760,51 @@ def run_batched(args, dev, ws, peaks, peak_src):
     flops = sum(64.0 * q.n * q.d * k for q, k in zip(probs, steps_per))
     nom_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: 152 SMs × 128 FP32 lanes × FMA × 2.07 GHz
     flat = [i for row in infos for i in row]
+    rflat = [i for row in rinfos for i in row if i is not None]
     out = {"value": round(ws * len(probs) * len(lams) / (ms / 1e3), 2), "unit": "(matrix, λ) solves/s",
            "ms_per_step": round(ms, 3), "steps": steps,
            "workload": f"{len(probs)} matrices (n log-uniform 8192–262144, d in 64–1024, "
                        f"{sum(4 * q.n * q.d for q in probs) / 1e9:.2f} GB of A), 16 λ in [1e-6, 1e-1], "
-                       f"Gaussian m = 4·sd(λ_min), tol {tol:g}",
+                       f"Gaussian m = 4·sd(λ_min); fp32 path to residual {tol:g}, then the "
+                       f"{sum(t > 0 for t in tols)} λ with κ(H) > {kappa_fp32:g} refined to {tol_ref:g}",
            "converged": sum(i.status == 0 for i in flat), "solves": len(flat),
-           "max_rel_resid": float(f"{max(i.rel_resid for i in flat):.3e}"),
+           "refined_converged": sum(i.status == 0 for i in rflat), "refined_solves": len(rflat),
+           "max_rel_resid_fp32": float(f"{max(i.rel_resid for i in flat):.3e}"),
+           "max_rel_resid_refined": float(f"{max(i.rel_resid for i in rflat):.3e}") if rflat else None,
+           "refined_outer_iters_mean": round(sum(i.outer_iters for i in rflat) / max(len(rflat), 1), 1),
+           "refined_inner_passes_mean": round(sum(i.inner_iters_total for i in rflat) / max(len(rflat), 1), 1),
            "outer_iters_max": max(i.outer_iters for i in flat),
-           "kernel_ms": {"sketch": round(sk_ms, 3), "path_apass": round(pa_ms, 3), "path_apass_launches": pa_n,
-                         "aab": round(aab_ms, 3), "aab_launches": aab_n},
+           "kernel_ms_path_solve": {"sketch": round(sk_ms, 3), "path_apass": round(pa_ms, 3),
+                                    "path_apass_launches": pa_n, "aab": round(aab_ms, 3), "aab_launches": aab_n},
            "path_apass_roofline": {"bound": "alu", "achieved": round(flops / (pa_ms / 1e3) / 1e12, 2),
                                    "peak": round(nom_fp32, 1), "unit": "TFLOP/s",
                                    "frac": round(flops / (pa_ms / 1e3) / 1e12 / nom_fp32, 4),
                                    "peak_source": "derived: 152 SMs × 128 FP32 FMA/clk × 2 flops × 2.07 GHz"}}
-    # the plain single-λ form on the same problems: one mihs_solve per
-    # (matrix, λ) on the matrix's handle (same sketch, same tolerance), over
-    # the first 8 matrices
+    # the plain single-λ form on the same problems at the same accuracy: one
+    # mihs_solve (residual 1e-7) or, for the refined λ, one
+    # mihs_solve_refined (residual 1e-10) per (matrix, λ) on the matrix's
+    # handle, over the first 8 matrices
     nsub = min(8, len(probs))
     x1 = [torch.empty(q.d, device=dev) for q in probs[:nsub]]
+    x64 = [torch.empty(q.d, dtype=torch.float64, device=dev) for q in probs[:nsub]]
+    Xp = [torch.empty(len(lams), q.d, device=dev) for q in probs[:nsub]]
 
-    def plain_pass():
+    def plain_pass(keep=False):
         for i in range(nsub):
             q, sk = probs[i], handles[i]
             sk.resketch(q.A, 100 + i)
             for l, lam in enumerate(lams):
-                sk.solve(q.A, q.b, lam, sds[i][l], tol=tol, max_outer=100, x=x1[i], want_info=False)
+                if tols[l] > 0:
+                    sk.solve_refined(q.A, q.b, lam, sds[i][l], tol=tol_ref, max_outer=200, x=x64[i],
+                                     want_info=False)
+                    if keep:
+                        Xp[i][l].copy_(x64[i])
+                else:
+                    sk.solve(q.A, q.b, lam, sds[i][l], tol=tol, max_outer=200, x=x1[i], want_info=False)
+                    if keep:
+                        Xp[i][l].copy_(x1[i])
 
-    plain_pass()
+    plain_pass(keep=True)
     torch.cuda.synchronize()
     e0.record(stream)
     plain_pass()
@@ -664,24 +812,41 @@ def run_batched(args, dev, ws, peaks, peak_src):
     torch.cuda.synchronize()
     ms_p = max_over_ranks(e0.elapsed_time(e1), ws)
 
-    def batched_sub():
-        for i in range(nsub):
-            handles[i].resketch(probs[i].A, 100 + i)
-        mihs.solve_batched(entries[:nsub], lams, sds=sds[:nsub], tol=tol, max_outer=100, want_info=False)
-
-    batched_sub()
+    step(sub=nsub)
     torch.cuda.synchronize()
     e0.record(stream)
-    batched_sub()
+    step(sub=nsub)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_b = max_over_ranks(e0.elapsed_time(e1), ws)
     out["plain_single_lambda"] = {
         "value": round(ws * nsub * len(lams) / (ms_p / 1e3), 2), "unit": "(matrix, λ) solves/s",
         "batched_same_sample": round(ws * nsub * len(lams) / (ms_b / 1e3), 2),
-        "sample": f"the first {nsub} matrices × {len(lams)} λ: one mihs_solve per (matrix, λ) on the "
-                  f"matrix's handle (same sketch, tol {tol:g}, graph rebuilt per λ), against "
-                  f"mihs_solve_batched on the same {nsub} matrices"}
+        "sample": f"the first {nsub} matrices × {len(lams)} λ: one mihs_solve (residual {tol:g}) or "
+                  f"mihs_solve_refined (residual {tol_ref:g}, the same λ as the batched form refines) per "
+                  f"(matrix, λ) on the matrix's handle (same sketch), against mihs_solve_batched + "
+                  f"mihs_refine_batched on the same {nsub} matrices"}
+    # error against the oracle on the sample, both forms (rank 0)
+    if int(os.environ.get("RANK", "0")) == 0:
+        from oracle import mihs_oracle as o
+        t0 = time.time()
+        err_b, err_p, per_lam = [], [], [0.0] * len(lams)
+        for i in range(nsub):
+            q = probs[i]
+            XS = o.ridge_path(q.A.cpu().numpy(), q.b.cpu().numpy(), lams)
+            Xb, Xq = Xs[i].cpu().double().numpy(), Xp[i].cpu().double().numpy()
+            for l in range(len(lams)):
+                eb, ep = o.rel_error(Xb[l], XS[l]), o.rel_error(Xq[l], XS[l])
+                err_b.append(eb)
+                err_p.append(ep)
+                per_lam[l] = max(per_lam[l], eb)
+        out["accuracy_vs_oracle"] = {
+            "sample": f"the first {nsub} matrices ({', '.join(q.name for q in probs[:nsub])}) × all "
+                      f"{len(lams)} λ; oracle: fp64 Gram, Cholesky per λ, two fp64 refinement steps",
+            "max_rel_err_batched": float(f"{max(err_b):.3e}"),
+            "max_rel_err_plain_single_lambda": float(f"{max(err_p):.3e}"),
+            "max_rel_err_batched_by_lambda": {f"{lam:.3g}": float(f"{e:.2e}") for lam, e in zip(lams, per_lam)},
+            "oracle_s": round(time.time() - t0, 1)}
     for sk in handles:
         sk.close()
     return out
@@ -950,12 +1115,11 @@ def run_reference(args, ws, rank, families):
         return
     from paper_1912_03514_gb300 import workloads as W
     p = W.problem_bandwidth(device="cpu", seed=1001, n=args.n, d=args.d)
-    iters = {f: 25 for f in families}  # fixed iteration budget per solve for the estimate
     # The first step times every piece of the oracle's work; each later step
     # re-times one piece in turn (a second or a few at 262144×1024), so that
     # the whole run stays within minutes for any --steps.  A step's value
     # combines the latest time of every piece.
-    ot = OracleTimer(p.A, p.b, p, families, rows=1)
+    ot = OracleTimer(p.A, p.b, p, families, rows=ORACLE_ROWS)
     vals = []
     for k in range(args.warmup + args.steps):
         if k == 0:
@@ -963,9 +1127,9 @@ def run_reference(args, ws, rank, families):
         else:
             ot.measure(ot.parts[(k - 1) % len(ot.parts)])
         if k >= args.warmup:
-            vals.append(ot.value(iters))
+            vals.append(ot.value())
     v = statistics.median(vals)
-    sample = ot.sample(iters) + "; one piece re-timed per step after the first"
+    sample = ot.sample() + "; one piece re-timed per step after the first"
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "solves/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

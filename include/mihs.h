@@ -141,7 +141,7 @@ int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda,
                               void* stream);
 
 /* Gradient step of Algorithm 1: g = Aᵀ(b − Ax) − λx, reading A once.
- *   b (n), x (d) inputs; g (d) output.  λ ≥ 0.
+ *   b (n), x (d) inputs; g (d) output.  0 ≤ λ ≤ FLT_MAX (fp32 arithmetic).
  * Allocates stream-ordered scratch for the split-K partial sums (one d-vector
  * per thread block) and frees it on the same stream.  The reduction order is
  * fixed, so repeated calls give bit-identical g.
@@ -153,14 +153,17 @@ int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda,
 /* The gradient of mihs_gradient (same arguments, same result) without any
  * allocation.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc/cudaMallocAsync at the moment they
- * need a gradient — e.g. code running inside a stream capture whose mode
- * forbids allocation, inside an allocator or memory-pool callback that must
- * not re-enter the allocator, or under a device-memory budget fixed up front.
+ * need a gradient — e.g. code inside an allocator or memory-pool callback
+ * that must not re-enter the allocator, code that may allocate only at
+ * start-up, or a process whose device-memory budget is fixed up front.
  * Its split-K scratch is a fixed 1.25 MiB array in the library's own device
  * memory, reserved on every GPU that loads the library and held until exit.
  *   - The first call on each device looks the array's device address up
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture.  A cudaDeviceReset of the
+ *     device invalidates the cached address: do not call this entry point
+ *     on a device after resetting it.
+ *   - λ must lie in [0, FLT_MAX] (the kernels compute in fp32).
  *   - Limit: (partial rows = min(#SMs, ⌈n/rows per block step⌉)) × d rounded
  *     up to 4 must fit in 160 × 2048 floats; larger cases return
  *     MIHS_ERR_UNSUPPORTED with a message (only GPUs with more than 160 SMs
@@ -338,7 +341,7 @@ mihs_opts mihs_default_opts(void);
  * rebuilt when A, lda, b, x, λ, α, β, eps_sub or max_inner change.  Setting
  * the environment variable MIHS_NO_GRAPH makes the host drive the steps.
  *   A     n×d (same n, d as the handle), leading dimension lda.
- *   b     n-vector.  λ > 0.
+ *   b     n-vector.  0 < λ ≤ FLT_MAX (AAb_Solver computes in fp32).
  *   x     d-vector: x¹ on entry if opts->warm_start, the solution on exit.
  *   info  optional HOST struct; when non-NULL the call synchronises the
  *         stream and fills it, and the return value reflects convergence
@@ -444,6 +447,37 @@ typedef struct {
 int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda,
                        const double* lambdas, const double* sds,
                        const mihs_opts* opts, mihs_info* infos, void* stream);
+
+/* Compensated refinement of chosen λ of a batch of paths, as
+ * mihs_solve_refined (Algorithm 1 with the fp64 iterate and the double-float
+ * gradient; the sketch only preconditions, Section 3.1, so the handle's SA
+ * serves unchanged).  Where κ(AᵀA + λI) is large, the fp32 fixed point of
+ * mihs_solve_batched lies far from x*(λ): at κ ≈ 1e6 a relative residual of
+ * 1e-6 leaves a relative error near 1e-3, and no fp32 residual certifies
+ * 1e-5.  For every problem i and every l with tols[l] > 0 this runs one
+ * refined solve of (A_i, b_i, λ_l) warm-started from row l of X_i (fp32, e.g.
+ * the result of mihs_solve_batched), stopping at the relative residual
+ * tols[l] (or after opts->max_outer steps), and writes the fp32 rounding of
+ * the fp64 solution back into that row.  Rows with tols[l] ≤ 0 are left as
+ * they are.
+ *   probs, nlambda, lambdas, sds  as mihs_solve_batched (sds NULL: each λ's
+ *            sd estimated by Algorithm 4, which synchronises).
+ *   tols     HOST array of nlambda target residuals (≤ 0: skip that λ).
+ *   opts     eps_sub, max_inner, max_outer; tol, sd and warm_start are
+ *            taken from tols, sds and the warm start above.
+ *   infos    HOST nprob × nlambda or NULL: the entries of refined λ are
+ *            overwritten (status, steps and residual of the refined solve),
+ *            the others left unchanged; non-NULL makes the call synchronise.
+ * Problems run concurrently on the internal streams of mihs_solve_batched
+ * (those whose refined solves use the grid form of AAb_Solver one after
+ * another on one of them), forked from and joined back into `stream`; the λ
+ * of one problem run in order on its handle.  The first refinement on a
+ * handle allocates its refinement workspace and one fp64 d-vector
+ * (cudaMalloc).  Returns the worst status.  Errors: INVALID_ARG, CUDA, OOM,
+ * TIMEOUT, NUMERIC. */
+int mihs_refine_batched(int nprob, const mihs_problem* probs, int nlambda,
+                        const double* lambdas, const double* sds, const double* tols,
+                        const mihs_opts* opts, mihs_info* infos, void* stream);
 
 /* ------------------------------------------------------------------------
  * Differentiation of the solution x(A, b, λ) = (AᵀA + λI)⁻¹Aᵀb.  The paper

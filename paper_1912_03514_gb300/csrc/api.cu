@@ -1,4 +1,5 @@
 // C ABI of libmihs: argument checks, handles and the host side of Algorithm 1.
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -146,6 +147,11 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restric
   if (j < d) b[j] = (float)a[j];
 }
 
+__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, int d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d) b[j] = (double)a[j];
+}
+
 // ‖g‖ for the warm-start reference norm ‖Aᵀb‖ (one block, fixed order).
 __global__ void ctl_set_gnorm0_kernel(SolveCtl* ctl, const float* g, int d) {
   __shared__ float red[32];
@@ -260,6 +266,11 @@ struct mihs_sketch_s {
   cudaGraphExec_t path_exec = nullptr;
   PathKey path_key = {};
   bool path_graph_failed = false;
+  // Refinement of chosen λ of a path (mihs_refine_batched): the fp64 iterate
+  // of the refined solve and pinned host copies of its control blocks.
+  double* ref_x64 = nullptr;
+  SolveCtl* ref_ctl_host = nullptr;
+  int ref_ctl_cap = 0;
 };
 
 namespace {
@@ -564,7 +575,7 @@ int mihs_gradient(const float* A, int64_t n, int64_t d, int64_t lda, const float
   int rc = check_matrix(A, n, d, lda, "mihs_gradient");
   if (rc) return rc;
   MIHS_ARG(b != nullptr && x != nullptr && g != nullptr, "mihs_gradient: null vector");
-  MIHS_ARG(lambda >= 0.0 && std::isfinite(lambda), "mihs_gradient: lambda must be finite, >= 0");
+  MIHS_ARG(lambda >= 0.0 && lambda <= (double)FLT_MAX, "mihs_gradient: lambda must be in [0, FLT_MAX]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = apass_num_partials(n, d);
   StreamScratch scratch;
@@ -582,7 +593,7 @@ static int aab_common(const float* SA, int64_t m, int64_t d, int64_t ldsa, const
   MIHS_ARG(m >= 1 && m < (1LL << 31), "%s: m=%lld out of range", who, (long long)m);
   MIHS_ARG(d >= 1 && d <= kMaxD, "%s: d=%lld outside [1, %d]", who, (long long)d, kMaxD);
   MIHS_ARG(ldsa >= d, "%s: ldsa must be >= d", who);
-  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "%s: lambda must be > 0", who);
+  MIHS_ARG(lambda > 0.0 && lambda <= (double)FLT_MAX, "%s: lambda must be in (0, FLT_MAX]", who);
   MIHS_ARG(eps_sub >= 0.0, "%s: eps_sub must be >= 0", who);
   (void)max_inner;
   return MIHS_OK;
@@ -611,7 +622,7 @@ int mihs_aab_solve_q(const void* SAq, int sa_prec, const float* scales, int64_t 
   MIHS_ARG(sa_prec == MIHS_SA_BF16 || sa_prec == MIHS_SA_FP8E4M3, "mihs_aab_solve_q: precision must be bf16 or fp8");
   MIHS_ARG(SAq != nullptr && g != nullptr && delta != nullptr, "mihs_aab_solve_q: null argument");
   MIHS_ARG(m >= 1 && d >= 1 && d <= kMaxD && ldq >= d && ldq % 16 == 0, "mihs_aab_solve_q: bad shape");
-  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda) && eps_sub >= 0.0, "mihs_aab_solve_q: bad lambda or eps");
+  MIHS_ARG(lambda > 0.0 && lambda <= (double)FLT_MAX && eps_sub >= 0.0, "mihs_aab_solve_q: bad lambda or eps");
   AabLaunch a = {};
   a.SA = SAq;
   a.sa_type = sa_prec;
@@ -858,6 +869,8 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk->path_partials) cudaFree(sk->path_partials);
   if (sk->SAq) cudaFree(sk->SAq);
   if (sk->path_ctl_host) cudaFreeHost(sk->path_ctl_host);
+  if (sk->ref_x64) cudaFree(sk->ref_x64);
+  if (sk->ref_ctl_host) cudaFreeHost(sk->ref_ctl_host);
   cudaFreeHost(sk->ctl_host);
   cudaFree(sk->SA);
   delete sk;
@@ -873,7 +886,7 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_solve");
   if (rc) return rc;
   MIHS_ARG((b != nullptr || rhs != nullptr) && xv != nullptr, "mihs_solve: null b or x");
-  MIHS_ARG(lambda > 0.0 && std::isfinite(lambda), "mihs_solve: lambda must be > 0");
+  MIHS_ARG(lambda > 0.0 && lambda <= (double)FLT_MAX, "mihs_solve: lambda must be in (0, FLT_MAX]");
   MIHS_ARG(opts->sd < (double)sk->m, "mihs_solve: sd=%g must be < m=%lld", opts->sd, (long long)sk->m);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
   MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve: eps_sub must be >= 0");
@@ -1096,7 +1109,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve_path: bad max_outer");
   MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve_path: eps_sub must be >= 0");
   for (int l = 0; l < nlambda; ++l) {
-    MIHS_ARG(lambdas[l] > 0.0 && std::isfinite(lambdas[l]), "mihs_solve_path: lambda[%d] must be > 0", l);
+    MIHS_ARG(lambdas[l] > 0.0 && lambdas[l] <= (double)FLT_MAX, "mihs_solve_path: lambda[%d] must be in (0, FLT_MAX]", l);
     if (sds != nullptr)
       MIHS_ARG(sds[l] < (double)sk->m, "mihs_solve_path: sd[%d]=%g must be < m", l, sds[l]);
   }
@@ -1259,7 +1272,7 @@ int mihs_gradient_path(const float* A, int64_t n, int64_t d, int64_t lda, const 
   PathScalars ps = {};
   ps.nl = nl;
   for (int l = 0; l < nl; ++l) {
-    MIHS_ARG(lambdas[l] >= 0.0 && std::isfinite(lambdas[l]), "mihs_gradient_path: lambda[%d] must be >= 0", l);
+    MIHS_ARG(lambdas[l] >= 0.0 && lambdas[l] <= (double)FLT_MAX, "mihs_gradient_path: lambda[%d] must be in [0, FLT_MAX]", l);
     ps.lam[l] = (float)lambdas[l];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1284,6 +1297,39 @@ int mihs_solve_path(mihs_sketch_t sk, const float* A, int64_t lda, const float* 
   return path_infos(sk, nlambda, infos);
 }
 
+// Internal streams of the batched entry points (per device, created on first
+// use): kBatchStreams streams and kBatchStreams + 1 events, the last one the
+// fork event.
+constexpr int kBatchStreams = 4;
+static int batch_streams(std::vector<cudaStream_t>& st, std::vector<cudaEvent_t>& ev) {
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> pool;  // per device
+  static std::vector<std::vector<cudaEvent_t>> evs;
+  int dev = 0;
+  MIHS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)pool.size() <= dev) {
+    pool.resize(dev + 1);
+    evs.resize(dev + 1);
+  }
+  if (pool[dev].empty()) {
+    for (int k = 0; k < kBatchStreams; ++k) {
+      cudaStream_t t;
+      cudaEvent_t e;
+      MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+      MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      pool[dev].push_back(t);
+      evs[dev].push_back(e);
+    }
+    cudaEvent_t e;
+    MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    evs[dev].push_back(e);  // the fork event
+  }
+  st = pool[dev];
+  ev = evs[dev];
+  return MIHS_OK;
+}
+
 int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const double* lambdas,
                        const double* sds, const mihs_opts* opts, mihs_info* infos, void* stream) {
   set_error("");
@@ -1297,37 +1343,12 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
   // grid form all go to stream 0 (two such grids must never wait for each
   // other's blocks, so they never run concurrently); the others are spread
   // over streams 1 … 3 (or all four when no problem uses the grid form).
-  constexpr int kStreams = 4;
+  constexpr int kStreams = kBatchStreams;
   const int nstreams = kStreams;
-  static std::mutex mu;
-  static std::vector<std::vector<cudaStream_t>> pool;  // per device
-  static std::vector<std::vector<cudaEvent_t>> evs;
-  int dev = 0;
-  MIHS_CUDA_TRY(cudaGetDevice(&dev));
   std::vector<cudaStream_t> st;
   std::vector<cudaEvent_t> ev;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if ((int)pool.size() <= dev) {
-      pool.resize(dev + 1);
-      evs.resize(dev + 1);
-    }
-    if (pool[dev].empty()) {
-      for (int k = 0; k < kStreams; ++k) {
-        cudaStream_t t;
-        cudaEvent_t e;
-        MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
-        MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        pool[dev].push_back(t);
-        evs[dev].push_back(e);
-      }
-      cudaEvent_t e;
-      MIHS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      evs[dev].push_back(e);  // the fork event
-    }
-    st = pool[dev];
-    ev = evs[dev];
-  }
+  int rc0 = batch_streams(st, ev);
+  if (rc0) return rc0;
   MIHS_CUDA_TRY(cudaEventRecord(ev[kStreams], s));
   for (int k = 0; k < nstreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kStreams], 0));
   int rc = MIHS_OK;
@@ -1361,6 +1382,111 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
     const int w = path_infos(probs[i].sk, nlambda, infos + (size_t)i * nlambda);
     if (w < 0) worst = w;
     else if (worst == MIHS_OK && w != MIHS_OK) worst = w;
+  }
+  return worst;
+}
+
+int mihs_refine_batched(int nprob, const mihs_problem* probs, int nlambda, const double* lambdas,
+                        const double* sds, const double* tols, const mihs_opts* opts, mihs_info* infos,
+                        void* stream) {
+  set_error("");
+  MIHS_ARG(nprob >= 0 && (nprob == 0 || probs != nullptr), "mihs_refine_batched: bad problem array");
+  MIHS_ARG(nlambda >= 1 && lambdas != nullptr && tols != nullptr && opts != nullptr,
+           "mihs_refine_batched: null lambdas, tols or opts, or nlambda < 1");
+  for (int i = 0; i < nprob; ++i) {
+    MIHS_ARG(probs[i].sk != nullptr && probs[i].X != nullptr && probs[i].b != nullptr,
+             "mihs_refine_batched: problem %d: null handle, b or X", i);
+    MIHS_ARG(probs[i].ldx >= probs[i].sk->d, "mihs_refine_batched: problem %d: ldx < d", i);
+    for (int j = 0; j < i; ++j)
+      MIHS_ARG(probs[i].sk != probs[j].sk, "mihs_refine_batched: problems %d and %d share a handle", j, i);
+  }
+  for (int l = 0; l < nlambda; ++l) {
+    if (!(tols[l] > 0.0)) continue;
+    MIHS_ARG(lambdas[l] > 0.0 && lambdas[l] <= (double)FLT_MAX,
+             "mihs_refine_batched: lambda[%d] must be in (0, FLT_MAX]", l);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Workspace first (cudaMalloc synchronises the device): the fp64 iterate
+  // and, with infos, pinned copies of the control blocks.
+  for (int i = 0; i < nprob; ++i) {
+    mihs_sketch_s* sk = probs[i].sk;
+    if (sk->ref_x64 == nullptr) {
+      cudaError_t e = cudaMalloc(&sk->ref_x64, sizeof(double) * (size_t)sk->dp);
+      if (e != cudaSuccess) {
+        sk->ref_x64 = nullptr;
+        set_error("mihs_refine_batched: cudaMalloc: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MIHS_ERR_OOM : MIHS_ERR_CUDA;
+      }
+    }
+    if (infos != nullptr && sk->ref_ctl_cap < nlambda) {
+      if (sk->ref_ctl_host) cudaFreeHost(sk->ref_ctl_host);
+      sk->ref_ctl_host = nullptr;
+      sk->ref_ctl_cap = 0;
+      MIHS_CUDA_TRY(cudaMallocHost(&sk->ref_ctl_host, sizeof(SolveCtl) * (size_t)nlambda));
+      sk->ref_ctl_cap = nlambda;
+    }
+  }
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> ev;
+  int rc = batch_streams(st, ev);
+  if (rc) return rc;
+  // Refined solves whose AAb_Solver takes the cooperative grid form run one
+  // after another on stream 0 (two such grids must never wait for each
+  // other's blocks); the others are spread over streams 1 … 3.
+  auto uses_grid = [](const mihs_sketch_s* sk) {
+    const int sa_type = sk->sa_prec != MIHS_SA_FP32 && sk->SAq != nullptr ? sk->sa_prec : MIHS_SA_FP32;
+    return aab_grid_wanted((int)sk->m, (int)sk->d, sa_type, sk->aab_form);
+  };
+  MIHS_CUDA_TRY(cudaEventRecord(ev[kBatchStreams], s));
+  for (int k = 0; k < kBatchStreams; ++k) MIHS_CUDA_TRY(cudaStreamWaitEvent(st[k], ev[kBatchStreams], 0));
+  int next = 0;
+  for (int i = 0; i < nprob && rc == MIHS_OK; ++i) {
+    const mihs_problem& q = probs[i];
+    mihs_sketch_s* sk = q.sk;
+    const int k = uses_grid(sk) ? 0 : 1 + (next++) % (kBatchStreams - 1);
+    const unsigned blocks = (unsigned)((sk->d + 255) / 256);
+    for (int l = 0; l < nlambda && rc == MIHS_OK; ++l) {
+      if (!(tols[l] > 0.0)) continue;
+      float* xrow = q.X + (size_t)l * q.ldx;
+      f32_to_f64_kernel<<<blocks, 256, 0, st[k]>>>(xrow, sk->ref_x64, (int)sk->d);
+      MIHS_CHECK_LAUNCH();
+      count_launch();
+      mihs_opts o = *opts;
+      o.tol = tols[l];
+      o.sd = sds != nullptr ? sds[(size_t)i * nlambda + l] : 0.0;
+      o.warm_start = 1;
+      rc = solve_impl(sk, q.A, q.lda, q.b, lambdas[l], &o, sk->ref_x64, true, nullptr, st[k]);
+      if (rc) {
+        set_error("mihs_refine_batched: problem %d, lambda[%d]: %s", i, l, mihs_last_error());
+        break;
+      }
+      f64_to_f32_kernel<<<blocks, 256, 0, st[k]>>>(sk->ref_x64, xrow, (int)sk->d);
+      MIHS_CHECK_LAUNCH();
+      count_launch();
+      if (infos != nullptr)
+        MIHS_CUDA_TRY(cudaMemcpyAsync(sk->ref_ctl_host + l, sk->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost,
+                                      st[k]));
+    }
+  }
+  for (int k = 0; k < kBatchStreams; ++k) {
+    MIHS_CUDA_TRY(cudaEventRecord(ev[k], st[k]));
+    MIHS_CUDA_TRY(cudaStreamWaitEvent(s, ev[k], 0));
+  }
+  if (rc || infos == nullptr) return rc;
+  MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+  int worst = MIHS_OK;
+  for (int i = 0; i < nprob; ++i) {
+    for (int l = 0; l < nlambda; ++l) {
+      if (!(tols[l] > 0.0)) continue;
+      const SolveCtl& c = probs[i].sk->ref_ctl_host[l];
+      mihs_info& inf = infos[(size_t)i * nlambda + l];
+      inf.outer_iters = c.outer;
+      inf.inner_iters_total = c.inner_total;
+      inf.rel_resid = c.gnorm0 > 0.f ? (double)c.gnorm / (double)c.gnorm0 : 0.0;
+      inf.status = c.done ? c.status : MIHS_NOT_CONVERGED;
+      if (inf.status < 0) worst = inf.status;
+      else if (worst == MIHS_OK && inf.status != MIHS_OK) worst = inf.status;
+    }
   }
   return worst;
 }

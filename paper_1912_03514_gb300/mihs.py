@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
         "mihs_solve_path": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp, ctypes.POINTER(_Opts), _vp, _i64, _vp,
                                    _vp]),
         "mihs_solve_batched": (_int, [_int, _vp, _int, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp]),
+        "mihs_refine_batched": (_int, [_int, _vp, _int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp]),
         "mihs_backward_refined": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp,
                                          _i64, _vp, _vp, ctypes.POINTER(_Info), _vp]),
         "mihs_backward": (_int, [_vp, _vp, _i64, _vp, _dbl, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _i64,
@@ -425,6 +426,37 @@ def solve_batched(problems, lambdas, sds=None, tol: float = 1e-6, max_outer: int
         return None
     flat = _infos(infos, len(problems) * nl)
     return [flat[i * nl:(i + 1) * nl] for i in range(len(problems))]
+
+
+def refine_batched(problems, lambdas, tols, sds=None, max_outer: int = 200, eps_sub: float = 0.1,
+                   max_inner: int = 0, want_info: bool = True, stream=None):
+    """mihs_refine_batched: compensated refinement of the λ with tols[l] > 0
+    of every problem's X (warm-started from X, result written back in fp32).
+    `problems` as for solve_batched.  Returns per problem a list over λ of
+    SolveInfo (None for λ not refined), or None."""
+    lam, nl = _dbl_array(lambdas)
+    tl, nt = _dbl_array(tols)
+    if nt != nl:
+        raise ValueError("tols must have one entry per λ")
+    arr = (_Problem * len(problems))()
+    for i, (sk, A, b, X) in enumerate(problems):
+        pa, n, d, lda = _mat(A, "A")
+        if (n, d) != (sk.n, sk.d) or tuple(X.shape) != (nl, d) or X.stride(1) != 1 or X.dtype != torch.float32:
+            raise ValueError(f"problem {i}: shapes do not match")
+        arr[i] = _Problem(sk._h.value, pa, lda, _vec(b, n, "b"), X.data_ptr(), X.stride(0))
+    sd_arr = None
+    if sds is not None:
+        flat = [float(v) for row in sds for v in row]
+        sd_arr = (ctypes.c_double * len(flat))(*flat)
+    o = _path_opts(0.0, max_outer, eps_sub, max_inner, True)
+    infos = (_Info * (len(problems) * nl))() if want_info else None
+    rc = lib().mihs_refine_batched(len(problems), arr, nl, lam, sd_arr, tl, ctypes.byref(o), infos,
+                                   _stream(stream))
+    _check(rc, allow_not_converged=True)
+    if not want_info:
+        return None
+    flat = _infos(infos, len(problems) * nl)
+    return [[flat[i * nl + l] if tols[l] > 0 else None for l in range(nl)] for i in range(len(problems))]
 
 
 @dataclass

@@ -122,24 +122,34 @@ def test_aab_fixed_passes_matches_oracle(m, d, lam, k):
 @pytest.mark.parametrize("m,d,lam", [(588, 1024, 1e-4), (256, 256, 0.0103), (1500, 300, 1e-3)])
 @pytest.mark.parametrize("eps", [0.5, 0.1, 1e-3])
 def test_aab_forcing_term(m, d, lam, eps):
-    """Stops on the forcing term like the oracle: the pass count matches the
-    oracle's fp32 run up to the few extra passes that rounding (loss of
-    orthogonality of the Lanczos vectors) can cost, and the returned Δ meets
-    the forcing term — or, when eps lies below what fp32 can certify for this
-    conditioning, the residual the oracle's fp32 run reaches."""
+    """Stops on the forcing term like the oracle's fp32 run.  Algorithm 5 does
+    not reorthogonalise its Lanczos vectors, so in fp32 they lose
+    orthogonality and the recursion's residual estimate t (Section 3.6) drifts
+    from the fp64 one: the pass at which t < eps can move by a few passes
+    (the oracle's fp32 and fp64 runs differ by 3 at m = d = 256, eps = 1e-3),
+    and the kernel's summation order differs from the oracle's fp32 order by
+    about as much again.  So the pass count must lie within ±2 of the
+    oracle's fp32 run.  The returned Δ must meet the forcing term wherever
+    fp32 can certify it, i.e. eps above κ(H)·u₃₂ (the rounding of H·Δ relative
+    to ‖g‖); below that (m = 588, d = 1024, λ = 1e-4: κ·u₃₂ ≈ 3e-3 > 1e-3) the
+    oracle's own fp32 run stalls above eps and the kernel must come within
+    10× of the residual it reaches."""
     SA, g = _sa_case(m, d, 7 * m + d)
     SAn, gn = SA.numpy().astype(np.float64), g.numpy().astype(np.float64)
     x32, k32 = o.aab_solve(SAn.astype(np.float32), gn.astype(np.float32), lam, eps, dtype=np.float32)
-    _, k64 = o.aab_solve(SAn, gn, lam, eps)
     passes = torch.zeros(1, dtype=torch.int32, device=DEV)
     delta = mihs.aab_solve(SA.to(DEV), g.to(DEV), lam, eps_sub=eps, passes=passes)
     kg = int(passes.item())
-    slack = max(2, int(0.1 * max(k32, k64)))
-    assert min(k32, k64) - slack <= kg <= max(k32, k64) + slack, (kg, k32, k64)
+    assert abs(kg - k32) <= 2, (kg, k32)
     H = SAn.T @ SAn + lam * np.eye(d)
+    ev = np.linalg.eigvalsh(H)
+    certifiable = eps > (ev[-1] / ev[0]) * U32
     res = np.linalg.norm(H @ _np(delta) - gn) / np.linalg.norm(gn)
     res32 = np.linalg.norm(H @ x32.astype(np.float64) - gn) / np.linalg.norm(gn)
-    assert res < max(eps * (1 + 1e-3), 10 * res32), (res, res32)
+    if certifiable:
+        assert res < eps * (1 + 1e-3), (res, eps)
+    else:
+        assert res32 > eps and res < 10 * res32, (res, res32)
 
 
 def test_aab_zero_rhs():
