@@ -102,90 +102,20 @@ __device__ __forceinline__ float strided_sum(const float* col, size_t stride, in
   return t;
 }
 
-// One sweep over the block's rows: w_i = SA_i·v − θp_i, ρ² share, and
-// U = SAᵀw accumulated in registers (lane ℓ: columns 4ℓ + 128c).
+// One sweep over the block's rows (SA in shared memory): the row dots
+// w_i = SA_i·v − θp_i with their ρ² share, then the column sums U = SA_bᵀw
+// with each thread owning its columns, stored straight to this block's row
+// of the global partials; the warps' ρ² shares are summed in order.
 template <int CH, typename TS>
-__device__ __forceinline__ float grid_sweep(const TS* sa, int pitch, int nr, int d, int dp, const float* v,
-                                            const float* p, float theta, float* w, const float* scales,
-                                            int sld, int r0, float4 (&ur)[CH]) {
+__device__ __forceinline__ void grid_sweep_store(const TS* sa, int pitch, int nr, int d, int dp, const float* v,
+                                                 const float* p, float theta, float* w, const float* scales,
+                                                 int sld, int r0, float* red, float* tmp, float* out,
+                                                 float* out_rho2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 vr[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int j = 4 * lane + 128 * c;
-    vr[c] = j < dp ? *reinterpret_cast<const float4*>(v + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-    ur[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float rsq = 0.f;
-  for (int i = warp; i < nr; i += kWarps) {
-    const TS* row = sa + (size_t)i * pitch;
-    const float* srow = scales != nullptr ? scales + (size_t)((r0 + i) >> 7) * sld : nullptr;
-    float4 a[CH];
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // four short chains (latency)
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int j = 4 * lane + 128 * c;
-      a[c] = j < dp ? load_sa4<TS>(row, j, d, true, srow != nullptr ? srow[c] : 1.f)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
-      s0 = fmaf(a[c].x, vr[c].x, s0);
-      s1 = fmaf(a[c].y, vr[c].y, s1);
-      s2 = fmaf(a[c].z, vr[c].z, s2);
-      s3 = fmaf(a[c].w, vr[c].w, s3);
-    }
-    const float wi = warp_sum((s0 + s1) + (s2 + s3)) - theta * p[i];
-    rsq = fmaf(wi, wi, rsq);
-    if (lane == 0) w[i] = wi;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      ur[c].x = fmaf(a[c].x, wi, ur[c].x);
-      ur[c].y = fmaf(a[c].y, wi, ur[c].y);
-      ur[c].z = fmaf(a[c].z, wi, ur[c].z);
-      ur[c].w = fmaf(a[c].w, wi, ur[c].w);
-    }
-  }
-  return rsq;
-}
-
-// Sums the eight warps' U registers in a fixed tree (through `buf`, 4·dp
-// floats) and writes the block's U to `out` (global); the warps' ρ² shares
-// are summed in order into out_rho2.
-template <int CH>
-__device__ __forceinline__ void block_reduce_store(float4 (&ur)[CH], float rsq, float* buf, int dp, float* red,
-                                                   float* out, float* out_rho2) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float rsq = row_dots<CH, TS>(sa, pitch, nr, v, p, theta, w, dp, scales, sld, r0);
   if (lane == 0) red[warp] = rsq;
-#pragma unroll
-  for (int half = kWarps / 2; half >= 1; half >>= 1) {
-    if (warp >= half && warp < 2 * half) {
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int j = 4 * lane + 128 * c;
-        if (j < dp) *reinterpret_cast<float4*>(buf + (size_t)(warp - half) * dp + j) = ur[c];
-      }
-    }
-    __syncthreads();
-    if (warp < half) {
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int j = 4 * lane + 128 * c;
-        if (j < dp) {
-          const float4 o = *reinterpret_cast<const float4*>(buf + (size_t)warp * dp + j);
-          ur[c].x += o.x;
-          ur[c].y += o.y;
-          ur[c].z += o.z;
-          ur[c].w += o.w;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int j = 4 * lane + 128 * c;
-      if (j < dp) __stcg(reinterpret_cast<float4*>(out + j), ur[c]);
-    }
-  }
+  __syncthreads();  // w complete
+  col_sums<CH, TS>(sa, pitch, nr, dp, w, scales, sld, r0, tmp, out);
   if (threadIdx.x == 0) {
     float t = 0.f;
 #pragma unroll
@@ -203,9 +133,10 @@ __host__ __device__ inline GridSmem grid_smem_layout(int dp, int Rpad, int cs, i
   GridSmem L;
   L.v = 0;
   L.buf = L.v + sizeof(float) * (size_t)dp;
-  // 4·dp floats for the tree reduction of U, at least kThreads for the
-  // column-slice reduction (nsub subsets × cs columns ≤ kThreads)
-  L.p = L.buf + sizeof(float) * (size_t)(4 * dp > kThreads ? 4 * dp : kThreads);
+  // max(4·dp, 4·kThreads) floats: the row groups' partial column sums of a
+  // sweep (ng·dp ≤ 4·kThreads when ng > 1) and the column-slice reduction
+  // (nsub subsets × cs columns ≤ kThreads)
+  L.p = L.buf + sizeof(float) * (size_t)(dp > kThreads ? 4 * dp : 4 * kThreads);
   L.w = L.p + sizeof(float) * (size_t)Rpad;
   L.dvs = L.w + sizeof(float) * (size_t)Rpad;
   L.xss = L.dvs + sizeof(float) * (size_t)cs;
@@ -312,6 +243,18 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
   // is still landing when the block exits).
   if (!mbar_wait(stage_bar, 0u, kWaitLimitNs)) alive = false;
   __syncthreads();
+  if constexpr (sizeof(TS) == 4) {
+    // Bulk-copied fp32 rows carry the caller's padding in columns [d, dp):
+    // zero them, so that the sweeps read every column without a mask.
+    if (bulk && d < dp && alive) {
+      const int pad = dp - d;
+      for (int e = tid; e < nr * pad; e += kThreads) {
+        const int i = e / pad;
+        reinterpret_cast<float*>(sa)[(size_t)i * P.sa_pitch + d + (e - i * pad)] = 0.f;
+      }
+      __syncthreads();
+    }
+  }
   if (!alive) {
     if (tid == 0) {
       atomicExch(&g_aab_grid_error, MIHS_ERR_TIMEOUT);
@@ -353,9 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
     __syncthreads();
     // First sweep: w = SA v (p = 0), its ρ² share and U = SAᵀw (ρp = w; the
     // normalisation by ρ is deferred so that one barrier publishes both).
-    float4 ur[CH];
-    float rsq = grid_sweep<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, 0.f, w, P.sa_scale, P.scale_ld, r0, ur);
-    block_reduce_store<CH>(ur, rsq, buf, dp, red, P.Upart + (size_t)blk * dp, P.rho2 + blk);
+    grid_sweep_store<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, 0.f, w, P.sa_scale, P.scale_ld, r0, red, buf,
+                             P.Upart + (size_t)blk * dp, P.rho2 + blk);
     alive = grid_barrier(gbar, s_ok);  // (A) ρ² and U partials
     const float lam = P.lambda;
     float rho = 0.f, rhobar = 0.f, c = 0.f, s = 0.f, phi = 0.f, theta = 0.f;
@@ -460,8 +402,8 @@ __global__ void __launch_bounds__(kThreads, 1) aab_grid_kernel(const AabGridPara
       }
       __syncthreads();
       // ---- ρ p := SA v − θ p (unnormalised in w until ρ is known), ρ², SAᵀw
-      rsq = grid_sweep<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, theta, w, P.sa_scale, P.scale_ld, r0, ur);
-      block_reduce_store<CH>(ur, rsq, buf, dp, red, P.Upart + (size_t)blk * dp, P.rho2 + blk);
+      grid_sweep_store<CH, TS>(sa, P.sa_pitch, nr, d, dp, v, p, theta, w, P.sa_scale, P.scale_ld, r0, red, buf,
+                               P.Upart + (size_t)blk * dp, P.rho2 + blk);
       alive = grid_barrier(gbar, s_ok);  // (A)
     }
   }

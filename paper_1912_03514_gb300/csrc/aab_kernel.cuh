@@ -235,6 +235,205 @@ __device__ __forceinline__ float fused_sweep(const TS* SAc, long long ldc, int n
   return rsq;  // this warp's share of ρ² (same in all lanes)
 }
 
+// Split sweep over SA rows held in shared memory (each row read twice per
+// pass, with no dependency between a row's dot and its update).  Rows sit at
+// `sa` with a pitch of `sp` elements; the columns in [d, dp) are zero there
+// (masked when staged, or zero in the quantised layouts), so every load is an
+// unmasked 16-byte (fp32), 8-byte (bf16) or 4-byte (fp8) read.
+
+// Four consecutive decoded elements of a row held in shared memory.
+template <typename TS>
+__device__ __forceinline__ float4 ld_sa_row4(const TS* row, int j, float scale);
+template <>
+__device__ __forceinline__ float4 ld_sa_row4<float>(const float* row, int j, float) {
+  return *reinterpret_cast<const float4*>(row + j);
+}
+template <>
+__device__ __forceinline__ float4 ld_sa_row4<__nv_bfloat16>(const __nv_bfloat16* row, int j, float s) {
+  return load_sa4<__nv_bfloat16>(row, j, 0, true, s);
+}
+template <>
+__device__ __forceinline__ float4 ld_sa_row4<__nv_fp8_e4m3>(const __nv_fp8_e4m3* row, int j, float s) {
+  return load_sa4<__nv_fp8_e4m3>(row, j, 0, true, s);
+}
+
+// Phase 1, row dots: w_i = SA_i·v − θ·p_i for the block's rows.  Warp `warp`
+// takes rows warp, warp + kWarps, …: four at a time (independent loads,
+// chains and shuffle trees) while four remain, then one at a time.  A lane's
+// column groups j = 4·lane + 128·c at or past dp read the group dp − 4 with
+// v = 0.  Lane 0 stores w_i.  Returns the warp's share of ρ² = Σ w_i² (rows in
+// a fixed order; the same in all lanes).
+template <int CH, typename TS>
+__device__ __forceinline__ float row_dots(const TS* sa, int sp, int nr, const float* v, const float* p, float theta,
+                                          float* w, int dp, const float* scales, int sld, int r0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 vr[CH];
+  int jc[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int j = 4 * lane + 128 * c;
+    jc[c] = j < dp ? j : dp - 4;
+    vr[c] = j < dp ? *reinterpret_cast<const float4*>(v + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float rsq = 0.f;
+  int i = warp;
+  for (; i + 3 * kWarps < nr; i += 4 * kWarps) {
+    float s0[4], s1[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      s0[r] = 0.f;
+      s1[r] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ii = i + r * kWarps;
+        const float sc = scales != nullptr ? scales[(size_t)((r0 + ii) >> 7) * sld + (jc[c] >> 7)] : 1.f;
+        const float4 a = ld_sa_row4<TS>(sa + (size_t)ii * sp, jc[c], sc);
+        s0[r] = fmaf(a.x, vr[c].x, s0[r]);
+        s1[r] = fmaf(a.y, vr[c].y, s1[r]);
+        s0[r] = fmaf(a.z, vr[c].z, s0[r]);
+        s1[r] = fmaf(a.w, vr[c].w, s1[r]);
+      }
+    }
+    float t[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) t[r] = s0[r] + s1[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) t[r] += __shfl_xor_sync(0xffffffffu, t[r], o);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int ii = i + r * kWarps;
+      const float wi = t[r] - theta * p[ii];
+      rsq = fmaf(wi, wi, rsq);
+      if (lane == 0) w[ii] = wi;
+    }
+  }
+  for (; i < nr; i += kWarps) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float sc = scales != nullptr ? scales[(size_t)((r0 + i) >> 7) * sld + (jc[c] >> 7)] : 1.f;
+      const float4 a = ld_sa_row4<TS>(sa + (size_t)i * sp, jc[c], sc);
+      s0 = fmaf(a.x, vr[c].x, s0);
+      s1 = fmaf(a.y, vr[c].y, s1);
+      s0 = fmaf(a.z, vr[c].z, s0);
+      s1 = fmaf(a.w, vr[c].w, s1);
+    }
+    const float wi = warp_sum(s0 + s1) - theta * p[i];
+    rsq = fmaf(wi, wi, rsq);
+    if (lane == 0) w[i] = wi;
+  }
+  return rsq;
+}
+
+// Phase 2, column sums: u_j = Σ_i SA_ij·w_i over the block's rows.  The
+// dp/4 column groups (16 bytes) are spread over the threads: with at least
+// kThreads groups, thread t owns groups t + kThreads·c over all rows; with
+// fewer, the threads form ng = kThreads/⌈groups⌉₃₂ row groups, group g
+// summing rows ≡ g (mod ng), and the ng partials are added in order of g
+// through `tmp` (ng·dp floats).  Each thread keeps four accumulators (rows
+// four apart, each in row order) added as (u0 + u1) + (u2 + u3).  w_i is a
+// shared-memory broadcast.  Writes u to out[0, dp) (shared or global memory);
+// synchronises the block when ng > 1.
+template <int CH, typename TS>
+__device__ __forceinline__ void col_sums(const TS* sa, int sp, int nr, int dp, const float* w, const float* scales,
+                                         int sld, int r0, float* tmp, float* out) {
+  constexpr int CC = (CH * 128 + 4 * kThreads - 1) / (4 * kThreads);
+  const int t = threadIdx.x;
+  const int groups = dp >> 2;
+  const int tg = groups >= kThreads ? kThreads : ((groups + 31) & ~31);
+  const int ng = kThreads / tg;
+  const int g = t / tg, jg = t - g * tg;
+  const bool active = g < ng && jg < groups;
+  float4 u[CC];
+  if (active) {
+    float4 acc[4][CC];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < CC; ++c) acc[r][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int jj[CC];
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      const int q = jg + kThreads * c;
+      jj[c] = 4 * (q < groups ? q : groups - 1);  // a group past the end: a valid load, never stored
+    }
+    int i = g;
+    const int step = ng;
+    for (; i + 3 * step < nr; i += 4 * step) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ii = i + r * step;
+        const float wi = w[ii];
+        const TS* row = sa + (size_t)ii * sp;
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+          const float sc = scales != nullptr ? scales[(size_t)((r0 + ii) >> 7) * sld + (jj[c] >> 7)] : 1.f;
+          const float4 a = ld_sa_row4<TS>(row, jj[c], sc);
+          acc[r][c].x = fmaf(a.x, wi, acc[r][c].x);
+          acc[r][c].y = fmaf(a.y, wi, acc[r][c].y);
+          acc[r][c].z = fmaf(a.z, wi, acc[r][c].z);
+          acc[r][c].w = fmaf(a.w, wi, acc[r][c].w);
+        }
+      }
+    }
+    for (int r = 0; i < nr; i += step, ++r) {  // the last < 4 rows of this group
+      const float wi = w[i];
+      const TS* row = sa + (size_t)i * sp;
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        const float sc = scales != nullptr ? scales[(size_t)((r0 + i) >> 7) * sld + (jj[c] >> 7)] : 1.f;
+        const float4 a = ld_sa_row4<TS>(row, jj[c], sc);
+        // rows i, i + step, i + 2·step go to accumulators 0, 1, 2
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (r == q) {
+            acc[q][c].x = fmaf(a.x, wi, acc[q][c].x);
+            acc[q][c].y = fmaf(a.y, wi, acc[q][c].y);
+            acc[q][c].z = fmaf(a.z, wi, acc[q][c].z);
+            acc[q][c].w = fmaf(a.w, wi, acc[q][c].w);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      u[c].x = (acc[0][c].x + acc[1][c].x) + (acc[2][c].x + acc[3][c].x);
+      u[c].y = (acc[0][c].y + acc[1][c].y) + (acc[2][c].y + acc[3][c].y);
+      u[c].z = (acc[0][c].z + acc[1][c].z) + (acc[2][c].z + acc[3][c].z);
+      u[c].w = (acc[0][c].w + acc[1][c].w) + (acc[2][c].w + acc[3][c].w);
+    }
+  }
+  if (ng == 1) {
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        const int q = jg + kThreads * c;
+        if (q < groups) *reinterpret_cast<float4*>(out + 4 * q) = u[c];
+      }
+    }
+    return;
+  }
+  if (active) *reinterpret_cast<float4*>(tmp + (size_t)g * dp + 4 * jg) = u[0];
+  __syncthreads();
+  for (int q = t; q < groups; q += kThreads) {
+    float4 sacc = *reinterpret_cast<const float4*>(tmp + 4 * q);
+    for (int gg = 1; gg < ng; ++gg) {
+      const float4 b = *reinterpret_cast<const float4*>(tmp + (size_t)gg * dp + 4 * q);
+      sacc.x += b.x;
+      sacc.y += b.y;
+      sacc.z += b.z;
+      sacc.w += b.w;
+    }
+    *reinterpret_cast<float4*>(out + 4 * q) = sacc;
+  }
+}
+
 template <int CL, int CH, typename TS>
 __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParams P) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -382,20 +581,28 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
   int k = 0;
   const int c0 = rank * P.cols_per;
   const int c1 = min(dp, c0 + P.cols_per);
-  if (theta1 > 0.f) {
-    const float inv_theta1 = 1.0f / theta1;
-    for (int j = tid; j < dp; j += kThreads) v[j] *= inv_theta1;
-    __syncthreads();
-    // One sweep: w = SA v (p = 0 here), ρ² partial and u = SAᵀw (ρ p = w, the
-    // normalisation by ρ deferred so that one barrier publishes both).
-    float rsq_w = fused_sweep<CH, TS>(SAc, ldc, nr, d, v, p, 0.f, w, wpart, dp, P.sa_vec != 0, P.sa_scale, P.scale_ld, r0);
-    if (lane == 0) red[warp] = rsq_w;
-    __syncthreads();
-    for (int j = tid; j < dp; j += kThreads) {
-      float t = 0.f;
+  const int ncol = max(0, c1 - c0);
+  const bool split = P.sa_in_smem != 0;
+  // One sweep: w = SA·v − θp (own rows), this block's SAᵀw in `up` and its
+  // ρ² share in scal[1].  With SA in shared memory, row dots then column
+  // sums; streaming SA from L2, the fused sweep that reads each row once.
+  auto sweep = [&](float theta_) {
+    if (split) {
+      const float rsq = row_dots<CH, TS>(sa, sp, nr, v, p, theta_, w, dp, P.sa_scale, P.scale_ld, r0);
+      if (lane == 0) red[warp] = rsq;
+      __syncthreads();  // w complete
+      col_sums<CH, TS>(sa, sp, nr, dp, w, P.sa_scale, P.scale_ld, r0, wpart, up);
+    } else {
+      const float rsq = fused_sweep<CH, TS>(SAc, ldc, nr, d, v, p, theta_, w, wpart, dp, P.sa_vec != 0,
+                                            P.sa_scale, P.scale_ld, r0);
+      if (lane == 0) red[warp] = rsq;
+      __syncthreads();
+      for (int j = tid; j < dp; j += kThreads) {
+        float t = 0.f;
 #pragma unroll
-      for (int q = 0; q < kWarps; ++q) t += wpart[(size_t)q * dp + j];
-      up[j] = t;
+        for (int q = 0; q < kWarps; ++q) t += wpart[(size_t)q * dp + j];
+        up[j] = t;
+      }
     }
     if (tid == 0) {
       float t = 0.f;
@@ -403,43 +610,80 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
       for (int q = 0; q < kWarps; ++q) t += red[q];
       scal[1] = t;
     }
-    cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-    if (warp == 0) {
-      const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
-      if (lane == 0) scal[2] = r2;
-    }
+  };
+  if (theta1 > 0.f) {
+    const float inv_theta1 = 1.0f / theta1;
+    for (int j = tid; j < dp; j += kThreads) v[j] *= inv_theta1;
     __syncthreads();
-    float rho = sqrtf(scal[2]);
-
+    // First sweep: w = SA v (p = 0), ρ² share and SAᵀw (ρ p = w; the
+    // normalisation by ρ is deferred so that one barrier publishes both).
+    sweep(0.f);
     const float lam = lam_;
-    float rhobar = sqrtf(rho * rho + lam);
-    float c = rho / rhobar;
-    float s = sqrtf(lam) / rhobar;
-    float phi = theta1 / rhobar;
-    {
-      const float inv = 1.0f / rhobar;
-      for (int j = tid; j < dp; j += kThreads) {
-        dv[j] = v[j] * inv;
-        xs[j] = phi * dv[j];
-      }
-    }
+    float rho = 0.f, rhobar = 0.f, c = 0.f, s = 0.f, phi = 0.f, theta = 0.f;
     float t = __int_as_float(0x7f800000);  // +inf
-    if (rho > 0.f) {
-      const float inv = 1.0f / rho;
-      for (int i = tid; i < nr; i += kThreads) p[i] = w[i] * inv;
-    }
-
-    while (t >= P.eps && k < P.max_passes && rho > 0.f) {
-      // θ v := SAᵀ p − ρ v  with SAᵀp = (Σ_ranks SAᵀw)/ρ on this block's column slice
+    const int q4 = P.cols_per >> 2;        // float4 groups in a column slice
+    float* ubuf = wpart;                   // CL × cols_per: the ranks' SAᵀw on this block's slice
+    bool first = true;
+    for (;;) {
+      cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
+      // ρ² (warp 0) and every rank's SAᵀw on this block's column slice, all
+      // loads issued together (one DSMEM round trip).
+      for (int e = tid; e < CL * q4; e += kThreads) {
+        const int r = e / q4, q = e - r * q4;
+        const int j = c0 + 4 * q;
+        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < dp) val = *reinterpret_cast<const float4*>(cluster.map_shared_rank(up, r) + j);
+        *reinterpret_cast<float4*>(ubuf + (size_t)r * P.cols_per + 4 * q) = val;
+      }
+      if (warp == 0) {
+        const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
+        if (lane == 0) scal[2] = r2;
+      }
+      __syncthreads();
+      rho = sqrtf(scal[2]);
+      if (first) {
+        rhobar = sqrtf(rho * rho + lam);
+        c = rho / rhobar;
+        s = sqrtf(lam) / rhobar;
+        phi = theta1 / rhobar;
+        const float inv = 1.0f / rhobar;
+        for (int jj = tid; jj < ncol; jj += kThreads) {
+          dv[c0 + jj] = v[c0 + jj] * inv;
+          xs[c0 + jj] = phi * dv[c0 + jj];
+        }
+        first = false;
+      } else {
+        // Eldén's rotation of √λ into the bidiagonal, then the φ recursion
+        // and the forward-substitution update (Section 3.6), on the slice.
+        const float lambar = sqrtf(lam + (s * theta) * (s * theta));
+        const float thetabar = c * theta;
+        rhobar = sqrtf(rho * rho + lambar * lambar);
+        const float inv_rhobar = 1.0f / rhobar;
+        c = rho * inv_rhobar;
+        s = lambar * inv_rhobar;
+        phi = -phi * thetabar * inv_rhobar;
+        for (int jj = tid; jj < ncol; jj += kThreads) {
+          const int j = c0 + jj;
+          const float dn = (v[j] - thetabar * dv[j]) * inv_rhobar;
+          dv[j] = dn;
+          xs[j] = fmaf(phi, dn, xs[j]);
+        }
+        t = fabsf(phi * rhobar) / theta1;
+        ++k;
+      }
+      if (rho > 0.f) {
+        const float inv = 1.0f / rho;
+        for (int i = tid; i < nr; i += kThreads) p[i] = w[i] * inv;
+      }
+      if (!(t >= P.eps && k < P.max_passes && rho > 0.f)) break;  // the same in every block
+      // θ v := SAᵀp − ρ v on the slice, SAᵀp = (Σ_ranks SAᵀw)/ρ (ranks in order)
       const float inv_rho = 1.0f / rho;
       float zpart = 0.f;
-      for (int j = c0 + tid; j < c1; j += kThreads) {
-        float u[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) u[r] = cluster.map_shared_rank(up, r)[j];
+      for (int jj = tid; jj < ncol; jj += kThreads) {
         float us = 0.f;
 #pragma unroll
-        for (int r = 0; r < CL; ++r) us += u[r];
+        for (int r = 0; r < CL; ++r) us += ubuf[(size_t)r * P.cols_per + jj];
+        const int j = c0 + jj;
         const float z = j < d ? us * inv_rho - rho * v[j] : 0.f;
         zsl[j] = z;
         zpart = fmaf(z, z, zpart);
@@ -447,64 +691,37 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
       zpart = block_sum(zpart, red);
       if (tid == 0) scal[0] = zpart;
       cluster.sync();  // (B) slices of θv and θ² partials visible
+      // θ² (warp 0) and all of θv from the slices' owners, loads issued together
+      constexpr int CV = (CH * 128 + 4 * kThreads - 1) / (4 * kThreads);
+      float4 zr[CV];
+#pragma unroll
+      for (int cc = 0; cc < CV; ++cc) {
+        const int j = 4 * tid + 4 * kThreads * cc;
+        zr[cc] = j < dp ? *reinterpret_cast<const float4*>(cluster.map_shared_rank(zsl, j >> P.cols_log2) + j)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       if (warp == 0) {
         const float t2 = cluster_scalar_sum<CL>(lane_scal, 0);
         if (lane == 0) scal[2] = t2;
       }
       __syncthreads();
-      const float theta = sqrtf(scal[2]);
+      theta = sqrtf(scal[2]);
       if (!(theta > 0.f)) break;  // invariant subspace: same decision everywhere
       const float inv_theta = 1.0f / theta;
-      for (int j = tid; j < dp; j += kThreads)
-        v[j] = cluster.map_shared_rank(zsl, j >> P.cols_log2)[j] * inv_theta;
+#pragma unroll
+      for (int cc = 0; cc < CV; ++cc) {
+        const int j = 4 * tid + 4 * kThreads * cc;
+        if (j < dp)
+          *reinterpret_cast<float4*>(v + j) =
+              make_float4(zr[cc].x * inv_theta, zr[cc].y * inv_theta, zr[cc].z * inv_theta, zr[cc].w * inv_theta);
+      }
       __syncthreads();
       // ρ p := SA v − θ p (kept unnormalised in w until ρ is known), its ρ²
-      // partial and SAᵀw, in one sweep.
-      rsq_w = fused_sweep<CH, TS>(SAc, ldc, nr, d, v, p, theta, w, wpart, dp, P.sa_vec != 0, P.sa_scale, P.scale_ld, r0);
-      if (lane == 0) red[warp] = rsq_w;
-      __syncthreads();
-      for (int j = tid; j < dp; j += kThreads) {
-        float tt = 0.f;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) tt += wpart[(size_t)q * dp + j];
-        up[j] = tt;
-      }
-      if (tid == 0) {
-        float tt = 0.f;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) tt += red[q];
-        scal[1] = tt;
-      }
-      cluster.sync();  // (A) ρ² partials and SAᵀw partials visible
-      if (warp == 0) {
-        const float r2 = cluster_scalar_sum<CL>(lane_scal, 1);
-        if (lane == 0) scal[2] = r2;
-      }
-      __syncthreads();
-      rho = sqrtf(scal[2]);
-      // Eldén's rotation of √λ into the bidiagonal, then the φ recursion and
-      // the forward-substitution update (Section 3.6).
-      const float lambar = sqrtf(lam + (s * theta) * (s * theta));
-      const float thetabar = c * theta;
-      rhobar = sqrtf(rho * rho + lambar * lambar);
-      const float inv_rhobar = 1.0f / rhobar;
-      c = rho * inv_rhobar;
-      s = lambar * inv_rhobar;
-      phi = -phi * thetabar * inv_rhobar;
-      for (int j = tid; j < dp; j += kThreads) {
-        const float dn = (v[j] - thetabar * dv[j]) * inv_rhobar;
-        dv[j] = dn;
-        xs[j] = fmaf(phi, dn, xs[j]);
-      }
-      t = fabsf(phi * rhobar) / theta1;
-      ++k;
-      if (rho > 0.f) {
-        const float inv = 1.0f / rho;
-        for (int i = tid; i < nr; i += kThreads) p[i] = w[i] * inv;
-      }
-      __syncthreads();
+      // share and SAᵀw.
+      sweep(theta);
     }
   }
+  __syncthreads();
 
   // Outputs: each block writes its column slice.
   {
