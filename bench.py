@@ -939,21 +939,23 @@ def run_mixed(args, dev, ws):
     tol = args.mixed_tol
     precs = ("fp32", "bf16", "fp8")
 
-    def solve_all(p, A, b, timed):
+    def solve_all(p, A, b, timed, lam=lam, sd=None, m=None):
+        sd = p.sd if sd is None else sd
+        m = p.m if m is None else m
         res = {}
-        sk = mihs.Sketch(A, "gaussian", p.m, seed=3)
+        sk = mihs.Sketch(A, "gaussian", m, seed=3)
         x = torch.empty(d, dtype=torch.float64, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream = torch.cuda.current_stream()
         for prec in precs:
             def step(want_info=False):
                 sk.resketch(A, 3)
-                return sk.solve_refined(A, b, lam, p.sd, tol=tol, max_outer=300, x=x, want_info=want_info)[1]
+                return sk.solve_refined(A, b, lam, sd, tol=tol, max_outer=300, x=x, want_info=want_info)[1]
             sk.set_precision(prec)
             try:
                 info = step(want_info=True)
-            except mihs.MihsError as e:  # a quantised SA can stop being an embedding
-                res[prec] = {"status": e.code, "error": str(e).split(":")[0]}
+            except mihs.MihsError as e:  # the library's guard: the quantised SA no longer preconditions
+                res[prec] = {"status": e.code, "error": str(e)[:400]}
                 continue
             r = {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters_total,
                  "rel_resid": float(f"{info.rel_resid:.3e}"), "x": x.cpu().numpy().copy()}
@@ -997,6 +999,18 @@ def run_mixed(args, dev, ws):
                 r["rel_err_vs_oracle"] = float(f"{o.rel_error(r['x'], xs):.3e}")
     for r in out["by_sa_precision"].values():
         r.pop("x", None)
+    # The same matrix at λ = 1e-3 (κ(H) ≈ 1e3), where fp8 and bf16 storage of
+    # SA still precondition (the guard accepts them): m = 4·sd(1e-3).
+    lam3 = 1e-3
+    sd3 = W.nominal_sd(p.sigma, lam3)
+    m3 = W.round_up(4.0 * sd3, 4)
+    r3 = solve_all(p, p.A, p.b, True, lam=lam3, sd=sd3, m=m3)
+    for r in r3.values():
+        r.pop("x", None)
+    out["lambda_1e-3"] = {"workload": f"the same A and b, λ = {lam3:g} (sd {sd3:.1f}, κ(H) ≈ 1e3), Gaussian m = {m3}, "
+                                      f"refinement to relative residual {tol:g} (relative error ≤ κ(H)·residual "
+                                      f"≈ {1e3 * tol:.0e})",
+                          "by_sa_precision": r3}
     del p
     torch.cuda.empty_cache()
     if args.mixed_sample_rows > 0:

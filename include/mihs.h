@@ -274,7 +274,16 @@ int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream);
  * targets below the fp32 floor.  Converts the current SA now and after every
  * mihs_resketch; the first call for a quantised precision allocates the
  * quantised copy (cudaMalloc).  MIHS_SA_FP32 switches back.  Sd estimation
- * (Algorithm 4) keeps using the fp32 SA.  Errors: INVALID_ARG, OOM, CUDA. */
+ * (Algorithm 4) keeps using the fp32 SA.
+ * Guard: each conversion also measures the rounding E = SA_q − SA (‖E‖_F²,
+ * read back to the host, so this call and mihs_resketch synchronise the
+ * stream for a quantised handle).  A solve (mihs_solve, _refined, _path,
+ * mihs_backward*) at a λ with ‖E‖_F²·(1/√m + 1/√d)² > λ/2 (an estimate of
+ * ‖E‖₂²) returns MIHS_ERR_UNSUPPORTED before launching anything: past that
+ * point the sketched Hessian is no longer within a factor 2 of the exact
+ * one, and the preconditioned spectrum can leave the region where the heavy
+ * ball of Theorem 1 converges (fp8 at κ(AᵀA + λI) ≈ 1e6 does).
+ * Errors: INVALID_ARG, OOM, CUDA. */
 int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream);
 
 /* Form of the inner solver (AAb_Solver, Algorithm 5) in a handle's solves

@@ -196,6 +196,8 @@ struct mihs_sketch_s {
   void* SAq = nullptr;         // quantised SA (m × ldq) when sa_prec != fp32
   float* sa_scales = nullptr;  // fp8 tile scales
   int64_t ldq = 0;
+  double* sa_qerr_dev = nullptr;  // kQuantErrBlocks partials + ‖SA_q − SA‖_F²
+  double sa_qerr = 0.0;           // host copy of ‖SA_q − SA‖_F² for the current SA_q
   float* partials;    // P × dp
   float* g;           // dp
   float* x_prev;      // dp
@@ -768,6 +770,38 @@ int mihs_sketch(const float* A, int64_t n, int64_t d, int64_t lda, int family, i
   return MIHS_OK;
 }
 
+// Quantises the handle's SA into SA_q and reads ‖SA_q − SA‖_F² back to the
+// host (synchronises the stream) for the guard of quantised solves.
+static int quantize_handle(mihs_sketch_t sk, cudaStream_t s) {
+  int rc = launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sk->sa_prec, sk->SAq, sk->ldq, sk->sa_scales, s);
+  if (rc) return rc;
+  rc = launch_quant_error(sk->SA, sk->m, sk->d, sk->dp, sk->sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
+                          sk->sa_qerr_dev, sk->sa_qerr_dev + kQuantErrBlocks, s);
+  if (rc) return rc;
+  MIHS_CUDA_TRY(cudaMemcpyAsync(&sk->sa_qerr, sk->sa_qerr_dev + kQuantErrBlocks, sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+  MIHS_CUDA_TRY(cudaStreamSynchronize(s));
+  return MIHS_OK;
+}
+
+// Solves on a quantised SA are refused where the rounding E = SA_q − SA can
+// no longer be trusted to leave a preconditioner: the sketched Hessian stays
+// within a factor 2 of the exact one (SA_qᵀSA_q + λI ⪰ ½(SAᵀSA + λI)) when
+// ‖E‖₂² ≤ λ/2, and beyond that the spectrum of (SA_qᵀSA_q + λI)⁻¹(AᵀA + λI)
+// can leave the region where the heavy ball of Theorem 1 converges (fp8 e4m3
+// at κ(AᵀA + λI) ≈ 1e6 puts its largest eigenvalue near 8, past the
+// 2(1 + β)/α ≈ 4.4 of β = 1/4).
+static int check_quantised(const mihs_sketch_s* sk, double lambda, const char* who) {
+  if (sk->sa_prec == MIHS_SA_FP32 || sk->SAq == nullptr) return MIHS_OK;
+  const double est = quant_spectral_estimate(sk->sa_qerr, sk->m, sk->d);
+  if (est <= 0.5 * lambda) return MIHS_OK;
+  set_error("%s: SA stored in %s has an estimated rounding ||SA_q - SA||_2^2 = %.3g = %.3g lambda > lambda/2 "
+            "(lambda = %g): at this lambda the quantised sketch no longer preconditions Algorithm 1; store SA "
+            "in a wider format (bf16 or fp32)", who, sk->sa_prec == MIHS_SA_BF16 ? "bf16" : "fp8 e4m3", est,
+            est / lambda, lambda);
+  return MIHS_ERR_UNSUPPORTED;
+}
+
 int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, void* stream) {
   set_error("");
   MIHS_ARG(sk != nullptr, "mihs_resketch: null handle");
@@ -781,8 +815,7 @@ int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, 
   else
     rc = mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
   if (rc || sk->sa_prec == MIHS_SA_FP32) return rc;
-  return launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sk->sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
-                            static_cast<cudaStream_t>(stream));
+  return quantize_handle(sk, static_cast<cudaStream_t>(stream));
 }
 
 int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream) {
@@ -793,7 +826,8 @@ int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream) {
   if (sa_prec != MIHS_SA_FP32 && sk->SAq == nullptr) {
     sk->ldq = sa_quant_ld(sk->d);
     const size_t qbytes = round_up((int64_t)sk->m * sk->ldq, 256);  // ≤ 1 byte/element more than fp8 needs
-    const size_t bytes = 2 * qbytes + sizeof(float) * (size_t)sa_scale_count(sk->m, sk->d);
+    const size_t sbytes = round_up(sizeof(float) * (size_t)sa_scale_count(sk->m, sk->d), 256);
+    const size_t bytes = 2 * qbytes + sbytes + sizeof(double) * (kQuantErrBlocks + 1);
     char* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
@@ -802,11 +836,11 @@ int mihs_sketch_set_precision(mihs_sketch_t sk, int sa_prec, void* stream) {
     }
     sk->SAq = p;
     sk->sa_scales = reinterpret_cast<float*>(p + 2 * qbytes);
+    sk->sa_qerr_dev = reinterpret_cast<double*>(p + 2 * qbytes + sbytes);
   }
   sk->sa_prec = sa_prec;
   if (sa_prec == MIHS_SA_FP32) return MIHS_OK;
-  return launch_quantize_sa(sk->SA, sk->m, sk->d, sk->dp, sa_prec, sk->SAq, sk->ldq, sk->sa_scales,
-                            static_cast<cudaStream_t>(stream));
+  return quantize_handle(sk, static_cast<cudaStream_t>(stream));
 }
 
 int mihs_sketch_set_aab(mihs_sketch_t sk, int form, int grid_blocks) {
@@ -890,6 +924,8 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
   MIHS_ARG(opts->sd < (double)sk->m, "mihs_solve: sd=%g must be < m=%lld", opts->sd, (long long)sk->m);
   MIHS_ARG(opts->max_outer >= 0 && opts->max_outer < (1 << 24), "mihs_solve: bad max_outer");
   MIHS_ARG(opts->eps_sub >= 0.0, "mihs_solve: eps_sub must be >= 0");
+  rc = check_quantised(sk, lambda, "mihs_solve");
+  if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = sk->n, d = sk->d;
   if (refined && sk->dd_partials == nullptr) {
@@ -1112,6 +1148,8 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
     MIHS_ARG(lambdas[l] > 0.0 && lambdas[l] <= (double)FLT_MAX, "mihs_solve_path: lambda[%d] must be in (0, FLT_MAX]", l);
     if (sds != nullptr)
       MIHS_ARG(sds[l] < (double)sk->m, "mihs_solve_path: sd[%d]=%g must be < m", l, sds[l]);
+    rc = check_quantised(sk, lambdas[l], "mihs_solve_path");
+    if (rc) return rc;
   }
   if (d > apass_path_max_d()) {
     set_error("mihs_solve_path: d=%lld > %d is not supported", (long long)d, apass_path_max_d());

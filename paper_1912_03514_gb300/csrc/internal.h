@@ -54,6 +54,19 @@ int64_t sa_quant_ld(int64_t d);                 // row pitch (elements) of quant
 int64_t sa_scale_count(int64_t m, int64_t d);   // fp8 tile scales
 int launch_quantize_sa(const float* SA, int64_t m, int64_t d, int64_t ldsa, int prec, void* out, int64_t ldq,
                        float* scales, cudaStream_t s);
+// ‖decode(q) − SA‖_F² in fp64 (deterministic: kQuantErrBlocks block partials
+// in `scratch`, summed in order) into *err_out (device).
+constexpr int kQuantErrBlocks = 512;
+int launch_quant_error(const float* SA, int64_t m, int64_t d, int64_t ldsa, int prec, const void* q, int64_t ldq,
+                       const float* scales, double* scratch, double* err_out, cudaStream_t s);
+// The quantisation guard: storing SA as SA_q = SA + E keeps the sketched
+// Hessian within a factor 2 of the exact one's (SA_qᵀSA_q + λI ⪰ ½(SAᵀSA + λI))
+// when ‖E‖₂² ≤ λ/2.  ‖E‖₂² is estimated from ‖E‖_F² as for a matrix of
+// independent equal-variance entries, ‖E‖_F²·(1/√m + 1/√d)².
+inline double quant_spectral_estimate(double fro2, int64_t m, int64_t d) {
+  const double f = 1.0 / ::sqrt((double)m) + 1.0 / ::sqrt((double)d);
+  return fro2 * f * f;
+}
 
 // ---- gradients of the solution (backward.cu) ------------------------------
 // dlambda = −xᵀv (fp64); db = Av; dA = r vᵀ − (Av) xᵀ with r = b − Ax.  Any of

@@ -8,6 +8,7 @@
 // point is where the exact gradient vanishes, Section 3.1), so a coarser SA
 // changes the rate, not the solution.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "internal.h"
@@ -67,7 +68,68 @@ __global__ void quant_fp8_kernel(const float* __restrict__ SA, int m, int d, lon
   }
 }
 
+// Σ (decoded q − SA)² over the block's elements (a fixed range per block),
+// each element's error formed in fp32 exactly as the AAb kernels decode it and
+// squared and summed in fp64: one partial per block.
+template <typename TQ>
+__global__ void quant_err_kernel(const float* __restrict__ SA, int m, int d, long long ldsa, const TQ* __restrict__ q,
+                                 long long ldq, const float* __restrict__ scales, int ntc,
+                                 double* __restrict__ partial) {
+  const long long total = (long long)m * d;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long e0 = (long long)blockIdx.x * per, e1 = e0 + per < total ? e0 + per : total;
+  double acc = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const long long i = e / d, j = e - i * d;
+    float dec;
+    if constexpr (sizeof(TQ) == 2) {
+      dec = __bfloat162float(q[i * ldq + j]);
+    } else {
+      const __half_raw h = __nv_cvt_fp8_to_halfraw(q[i * ldq + j].__x, __NV_E4M3);
+      dec = __half2float(__half(h)) * scales[(size_t)(i / kTile) * ntc + j / kTile];
+    }
+    const double err = (double)dec - (double)SA[i * ldsa + j];
+    acc = fma(err, err, acc);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void quant_err_sum_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < n; ++b) t += partial[b];
+    *out = t;
+  }
+}
+
 }  // namespace
+
+int launch_quant_error(const float* SA, int64_t m, int64_t d, int64_t ldsa, int prec, const void* q, int64_t ldq,
+                       const float* scales, double* scratch, double* err_out, cudaStream_t s) {
+  if (m == 0) {
+    MIHS_CUDA_TRY(cudaMemsetAsync(err_out, 0, sizeof(double), s));
+    return MIHS_OK;
+  }
+  const int ntc = (int)((round_up(d, 4) + kTile - 1) / kTile);
+  if (prec == MIHS_SA_BF16)
+    quant_err_kernel<__nv_bfloat16><<<kQuantErrBlocks, 256, 0, s>>>(
+        SA, (int)m, (int)d, ldsa, static_cast<const __nv_bfloat16*>(q), ldq, scales, ntc, scratch);
+  else
+    quant_err_kernel<__nv_fp8_e4m3><<<kQuantErrBlocks, 256, 0, s>>>(
+        SA, (int)m, (int)d, ldsa, static_cast<const __nv_fp8_e4m3*>(q), ldq, scales, ntc, scratch);
+  MIHS_CHECK_LAUNCH();
+  quant_err_sum_kernel<<<1, 32, 0, s>>>(scratch, kQuantErrBlocks, err_out);
+  MIHS_CHECK_LAUNCH();
+  count_launch(2);
+  return MIHS_OK;
+}
 
 int64_t sa_quant_ld(int64_t d) { return round_up(d, 16); }
 int64_t sa_scale_count(int64_t m, int64_t d) {

@@ -101,9 +101,8 @@ def test_refined_solve_bf16_sa_ill_conditioned():
     """κ(H) ≈ 1e6 (the mixed-precision workload's conditioning at a size the
     oracle refines quickly): bf16 SA with refinement reaches 1e-10.  (fp8's
     2⁻⁴ relative rounding of every entry swamps the directions of A with
-    σ_i ≪ 2⁻⁴·σ_1, so SAq stops being a subspace embedding for them and the
-    iteration stalls near 1e-8 here; it is tested on the well-conditioned
-    problem above.)"""
+    σ_i ≪ 2⁻⁴·σ_1, so SAq stops preconditioning them: the library refuses
+    that solve, test_fp8_refused_where_it_cannot_precondition.)"""
     n, d = 65536, 512
     sigma = W.profile_exponential(d, 8.0)
     p = W.make_problem(n, d, sigma, 1e-6, 40.0, seed=21)
@@ -114,6 +113,36 @@ def test_refined_solve_bf16_sa_ill_conditioned():
         x, info = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-14, max_outer=400)
     err = o.rel_error(x.cpu().numpy(), xs)
     assert err <= 1e-10, (err, info)
+
+
+def test_fp8_refused_where_it_cannot_precondition():
+    """At κ(AᵀA + λI) ≈ 1e6 the fp8 rounding of SA is ≈ 75·λ in spectral norm
+    (the oracle's test_quantised_sa_spectrum_reading): every solve on an fp8
+    handle there returns MIHS_ERR_UNSUPPORTED with a message before launching
+    anything, bf16 storage of the same sketch is accepted and reaches the
+    oracle's solution, and fp8 at λ = 1e-3 (4 decades) is accepted too."""
+    n, d = 16384, 512
+    p = W.make_problem(n, d, W.profile_exponential(d, 8.0), 1e-6, 40.0, seed=1012)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    with mihs.Sketch(A, "gaussian", p.m, seed=3) as sk:
+        sk.set_precision("fp8")
+        for call in (lambda: sk.solve(A, b, p.lam, p.sd, tol=1e-6),
+                     lambda: sk.solve_refined(A, b, p.lam, p.sd, tol=1e-12),
+                     lambda: sk.solve_path(A, b, [1e-3, p.lam], sds=[10.0, p.sd], tol=1e-6)):
+            with pytest.raises(mihs.MihsError) as e:
+                call()
+            assert e.value.code == mihs.UNSUPPORTED and "no longer preconditions" in str(e.value), str(e.value)
+        sk.set_precision("bf16")
+        x, info = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-14, max_outer=400)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam, refine=3, extended=True)
+    assert info.converged and o.rel_error(x.cpu().numpy(), xs) <= 1e-10, info
+    q = W.make_problem(n, d, W.profile_exponential(d, 4.0), 1e-3, 40.0, seed=1013)
+    Aq, bq = q.A.to(DEV), q.b.to(DEV)
+    with mihs.Sketch(Aq, "gaussian", q.m, seed=3) as sk:
+        sk.set_precision("fp8")
+        xq, iq = sk.solve_refined(Aq, bq, q.lam, q.sd, tol=1e-12, max_outer=300)
+    xsq = o.exact_solve(q.A.numpy(), q.b.numpy(), q.lam, refine=3, extended=True)
+    assert iq.converged and o.rel_error(xq.cpu().numpy(), xsq) <= 1e-10, iq
 
 
 def test_path_with_bf16_sa():

@@ -700,3 +700,33 @@ def test_corollary3_iteration_count_closed_form():
     with β = 1/100, η = 1e-6 needs 6."""
     assert math.isclose(o.corollary3_iters(2.0 ** -10, 0.25), 10.0, rel_tol=1e-12)
     assert math.isclose(o.corollary3_iters(1e-6, 0.01), 6.0, rel_tol=1e-12)
+
+
+def test_quantised_sa_spectrum_reading():
+    """Reading of quantised SA storage (the sketch only preconditions, Section
+    3.1; the heavy ball of Theorem 1 converges for eigenvalues μ of
+    (SAᵀSA + λI)⁻¹(AᵀA + λI) with α·μ < 2(1 + β)).  At κ(AᵀA + λI) ≈ 1e6
+    (8 decades, λ = 1e-6) bf16 rounding of SA keeps μ inside that region and
+    fp8 e4m3 with 128 × 128 tile scales pushes it out, and the estimate
+    ‖E‖_F²·(1/√m + 1/√d)² used by the library's guard tracks ‖E‖₂² of the
+    actual rounding E = SA_q − SA within a factor 2 and sits on the same side
+    of λ/2."""
+    n, d, lam = 4096, 256, 1e-6
+    sig = W.profile_exponential(d, 8.0)
+    p = W.make_problem(n, d, sig, lam, 40.0, 77)
+    A = p.A.numpy().astype(np.float64)
+    m = min(n, W.round_up(4 * p.sd, 4))
+    SA = o.sketch_apply(o.GAUSSIAN, p.A.numpy(), m, 5)
+    alpha, beta = o.momentum_params(p.sd, m)
+    edge = 2 * (1 + beta) / alpha
+    out = {}
+    for prec in ("bf16", "fp8"):
+        dec = o.quantize_sa(SA.astype(np.float32), prec)[2]
+        E = dec - SA.astype(np.float32).astype(np.float64)
+        e2 = np.linalg.norm(E, 2) ** 2
+        est = np.sum(E * E) * (1 / np.sqrt(m) + 1 / np.sqrt(d)) ** 2
+        assert 0.5 * e2 <= est <= 2 * e2, (prec, est, e2)
+        mu = o.sketched_hessian_eigs(A, dec, lam)
+        out[prec] = (est / lam, mu.max())
+    assert out["bf16"][0] <= 0.5 and out["bf16"][1] < edge, out
+    assert out["fp8"][0] > 0.5 and out["fp8"][1] > edge, out
