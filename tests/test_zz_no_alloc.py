@@ -14,6 +14,7 @@ must leave the device's free memory unchanged.  The file is collected last
 and holds whether it runs alone or after the rest.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -70,14 +71,22 @@ def test_noalloc_allocates_nothing():
     g = torch.empty(d, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     assert fn(A.data_ptr(), n, d, d, b.data_ptr(), x.data_ptr(), 0.5, g.data_ptr(), stream) == 0
-    torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    torch_bytes = torch.cuda.memory_allocated()
-    for _ in range(3):
-        assert fn(A.data_ptr(), n, d, d, b.data_ptr(), x.data_ptr(), 0.5, g.data_ptr(), stream) == 0
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0 and torch.cuda.memory_allocated() == torch_bytes
+    # no garbage collection inside the measured window (it would release
+    # tensors of earlier tests and move torch's counter)
+    gc.collect()
+    gc.disable()
+    try:
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        torch_bytes = torch.cuda.memory_allocated()
+        for _ in range(3):
+            assert fn(A.data_ptr(), n, d, d, b.data_ptr(), x.data_ptr(), 0.5, g.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        torch_bytes1 = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
+    assert free1 == free0 and torch_bytes1 == torch_bytes
     assert torch.equal(g, mihs.gradient(A, b, x, 0.5))
 
 
