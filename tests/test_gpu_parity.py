@@ -90,6 +90,32 @@ AAB_CASES = [  # m, d, lam
 ]
 
 
+
+@pytest.mark.parametrize("n,d,cut", [(20000, 1024, 7000), (3001, 129, 1500)])
+def test_gradient_row_shards_sum_to_the_gradient(n, d, cut):
+    """Virtual row shards on one GPU: the library's gradients of A[:cut] (λ = 0)
+    and A[cut:] (with λ) summed give g = Aᵀ(b − Ax) − λx within the fp32
+    bound of the deeper shard plus one add (the all-reduce of one d-vector
+    that a row-sharded solve would need per step)."""
+    lda = (d + 3) // 4 * 4
+    A = W.padded_matrix(n, d, lda, seed=17 + d)
+    b = W.randn((n,), 18)
+    x = W.randn((d,), 19, scale=0.3)
+    lam = 0.37
+    Ad = A.to(DEV)
+    A1 = Ad[:cut].as_strided((cut, d), (lda, 1))
+    A2 = Ad[cut:].as_strided((n - cut, d), (lda, 1))
+    bd, xd = b.to(DEV), x.to(DEV)
+    g1 = mihs.gradient(A1, bd[:cut].contiguous(), xd, 0.0).double()
+    g2 = mihs.gradient(A2, bd[cut:].contiguous(), xd, lam).double()
+    g = (g1 + g2).cpu().numpy()
+    An = A[:, :d].numpy().astype(np.float64)
+    ref = o.gradient(An, b.numpy(), x.numpy(), lam)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    dr, da = apass_depths(max(cut, n - cut), d, sms)
+    bound = gradient_bound(An, b.numpy(), x.numpy(), lam, dr, da + 1)
+    assert np.all(np.abs(g - ref) <= bound), float(np.max(np.abs(g - ref) / bound))
+
 def _sa_case(m, d, seed):
     SA = W.randn((m, d), seed, scale=1.0 / math.sqrt(m))
     g = W.randn((d,), seed + 1)
