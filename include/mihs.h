@@ -449,10 +449,13 @@ typedef struct {
 } mihs_problem;
 
 /* mihs_solve_path for nprob independent problems sharing one λ list:
- * the problems run concurrently on four internal streams (one with
- * MIHS_PATH_AAB=grid) forked from and joined back into `stream`.  sds: HOST nprob × nlambda (row i for problem i) or
- * NULL; infos: HOST nprob × nlambda or NULL (then no synchronisation).
- * Every problem must have its own handle.  Returns the worst status. */
+ * the problems run concurrently on internal streams (8 by default; the
+ * environment variable MIHS_BATCH_STREAMS sets 2 … 32) forked from and
+ * joined back into `stream`; problems whose steps use the cooperative grid
+ * form of AAb_Solver share one of them.  sds: HOST nprob × nlambda (row i
+ * for problem i) or NULL; infos: HOST nprob × nlambda or NULL (then no
+ * synchronisation).  Every problem must have its own handle.  Returns the
+ * worst status. */
 int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda,
                        const double* lambdas, const double* sds,
                        const mihs_opts* opts, mihs_info* infos, void* stream);

@@ -1336,10 +1336,20 @@ int mihs_solve_path(mihs_sketch_t sk, const float* A, int64_t lda, const float* 
 }
 
 // Internal streams of the batched entry points (per device, created on first
-// use): kBatchStreams streams and kBatchStreams + 1 events, the last one the
-// fork event.
-constexpr int kBatchStreams = 4;
+// use): batch_stream_count() streams and one more event than streams, the
+// last one the fork event.  Problems whose solves use the cooperative grid
+// form of AAb_Solver share stream 0; the others are spread over the rest, so
+// that the small sketches' cluster kernels (1–8 SMs each) fill the GPU.
+static int batch_stream_count() {
+  static const int n = [] {
+    int v = 8;
+    if (const char* e = std::getenv("MIHS_BATCH_STREAMS")) v = std::atoi(e);
+    return v < 2 ? 2 : (v > 32 ? 32 : v);
+  }();
+  return n;
+}
 static int batch_streams(std::vector<cudaStream_t>& st, std::vector<cudaEvent_t>& ev) {
+  const int kBatchStreams = batch_stream_count();
   static std::mutex mu;
   static std::vector<std::vector<cudaStream_t>> pool;  // per device
   static std::vector<std::vector<cudaEvent_t>> evs;
@@ -1380,8 +1390,8 @@ int mihs_solve_batched(int nprob, const mihs_problem* probs, int nlambda, const 
   // into the caller's stream.  Problems whose path steps use the cooperative
   // grid form all go to stream 0 (two such grids must never wait for each
   // other's blocks, so they never run concurrently); the others are spread
-  // over streams 1 … 3 (or all four when no problem uses the grid form).
-  constexpr int kStreams = kBatchStreams;
+  // over the other streams (or all of them when no problem uses the grid form).
+  const int kStreams = batch_stream_count();
   const int nstreams = kStreams;
   std::vector<cudaStream_t> st;
   std::vector<cudaEvent_t> ev;
@@ -1468,9 +1478,10 @@ int mihs_refine_batched(int nprob, const mihs_problem* probs, int nlambda, const
   std::vector<cudaEvent_t> ev;
   int rc = batch_streams(st, ev);
   if (rc) return rc;
+  const int kBatchStreams = batch_stream_count();
   // Refined solves whose AAb_Solver takes the cooperative grid form run one
   // after another on stream 0 (two such grids must never wait for each
-  // other's blocks); the others are spread over streams 1 … 3.
+  // other's blocks); the others are spread over the other streams.
   auto uses_grid = [](const mihs_sketch_s* sk) {
     const int sa_type = sk->sa_prec != MIHS_SA_FP32 && sk->SAq != nullptr ? sk->sa_prec : MIHS_SA_FP32;
     return aab_grid_wanted((int)sk->m, (int)sk->d, sa_type, sk->aab_form);
