@@ -82,7 +82,7 @@ def parse():
                     help="form of AAb_Solver in the refined leg's solves (same values as --aab)")
     ap.add_argument("--profile-op", choices=["apass", "apass-dd", "backward", "path", "aab", "aab-late", "aab-wide",
                                             "aab-wide-bf16", "dual-grad",
-                                            "gaussian", "gaussian-bf16", "countsketch", "srht"],
+                                            "gaussian", "gaussian-bf16", "gaussian-fp8", "countsketch", "srht"],
                     help="time one kernel family alone on the workload (for ncu captures)")
     return ap.parse_args()
 
@@ -934,7 +934,8 @@ def run_mixed(args, dev, ws):
     """2²¹ × 2048, σ_i = 10^(−8(i−1)/2047), λ = 1e-6 (sd ≈ 768, κ(H) ≈ 1e6),
     40 dB SNR, Gaussian sketch with m = 4·sd: compensated-refinement solves to
     a relative residual of --mixed-tol with SA stored in fp32, bf16 and fp8
-    inside AAb_Solver (bf16 / fp8 handles form S·A from bf16 operands).  One
+    inside AAb_Solver (bf16 handles form S·A from bf16 operands, fp8 handles
+    from e4m3 operands).  One
     step = sketch + refined solve.  The relative error against the oracle is
     measured on a sample with the same σ profile, λ and sketch size at
     --mixed-sample-rows rows (the oracle's fp64 Gram of all 2²¹ rows takes
@@ -997,8 +998,9 @@ def run_mixed(args, dev, ws):
     out = {"workload": f"{p.name}, SNR 40 dB, λ = 1e-6 (sd {p.sd:.1f}, κ(H) ≈ 1e6), Gaussian m = {p.m}, "
                        f"refinement to relative residual {tol:g}; A = {4 * n * d / 1e9:.1f} GB",
            "unit": "solves/s",
-           "sketch_operands": "fp32 SA: tf32 S and A; bf16 / fp8 SA: S·A formed from bf16 S and A "
-                              "(fp32 accumulation), then stored in that precision",
+           "sketch_operands": "fp32 SA: tf32 S and A; bf16 SA: S·A formed from bf16 S and A; fp8 SA: "
+                              "from e4m3 S and A (A scaled by a power of two); fp32 accumulation, then "
+                              "stored in that precision",
            "by_sa_precision": solve_all(p, p.A, p.b, True)}
     if args.mixed_oracle:
         from oracle import mihs_oracle as o
@@ -1110,9 +1112,10 @@ def run_profile_op(args, local):
         skp = mihs.Sketch(q.A, "gaussian", m, seed=3)
         Xp = torch.empty(16, q.d, device=dev)
         fn = lambda: skp.solve_path(q.A, q.b, lams, sds=sds, tol=1e-6, max_outer=100, X=Xp, want_info=False)
-    elif op == "gaussian-bf16":
+    elif op in ("gaussian-bf16", "gaussian-fp8"):
         SA = torch.empty(p.m, p.d, device=dev)
-        fn = lambda: mihs.sketch_gaussian_bf16(A, p.m, 3, SA=SA)
+        form = mihs.sketch_gaussian_bf16 if op == "gaussian-bf16" else mihs.sketch_gaussian_fp8
+        fn = lambda: form(A, p.m, 3, SA=SA)
     elif op == "backward":
         v = W.randn((p.d,), seed=6, scale=0.01).to(dev)
         fn = lambda: mihs.backward_grads(A, b, x, v)

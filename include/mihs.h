@@ -140,6 +140,20 @@ int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda,
                               int64_t m, uint64_t seed, float* SA, int64_t ldsa,
                               void* stream);
 
+/* The same Gaussian sketch formed from fp8 e4m3 operands on the tensor
+ * cores (tcgen05.mma kind::f8f6f4, fp32 accumulation): every entry of S is
+ * rounded to e4m3, A is multiplied by the power of two 2^k that puts max|A|
+ * in [128, 256) (exact; one extra pass over A for the maximum; k ≤ 127) and
+ * rounded to e4m3 (round to nearest even, saturating), and the sum is
+ * multiplied by 2^−k and 1/√m.  e4m3 keeps 3 mantissa
+ * bits, so this sketch perturbs the preconditioner by a relative 2⁻⁴ of A's
+ * entries; it is what a handle storing SA in fp8 forms, and the guard of
+ * mihs_sketch_set_precision decides at which λ that storage is accepted.
+ * Arguments, scratch and errors as mihs_sketch_gaussian_bf16. */
+int mihs_sketch_gaussian_fp8(const float* A, int64_t n, int64_t d, int64_t lda,
+                             int64_t m, uint64_t seed, float* SA, int64_t ldsa,
+                             void* stream);
+
 /* Gradient step of Algorithm 1: g = Aᵀ(b − Ax) − λx, reading A once.
  *   b (n), x (d) inputs; g (d) output.  0 ≤ λ ≤ FLT_MAX (fp32 arithmetic).
  * Allocates stream-ordered scratch for the split-K partial sums (one d-vector
@@ -275,6 +289,8 @@ int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream);
  * mihs_resketch; the first call for a quantised precision allocates the
  * quantised copy (cudaMalloc).  MIHS_SA_FP32 switches back.  Sd estimation
  * (Algorithm 4) keeps using the fp32 SA.
+ * A Gaussian handle re-forms S·A from operands of the storage precision
+ * (mihs_sketch_gaussian_bf16 / _fp8) on every mihs_resketch.
  * Guard: each conversion also measures the rounding E = SA_q − SA (‖E‖_F²,
  * read back to the host, so this call and mihs_resketch synchronise the
  * stream for a quantised handle).  A solve (mihs_solve, _refined, _path,

@@ -36,6 +36,8 @@ Contents and the passage each follows:
   gaussian_sketch_bf16 . the Gaussian sketch from bf16-rounded S and A, summed
                           exactly (the operand format of the bf16 tensor-core
                           sketch; a format, not the paper's).
+  gaussian_sketch_fp8 .. the same from e4m3-rounded S and scaled A (round_e4m3,
+                          fp8_scale; the operand format of the fp8 sketch).
   quantize_sa .......... storage of SA in bf16, or fp8 e4m3 with one scale per
                           128 × 128 tile (a format, not the paper's: the
                           sketch only preconditions, Section 3.1); torch's
@@ -164,6 +166,42 @@ def gaussian_sketch_bf16(A: np.ndarray, m: int, seed: int) -> np.ndarray:
     n = A.shape[0]
     Z = gaussian_sketch_matrix(m, n, seed) * math.sqrt(m)
     return (round_bf16(Z) @ round_bf16(A)) / math.sqrt(m)
+
+
+def round_e4m3(x) -> np.ndarray:
+    """Round to the nearest fp8 e4m3 value (4 exponent bits with bias 7, 3
+    mantissa bits, no infinities: largest finite ±448, smallest subnormal
+    2⁻⁹), ties to even, magnitudes beyond 448 saturating to ±448 — through
+    torch's CPU cast of the fp32 value (clamped first); returned as fp64."""
+    import torch
+    t = torch.as_tensor(np.asarray(x, dtype=np.float32)).clamp(-448.0, 448.0)
+    return t.to(torch.float8_e4m3fn).to(torch.float64).numpy()
+
+
+def fp8_scale(A) -> tuple:
+    """The scale of A for e4m3 operands: the power of two s = 2^k with
+    max|A|·s in [128, 256) (k = 8 − e for max|A| = f·2^e, f ∈ [½, 1), capped
+    at 127; k = 0 for A = 0), so that scaling is exact and stays below e4m3's
+    448; returns (s, 1/s)."""
+    A32 = np.asarray(A, dtype=np.float32)
+    mx = float(np.max(np.abs(A32))) if A32.size else 0.0
+    k = min(8 - math.frexp(mx)[1], 127) if mx > 0 else 0
+    return np.float32(2.0 ** k), 2.0 ** -k
+
+
+def gaussian_sketch_fp8(A: np.ndarray, m: int, seed: int) -> np.ndarray:
+    """The Gaussian sketch formed from fp8 e4m3 operands (a format of the
+    preconditioner, not the paper's: the sketch only preconditions, Section
+    3.1): SA = (1/√m)·(1/s)·Z̃·Ã with Z̃ the N(0,1) matrix of
+    gaussian_sketch_rows (before the 1/√m) rounded to e4m3, Ã = e4m3(A·s)
+    and s the power of two of fp8_scale, the products summed exactly
+    (fp64)."""
+    A32 = np.asarray(A, dtype=np.float32)
+    n = A32.shape[0]
+    s, inv = fp8_scale(A32)
+    Z = gaussian_sketch_matrix(m, n, seed) * math.sqrt(m)
+    At = round_e4m3((A32 * s).astype(np.float32))
+    return (round_e4m3(Z) @ At) * inv / math.sqrt(m)
 
 
 def countsketch_hash(n: int, m: int, seed: int):

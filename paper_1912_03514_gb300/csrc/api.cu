@@ -526,23 +526,33 @@ int mihs_sketch_apply(const float* A, int64_t n, int64_t d, int64_t lda, int fam
   return rc;
 }
 
-int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
-                              float* SA, int64_t ldsa, void* stream) {
+static int gaussian_lowp(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
+                         int64_t ldsa, void* stream, int prec, const char* who) {
   set_error("");
-  int rc = check_matrix(A, n, d, lda, "mihs_sketch_gaussian_bf16");
+  int rc = check_matrix(A, n, d, lda, who);
   if (rc) return rc;
-  MIHS_ARG(SA != nullptr, "mihs_sketch_gaussian_bf16: null SA");
-  MIHS_ARG(m >= 1 && m <= n, "mihs_sketch_gaussian_bf16: m=%lld outside [1, n]", (long long)m);
-  MIHS_ARG(ldsa >= d, "mihs_sketch_gaussian_bf16: ldsa < d");
+  MIHS_ARG(SA != nullptr, "%s: null SA", who);
+  MIHS_ARG(m >= 1 && m <= n, "%s: m=%lld outside [1, n]", who, (long long)m);
+  MIHS_ARG(ldsa >= d, "%s: ldsa < d", who);
   if (!gaussian_tc_available()) {
-    set_error("mihs_sketch_gaussian_bf16: the tensor-core sketch is unavailable (no cuTensorMapEncodeTiled)");
+    set_error("%s: the tensor-core sketch is unavailable (no cuTensorMapEncodeTiled)", who);
     return MIHS_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   timing_begin(kTimerSketch, s);
-  rc = sketch_gaussian_tc(A, n, d, lda, m, seed, SA, ldsa, s, true);
+  rc = sketch_gaussian_tc(A, n, d, lda, m, seed, SA, ldsa, s, prec);
   timing_end(kTimerSketch, s);
   return rc;
+}
+
+int mihs_sketch_gaussian_bf16(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
+                              float* SA, int64_t ldsa, void* stream) {
+  return gaussian_lowp(A, n, d, lda, m, seed, SA, ldsa, stream, 1, "mihs_sketch_gaussian_bf16");
+}
+
+int mihs_sketch_gaussian_fp8(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
+                             float* SA, int64_t ldsa, void* stream) {
+  return gaussian_lowp(A, n, d, lda, m, seed, SA, ldsa, stream, 2, "mihs_sketch_gaussian_fp8");
 }
 
 int mihs_timing(int on) {
@@ -808,10 +818,13 @@ int mihs_resketch(mihs_sketch_t sk, const float* A, int64_t lda, uint64_t seed, 
   int rc = check_matrix(A, sk->n, sk->d, lda, "mihs_resketch");
   if (rc) return rc;
   sk->seed = seed;
-  // A handle whose SA is stored quantised forms a Gaussian S·A from bf16
-  // operands too (fp32 accumulation): the sketch only preconditions.
-  if (sk->family == MIHS_GAUSSIAN && sk->sa_prec != MIHS_SA_FP32)
+  // A handle whose SA is stored quantised forms a Gaussian S·A from operands
+  // of that precision too (bf16, or fp8 e4m3 with A scaled; fp32
+  // accumulation): the sketch only preconditions.
+  if (sk->family == MIHS_GAUSSIAN && sk->sa_prec == MIHS_SA_BF16)
     rc = mihs_sketch_gaussian_bf16(A, sk->n, sk->d, lda, sk->m, seed, sk->SA, sk->dp, stream);
+  else if (sk->family == MIHS_GAUSSIAN && sk->sa_prec == MIHS_SA_FP8E4M3)
+    rc = mihs_sketch_gaussian_fp8(A, sk->n, sk->d, lda, sk->m, seed, sk->SA, sk->dp, stream);
   else
     rc = mihs_sketch_apply(A, sk->n, sk->d, lda, sk->family, sk->m, seed, sk->SA, sk->dp, stream);
   if (rc || sk->sa_prec == MIHS_SA_FP32) return rc;

@@ -159,9 +159,10 @@ int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m
                     uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 // tcgen05 version of the Gaussian sketch (sketch_gaussian_tc.cu).
 bool gaussian_tc_available();
-// bf16 = true: S and A rounded to bf16 (kind::f16 MMAs, fp32 accumulation).
+// prec: 0 tf32 operands, 1 S and A rounded to bf16, 2 S and A·256/max|A|
+// rounded to fp8 e4m3 (the scale undone in the reduction).
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
-                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s, bool bf16 = false);
+                       uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s, int prec = 0);
 int gauss_tc_device_error(int* code);
 int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                        uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);

@@ -27,6 +27,10 @@
 // buffer that a small kernel sums in a fixed order and scales by 1/√m.
 // Every mbarrier wait is bounded; a wait that runs out records
 // MIHS_ERR_TIMEOUT, the block still frees its tensor memory and returns.
+// Operand precisions (the sketch only preconditions, Section 3.1): tf32
+// (32 K per 128-byte row), bf16 (64 K) or fp8 e4m3 (128 K; A scaled by the
+// power of two that puts max|A| in [128, 256) before rounding, the scale
+// undone exactly in the reduction).
 #include <cuda.h>
 
 #include <cmath>
@@ -48,20 +52,21 @@ constexpr int kThreads = (2 + kGenWarps + kTrWarps) * 32;  // warp 0: MMA, warp 
 constexpr uint32_t kSBytes = TM * TK * 4;       // one 128-row S tile: 16 KB
 constexpr uint32_t kABytes = TK * TN * 4;       // one 32-row fp32 A tile: 32 KB
 
-// Shape of one kernel variant.  BF: bf16 operands (64 K per 128-byte
-// swizzled row) or tf32 (32 K), so both use the same layout and descriptors.
+// Shape of one kernel variant.  PREC: 0 tf32 (32 K per 128-byte swizzled
+// row), 1 bf16 (64 K), 2 fp8 e4m3 (128 K): all use the same layout and
+// descriptors, and each MMA consumes 32 bytes of K.
 // MT: sketch-row tiles per block (two TMEM accumulators of 256 columns when
 // MT = 2, so that each staged and transposed A tile feeds twice the MMA
 // work — the kernel is bound by shared-memory traffic, not by the MMA).
 // Operand ring and staging ring (TMA → transposers) depths fill ≤ 227 KB.
-template <bool BF, int MT>
+template <int PREC, int MT>
 struct TcCfg {
-  static constexpr int KT = BF ? 64 : 32;        // K rows per operand stage
+  static constexpr int KT = 32 << PREC;          // K rows per operand stage
   static constexpr int NSLOT = KT / TK;          // 32-row TMA loads per stage
   static constexpr uint32_t SBytes = MT * kSBytes;
   static constexpr uint32_t StageBytes = SBytes + kABytes;
-  static constexpr int NSTAGE = MT == 1 ? (BF ? 2 : 3) : 2;
-  static constexpr int NSTG = MT == 1 ? (BF ? 4 : 2) : 3;
+  static constexpr int NSTAGE = MT == 1 ? (PREC > 0 ? 2 : 3) : 2;
+  static constexpr int NSTG = MT == 1 ? (PREC > 0 ? 4 : 2) : 3;
   static constexpr uint32_t TmemCols = 256u * MT;
   static constexpr size_t Smem = (size_t)NSTAGE * StageBytes + (size_t)NSTG * kABytes + 1024 /*align*/ +
                                  256 /*barriers*/;
@@ -84,6 +89,9 @@ constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (0u << 15) 
                                 ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (0u << 16) |
                                 ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// kind::f8f6f4 with both operands e4m3 (format 0).
+constexpr uint32_t kIdescFp8 = (1u << 4) | (0u << 7) | (0u << 10) | (0u << 15) | (0u << 16) |
+                               ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
@@ -101,6 +109,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescFp8), "r"(accumulate)
+      : "memory");
+}
+
+// Four fp32 values → four e4m3 bytes (round to nearest even, saturating to
+// ±448), the first in the lowest byte (the lowest K index).
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
 // Two fp32 values → one bf16x2 word (round to nearest even); `lo` lands in
@@ -209,15 +235,17 @@ struct GaussTcArgs {
   float* part;          // [gridDim.z][m][dp]
   int dp;
   int cn;               // blocks per cluster (= column tiles of A, gridDim.x)
+  const float* ascale;  // fp8: [0] = the power-of-two scale applied before rounding A, [1] = its inverse
 };
 
-// BF = false: tf32 operands (kind::tf32, 32 K per stage); BF = true: S and A
-// rounded to bf16 (kind::f16, 64 K per stage, two TMA loads of 32 rows).
+// PREC 0: tf32 operands (kind::tf32, 32 K per stage); 1: S and A rounded to
+// bf16 (kind::f16, 64 K per stage, two TMA loads of 32 rows); 2: S and the
+// scaled A rounded to e4m3 (kind::f8f6f4, 128 K per stage, four loads).
 // MT sketch-row tiles of 128 per block, one TMEM accumulator each.
-template <bool BF, int MT>
+template <int PREC, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
 gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a) {
-  using C = TcCfg<BF, MT>;
+  using C = TcCfg<PREC, MT>;
   constexpr int KT = C::KT;
   constexpr int NSLOT = C::NSLOT;  // TMA loads (staging slots) per operand stage
   constexpr int NSTAGE = C::NSTAGE;
@@ -295,7 +323,9 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
 #pragma unroll
           for (int t = 0; t < MT; ++t) {
             const uint64_t ad = smem_desc_sw128(sS + t * kSBytes + kk * 32, 16, 1024);
-            if constexpr (BF)
+            if constexpr (PREC == 2)
+              mma_fp8(tmem + 256u * t, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
+            else if constexpr (PREC == 1)
               mma_bf16(tmem + 256u * t, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
             else
               mma_tf32(tmem + 256u * t, ad, bd, (kb > 0 || kk > 0) ? 1u : 0u);
@@ -335,6 +365,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
   } else if (warp >= 2 + kGenWarps) {
     // ------------------------------------------------ A transposers: staging → K-major
     const int tt = threadIdx.x - (2 + kGenWarps) * 32;  // 0..127: columns tt, tt + 128
+    const float as = PREC == 2 ? a.ascale[0] : 1.f;
     bool stop = false;
     for (int kb = 0; kb < nkb && !stop; ++kb) {
       const int s = kb % NSTAGE;
@@ -357,7 +388,20 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
         for (int h = 0; h < 2; ++h) {
           const int c = tt + 128 * h;
           unsigned char* row = dstA + (c >> 3) * 1024 + (c & 7) * 128;
-          if constexpr (BF) {
+          if constexpr (PREC == 2) {
+            // 16-byte chunk ch = 2·sl + hh holds K = 16ch … 16ch + 15 as e4m3
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const float* r = src + (size_t)(16 * hh) * TN + c;
+              uint4 v;
+              v.x = pack_e4m3x4(r[0 * TN] * as, r[1 * TN] * as, r[2 * TN] * as, r[3 * TN] * as);
+              v.y = pack_e4m3x4(r[4 * TN] * as, r[5 * TN] * as, r[6 * TN] * as, r[7 * TN] * as);
+              v.z = pack_e4m3x4(r[8 * TN] * as, r[9 * TN] * as, r[10 * TN] * as, r[11 * TN] * as);
+              v.w = pack_e4m3x4(r[12 * TN] * as, r[13 * TN] * as, r[14 * TN] * as, r[15 * TN] * as);
+              const int ch = 2 * sl + hh;
+              *reinterpret_cast<uint4*>(row + ((ch ^ (c & 7)) << 4)) = v;
+            }
+          } else if constexpr (PREC == 1) {
             // 16-byte chunk ch = 4·sl + cc holds K = 8ch … 8ch + 7 as bf16
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
@@ -417,7 +461,29 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
         const int gt = g_lo + (e >> 3), c = e & 7;
         const int gi = i0 + gt;
         uint4 out = make_uint4(0u, 0u, 0u, 0u);
-        if constexpr (BF) {
+        if constexpr (PREC == 2) {
+          // chunk c: K = kbase + 16c … + 15, four Philox counters
+          const int j0 = kbase + 16 * c;
+          if (gi < a.m && j0 < kb1) {
+            float z[16];
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+              const uint4 w = philox4x32_10(make_uint4((uint32_t)((j0 >> 2) + hh), (uint32_t)gi, kTagGaussian, 0u),
+                                            a.k0, a.k1);
+              const float2 za = box_muller_fast(w.x, w.y);
+              const float2 zb = box_muller_fast(w.z, w.w);
+              z[4 * hh + 0] = za.x;
+              z[4 * hh + 1] = za.y;
+              z[4 * hh + 2] = zb.x;
+              z[4 * hh + 3] = zb.y;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (j0 + q >= kb1) z[q] = 0.f;
+            out = make_uint4(pack_e4m3x4(z[0], z[1], z[2], z[3]), pack_e4m3x4(z[4], z[5], z[6], z[7]),
+                             pack_e4m3x4(z[8], z[9], z[10], z[11]), pack_e4m3x4(z[12], z[13], z[14], z[15]));
+          }
+        } else if constexpr (PREC == 1) {
           // chunk c: K = kbase + 8c … + 7, two Philox counters
           const int j0 = kbase + 8 * c;
           if (gi < a.m && j0 < kb1) {
@@ -505,15 +571,53 @@ done:
   }
 }
 
-// SA[i][c] = scale · Σ_z part[z][i][c] (fixed order).
+// SA[i][c] = scale · (ascale ? ascale[1] : 1) · Σ_z part[z][i][c] (fixed order).
 __global__ void gauss_tc_reduce_kernel(const float* __restrict__ part, int KS, int m, int d, int dp,
-                                       float scale, float* __restrict__ SA, long long ldsa) {
+                                       float scale, const float* __restrict__ ascale, float* __restrict__ SA,
+                                       long long ldsa) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)m * d) return;
   const int i = (int)(idx / d), c = (int)(idx - (long long)i * d);
   float s = 0.f;
   for (int z = 0; z < KS; ++z) s += part[((size_t)z * m + i) * dp + c];
+  if (ascale != nullptr) s *= ascale[1];
   SA[(long long)i * ldsa + c] = s * scale;
+}
+
+// max |A| over the matrix (fp32 bit patterns of non-negative values order as
+// unsigned integers, so an atomic max on them is exact and order-free).
+// max|A| over the n×d matrix (fp32 bits, atomicMax: the order of non-negative
+// floats is that of their bit patterns).  One warp per row at a time, 16-byte
+// loads when the rows allow them (vec: lda % 4 == 0, A 16-byte aligned).
+__global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ A, long long n, int d, long long lda,
+                                                     int vec, unsigned int* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long wpb = blockDim.x >> 5;
+  float mx = 0.f;
+  const int d4 = vec ? (d & ~3) : 0;
+  for (long long i = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (long long)gridDim.x * wpb) {
+    const float* row = A + i * lda;
+    for (int j = 4 * lane; j < d4; j += 128) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(row + j));
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int j = d4 + lane; j < d; j += 32) mx = fmaxf(mx, fabsf(__ldcs(row + j)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+// ascale[0] = 2^(8−e) with max|A| = f·2^e, f ∈ [½, 1), so that max|A|·ascale[0]
+// lies in [128, 256) (e4m3 reaches 448) and the scaling is exact; ascale[1]
+// its inverse.  The exponent is capped at 127 (a max|A| below 2⁻¹¹⁹ then
+// maps below 128); A = 0 takes the scale 1.
+__global__ void ascale_kernel(const unsigned int* __restrict__ mx, float* __restrict__ ascale) {
+  const float m = __uint_as_float(*mx);
+  int e = 0;
+  if (m > 0.f) (void)frexpf(m, &e);
+  const int k = m > 0.f ? min(8 - e, 127) : 0;
+  ascale[0] = ldexpf(1.0f, k);
+  ascale[1] = ldexpf(1.0f, -k);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -539,7 +643,7 @@ EncodeTiledFn encode_fn() {
 bool gaussian_tc_available() { return encode_fn() != nullptr; }
 
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
-                       int64_t ldsa, cudaStream_t s, bool bf16) {
+                       int64_t ldsa, cudaStream_t s, int prec) {
   using KernFn = void (*)(const CUtensorMap, const GaussTcArgs);
   // Two 128-row sketch tiles per block whenever there are two to share the
   // staged A tiles (MIHS_GAUSSIAN_MT=1 keeps one).
@@ -549,11 +653,13 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   }();
   const int tm = (int)((m + TM - 1) / TM);
   const int MT = (tm >= 2 && !force_mt1) ? 2 : 1;
-  const KernFn kern = bf16 ? (MT == 2 ? gauss_tc_kernel<true, 2> : gauss_tc_kernel<true, 1>)
-                           : (MT == 2 ? gauss_tc_kernel<false, 2> : gauss_tc_kernel<false, 1>);
-  const size_t kSmemBytes = bf16 ? (MT == 2 ? TcCfg<true, 2>::Smem : TcCfg<true, 1>::Smem)
-                                 : (MT == 2 ? TcCfg<false, 2>::Smem : TcCfg<false, 1>::Smem);
-  const int KT = bf16 ? TcCfg<true, 1>::KT : TcCfg<false, 1>::KT;
+  const KernFn kern = prec == 2   ? (MT == 2 ? gauss_tc_kernel<2, 2> : gauss_tc_kernel<2, 1>)
+                     : prec == 1 ? (MT == 2 ? gauss_tc_kernel<1, 2> : gauss_tc_kernel<1, 1>)
+                                 : (MT == 2 ? gauss_tc_kernel<0, 2> : gauss_tc_kernel<0, 1>);
+  const size_t kSmemBytes = prec == 2   ? (MT == 2 ? TcCfg<2, 2>::Smem : TcCfg<2, 1>::Smem)
+                            : prec == 1 ? (MT == 2 ? TcCfg<1, 2>::Smem : TcCfg<1, 1>::Smem)
+                                        : (MT == 2 ? TcCfg<0, 2>::Smem : TcCfg<0, 1>::Smem);
+  const int KT = 32 << prec;
   const int tmb = (tm + MT - 1) / MT;  // blocks along the sketch rows
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) {
@@ -615,8 +721,20 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   KS = (n + rows_per_split - 1) / rows_per_split;
   const int dp = (int)round_up(d, 4);
   StreamScratch scratch;
-  int rc = scratch.alloc(sizeof(float) * (size_t)KS * m * dp, s);
+  int rc = scratch.alloc(sizeof(float) * (size_t)KS * m * dp + 64, s);
   if (rc) return rc;
+  float* ascale = nullptr;
+  if (prec == 2) {  // the scale of A for e4m3: one pass over A for max |A|
+    unsigned int* mx = reinterpret_cast<unsigned int*>(static_cast<float*>(scratch.p) + (size_t)KS * m * dp);
+    ascale = reinterpret_cast<float*>(mx) + 4;
+    MIHS_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
+    const int vec = (lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0) ? 1 : 0;
+    absmax_kernel<<<(unsigned)(4 * num_sms()), 256, 0, s>>>(A, n, (int)d, lda, vec, mx);
+    MIHS_CHECK_LAUNCH();
+    ascale_kernel<<<1, 1, 0, s>>>(mx, ascale);
+    MIHS_CHECK_LAUNCH();
+    count_launch(2);
+  }
   GaussTcArgs args;
   args.n = (int)n;
   args.d = (int)d;
@@ -627,6 +745,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   args.part = static_cast<float*>(scratch.p);
   args.dp = dp;
   args.cn = tn;
+  args.ascale = ascale;
   {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -644,7 +763,7 @@ int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_
   }
   const long long tot = (long long)m * d;
   gauss_tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      args.part, (int)KS, (int)m, (int)d, dp, (float)(1.0 / std::sqrt((double)m)), SA, ldsa);
+      args.part, (int)KS, (int)m, (int)d, dp, (float)(1.0 / std::sqrt((double)m)), ascale, SA, ldsa);
   MIHS_CHECK_LAUNCH();
   count_launch(2);
   return MIHS_OK;

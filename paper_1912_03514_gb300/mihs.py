@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
         "mihs_copy_to_device": (_int, [_vp, _vp, _i64, _vp]),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_sketch_gaussian_bf16": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
+        "mihs_sketch_gaussian_fp8": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
         "mihs_gradient": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_gradient_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _dbl, _vp, _vp]),
         "mihs_aab_solve": (_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _dbl, _int, _vp, _vp, _vp]),
@@ -230,6 +231,21 @@ def sketch_gaussian_bf16(A: torch.Tensor, m: int, seed: int, SA: torch.Tensor | 
     if (mm, dd) != (m, d):
         raise ValueError("SA has the wrong shape")
     _check(lib().mihs_sketch_gaussian_bf16(pa, n, d, lda, m, seed & (2**64 - 1), ps, ldsa, _stream(stream)))
+    return SA
+
+
+def sketch_gaussian_fp8(A: torch.Tensor, m: int, seed: int, SA: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """The Gaussian SA = S·A formed from e4m3-rounded S and A·2^k, 2^k the
+    power of two putting max|A| in [128, 256) (fp32 accumulation, the scale
+    undone)."""
+    pa, n, d, lda = _mat(A, "A")
+    if SA is None:
+        SA = torch.empty(m, d, dtype=torch.float32, device=A.device)
+    ps, mm, dd, ldsa = _mat(SA, "SA")
+    if (mm, dd) != (m, d):
+        raise ValueError("SA has the wrong shape")
+    _check(lib().mihs_sketch_gaussian_fp8(pa, n, d, lda, m, seed & (2**64 - 1), ps, ldsa, _stream(stream)))
     return SA
 
 

@@ -194,6 +194,87 @@ def test_gaussian_bf16_sketch_matches_oracle(n, d, m):
     assert torch.equal(SA, SA2), "not deterministic"
 
 
+# -------------------------------------------- Gaussian sketch from fp8 operands
+def _z_window(Z):
+    """Half-width of the interval around the fp64 N(0,1) entry z that holds
+    the kernel's fast-intrinsic Box–Muller value: CUDA documents the fast
+    log's absolute error as 2⁻²¹·⁴¹ on [½, 2] (3 ulp elsewhere) and the fast
+    sin/cos's as 2⁻²¹·⁴¹ on [−π, π], so t = −2 ln u₁ moves by ≤ 2⁻²⁰ and
+    r = √t by ≤ min(√2⁻²⁰, 2⁻²⁰/r) ≤ min(2⁻¹⁰, 2⁻²⁰/|z|); 2⁻¹⁶(1 + |z|)
+    covers the rest (angle, ulp roundings) with room."""
+    a = np.abs(Z)
+    return 2.0 ** -16 * (1.0 + a) + np.minimum(2.0 ** -10, 2.0 ** -20 / np.maximum(a, 2.0 ** -40))
+
+
+@pytest.mark.parametrize("n,d,m", [(4096, 256, 256), (5000, 700, 300), (2049, 1500, 129), (100, 520, 40),
+                                   (12000, 2048, 260), (777, 33, 17)])
+def test_gaussian_fp8_sketch_matches_oracle(n, d, m):
+    """S·A from e4m3 operands on the tensor cores (kind::f8f6f4) against
+    the oracle's exact sum of the same rounded operands.  The scaled A is
+    rounded identically on both sides (an exact power-of-two scale, then
+    round-to-nearest-even); an entry of S within the fast intrinsics' error
+    of an e4m3 rounding boundary may take either neighbour, which the bound
+    carries entry by entry (ΔZ); products are exact in fp32, sums carry γ_K,
+    the two scalings 3u."""
+    lda = (d + 3) // 4 * 4
+    A = W.padded_matrix(n, d, lda, seed=n + 7 * d + 8)
+    seed = 0xF8 + n
+    Ad = A.to(DEV).as_strided((n, d), (lda, 1))
+    SA = mihs.sketch_gaussian_fp8(Ad, m, seed)
+    SA2 = mihs.sketch_gaussian_fp8(Ad, m, seed)
+    torch.cuda.synchronize()
+    An = A[:, :d].numpy()
+    ref = o.gaussian_sketch_fp8(An, m, seed)
+    s, inv = o.fp8_scale(An)
+    A8 = np.abs(o.round_e4m3(An * s))
+    Z = o.gaussian_sketch_matrix(m, n, seed) * math.sqrt(m)
+    h = _z_window(Z)
+    lo, hi, mid = o.round_e4m3(Z - h), o.round_e4m3(Z + h), o.round_e4m3(Z)
+    dz = np.maximum(np.abs(hi - mid), np.abs(mid - lo))
+    zmax = np.maximum(np.abs(lo), np.abs(hi))
+    c = inv / math.sqrt(m)
+    bound = ((gamma(n + 16) + 4 * U32) * (zmax @ A8) + (1 + 4 * U32) * (dz @ A8)) * c + 1e-30
+    got = SA.double().cpu().numpy()
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound)}"
+    assert torch.equal(SA, SA2), "not deterministic"
+    # the operands really are e4m3: SA differs from the bf16-operand sketch
+    # by about 2⁻⁴ of |S|·|A|, far more than the bf16 rounding
+    SAb = mihs.sketch_gaussian_bf16(Ad, m, seed).double().cpu().numpy()
+    assert np.max(np.abs(got - SAb)) > 1e-3 * np.max(np.abs(SAb))
+
+
+def test_gaussian_fp8_sketch_of_a_scaled_matrix_and_of_zero():
+    """A power-of-two rescaling of A commutes with the fp8 sketch bit for
+    bit (the scale is a power of two chosen from max|A|), and A = 0 gives
+    SA = 0."""
+    n, d, m = 3000, 96, 64
+    A = W.randn((n, d), 5).to(DEV)
+    SA = mihs.sketch_gaussian_fp8(A, m, 77)
+    SA2 = mihs.sketch_gaussian_fp8(A * 2.0 ** -30, m, 77)
+    SA0 = mihs.sketch_gaussian_fp8(torch.zeros_like(A), m, 77)
+    torch.cuda.synchronize()
+    assert torch.equal(SA * 2.0 ** -30, SA2)
+    assert torch.count_nonzero(SA0).item() == 0
+
+
+def test_gaussian_handle_with_fp8_storage_forms_sa_in_fp8():
+    """A Gaussian handle stored in fp8 re-forms SA from e4m3 operands on
+    resketch (its fp32 SA, which it then stores in fp8, is the row-level
+    call's result byte for byte), and the refined solve reaches 1e-10."""
+    p = W.problem_small()
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    xs = o.exact_solve(p.A.numpy(), p.b.numpy(), p.lam, refine=3, extended=True)
+    with mihs.Sketch(A, "gaussian", p.m, seed=23) as sk:
+        sk.set_precision("fp8")
+        sk.resketch(A, 23)
+        sa8 = sk.sa().clone()
+        x, info = sk.solve_refined(A, b, p.lam, p.sd, tol=1e-13, max_outer=300)
+    assert torch.equal(sa8, mihs.sketch_gaussian_fp8(A, p.m, 23))
+    assert info.converged and o.rel_error(x.cpu().numpy(), xs) <= 1e-10, info
+
+
 def test_gaussian_handle_with_bf16_storage_forms_sa_in_bf16():
     """A Gaussian handle stored in bf16 re-forms SA from bf16 operands on
     resketch (the same bytes as the row-level call), and the refined solve

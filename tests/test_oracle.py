@@ -730,3 +730,41 @@ def test_quantised_sa_spectrum_reading():
         out[prec] = (est / lam, mu.max())
     assert out["bf16"][0] <= 0.5 and out["bf16"][1] < edge, out
     assert out["fp8"][0] > 0.5 and out["fp8"][1] > edge, out
+
+
+def test_round_e4m3_against_the_format():
+    """e4m3: 3 mantissa bits, bias 7, largest finite 448, smallest subnormal
+    2⁻⁹; ties to even; saturation at ±448."""
+    cases = [(1.0, 1.0), (1.0625, 1.0), (1.1875, 1.25), (17.0, 16.0), (19.0, 20.0), (448.0, 448.0),
+             (500.0, 448.0), (-1000.0, -448.0), (2.0 ** -9, 2.0 ** -9), (2.0 ** -10, 0.0),
+             (3 * 2.0 ** -10, 2.0 ** -8), (0.3, 0.3125), (-2.2, -2.25), (240.0, 240.0), (232.0, 224.0)]
+    got = o.round_e4m3([c[0] for c in cases])
+    assert list(got) == [c[1] for c in cases], list(zip([c[0] for c in cases], got))
+
+
+def test_gaussian_sketch_fp8_by_loops():
+    """The fp8-operand sketch entry by entry: the N(0,1) entries of
+    gaussian_sketch_rows rounded to e4m3, A scaled by the power of two that
+    puts max|A| in [128, 256) and rounded to e4m3, products summed exactly
+    (math.fsum), the scale and 1/√m undone."""
+    rng = np.random.default_rng(3)
+    n, d, m, seed = 37, 5, 3, 99
+    A = (rng.standard_normal((n, d)) * 0.013).astype(np.float32)
+    got = o.gaussian_sketch_fp8(A, m, seed)
+    mx = float(np.max(np.abs(A)))
+    k = 0
+    while mx * 2.0 ** k < 128.0:
+        k += 1
+    assert 128.0 <= mx * 2.0 ** k < 256.0
+    Z = o.gaussian_sketch_rows(np.arange(m), n, m, seed) * math.sqrt(m)
+    for i in range(m):
+        for j in range(d):
+            terms = [float(o.round_e4m3(Z[i, kk])) * float(o.round_e4m3(A[kk, j] * 2.0 ** k)) for kk in range(n)]
+            want = math.fsum(terms) * 2.0 ** -k / math.sqrt(m)
+            assert got[i, j] == pytest.approx(want, rel=1e-14, abs=1e-18), (i, j)
+    # the scale for A = 0, a power of two above 1, and a tiny maximum
+    assert o.fp8_scale(np.zeros((2, 2))) == (1.0, 1.0)
+    assert o.fp8_scale(np.array([[3.0]])) == (64.0, 1.0 / 64)
+    assert o.fp8_scale(np.array([[256.0]])) == (0.5, 2.0)
+    s, inv = o.fp8_scale(np.array([[1e-40]], dtype=np.float32))
+    assert s == np.float32(2.0 ** 127) and inv == 2.0 ** -127
