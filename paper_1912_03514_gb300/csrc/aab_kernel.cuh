@@ -553,9 +553,12 @@ __global__ void __launch_bounds__(kThreads, 1) aab_cluster_kernel(const AabParam
     const float g0 = g0known ? gnorm0 : theta1;
     if (hist_ != nullptr && rank == 0 && tid == 0 && outer < kHistCap) hist_[outer] = theta1;
     const bool bad = !(theta1 <= 3.0e38f);
-    // A refinement correction's gradient is approximate: it never stops the solve.
+    // A refinement correction's gradient is approximate: it never stops the
+    // solve; nor does a refinement solve's plain fp32 gradient (phase 0), whose
+    // rounding floor lies above the tolerances refinement is asked for (it
+    // can round to zero near the solution): only a compensated one certifies.
     const bool correction = phase == 1 && corr && !refresh;
-    const bool conv = tol > 0.f && theta1 <= tol * g0 && !correction;
+    const bool conv = tol > 0.f && theta1 <= tol * g0 && !correction && phase != 0;
     const bool capped = outer >= max_outer;
     if (rank == 0 && tid == 0) refine_step_update(ctl_, phase, refresh, corr, theta1, g0, tol, switch_tol);
     if (bad || conv || capped) {

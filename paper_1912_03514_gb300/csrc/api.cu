@@ -490,7 +490,10 @@ int mihs_device_status(int* code) {
   int gr = 0;
   rc = aab_grid_device_error(&gr);
   if (rc) return rc;
-  *code = a ? a : (g ? g : (dd ? dd : (pa ? pa : (ab ? ab : gr))));
+  int sr = 0;
+  rc = srht_device_error(&sr);
+  if (rc) return rc;
+  *code = a ? a : (g ? g : (dd ? dd : (pa ? pa : (ab ? ab : (gr ? gr : sr)))));
   return MIHS_OK;
 }
 

@@ -1,6 +1,7 @@
 // Host-side launchers shared between the translation units of libmihs.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -159,6 +160,13 @@ int sketch_gaussian(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m
                     uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 // tcgen05 version of the Gaussian sketch (sketch_gaussian_tc.cu).
 bool gaussian_tc_available();
+// A tiled tensor map over the rows × cols fp32 matrix A (row pitch ld
+// elements, 16-byte aligned, ld·4 a multiple of 16), box box_cols × box_rows,
+// no swizzle, zero fill out of bounds, L2 promotion of 128 or 256 bytes.
+// UNSUPPORTED without the driver entry point or when the driver rejects the
+// layout.
+int encode_tmap_2d_f32(CUtensorMap* map, const float* A, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                       int box_rows, int l2_promotion);
 // prec: 0 tf32 operands, 1 S and A rounded to bf16, 2 S and A·256/max|A|
 // rounded to fp8 e4m3 (the scale undone in the reduction).
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
@@ -168,6 +176,7 @@ int sketch_countsketch(const float* A, int64_t n, int64_t d, int64_t lda, int64_
                        uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
 int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m,
                 uint64_t seed, float* SA, int64_t ldsa, cudaStream_t s);
+int srht_device_error(int* code);
 
 // ---- statistical dimension (hutchinson.cu) ----------------------------------
 // Algorithm 4; synchronises `s` and writes the estimate to *sd_out (host).

@@ -181,15 +181,7 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // Box–Muller with CUDA's fast intrinsics (its results are rounded to tf32,
 // 2⁻¹¹ relative, so the intrinsics' ~2⁻²¹ error is invisible): the same
@@ -641,6 +633,21 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 bool gaussian_tc_available() { return encode_fn() != nullptr; }
+
+int encode_tmap_2d_f32(CUtensorMap* map, const float* A, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                       int box_rows, int l2_promotion) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return MIHS_ERR_UNSUPPORTED;
+  const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim, gstride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         l2_promotion == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? MIHS_OK : MIHS_ERR_UNSUPPORTED;
+}
 
 int sketch_gaussian_tc(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed, float* SA,
                        int64_t ldsa, cudaStream_t s, int prec) {

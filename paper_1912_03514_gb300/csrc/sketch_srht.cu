@@ -13,7 +13,15 @@
 // and adds the signed sampled rows into an m×32 accumulator kept in shared
 // memory.  A is read once (O(nd log B) additions on the SIMT pipes); the
 // cross-block combine costs O(m·d·n_p/B).
+//
+// Pipelined form (srht_tma_kernel, n > 256 with 16-byte aligned rows): B =
+// 512, a producer warp loads each 512-row × 32-column unit with two TMA
+// tile loads into a two-deep shared-memory ring (rows past n read as zeros),
+// and 16 consumer warps transform one unit in place while the next one is in
+// flight.  Blocks of H·D·A that lie wholly in the zero padding (rows ≥ n) are
+// skipped: they add nothing.
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -168,6 +176,169 @@ __global__ void __launch_bounds__(kThreads, 1) srht_block_kernel(const SrhtArgs 
   }
 }
 
+__device__ int g_srht_error = 0;
+
+constexpr int kTB = 512;                        // rows per unit of the pipelined form
+constexpr int kTL1 = 5, kTL2 = 4;               // B = 2^5 · 2^4
+constexpr int kTBoxRows = 256;                  // rows per TMA tile load
+constexpr int kTNBuf = 2;                       // ring depth
+constexpr uint32_t kTUnitBytes = kTB * kW * 4;  // 64 KB
+constexpr int kTCons = 16;                      // consumer warps (one per stage-1 row class)
+constexpr int kTThreads = (kTCons + 1) * 32;    // + the producer warp
+
+__host__ __device__ constexpr size_t srht_tma_smem(int m, bool acc_in_smem) {
+  return 128 /*align*/ + (size_t)kTNBuf * kTUnitBytes + 64 /*barriers, flags*/ + 8 * (size_t)m +
+         (acc_in_smem ? (size_t)m * kW * 4 : 0);
+}
+
+// kTCons consumer warps and one producer; the m × 32 accumulator lives in
+// shared memory (acc_in_smem) or in the block's global partial slot.  (A
+// register accumulator, 8 consumer warps owning m/8 rows each, measured
+// slower: the sampled-row gathers then form one long dependent chain per
+// warp.)
+__global__ void __launch_bounds__(kTThreads, 1) srht_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                 const SrhtArgs a) {
+  constexpr int NC = kTCons, NT = NC * 32;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);  // TMA destinations: 128-byte aligned
+  float* ring = reinterpret_cast<float*>(base);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kTNBuf * kTUnitBytes);
+  uint64_t* empty = full + kTNBuf;
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(empty + kTNBuf);
+  // sampled row r: {offset of r_lo = r mod B in a unit (floats), r_hi = ⌊r/B⌋}
+  int2* rows_s = reinterpret_cast<int2*>(base + (size_t)kTNBuf * kTUnitBytes + 64);
+  float* acc_s = reinterpret_cast<float*>(rows_s + a.m);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const long long u0 = (long long)blockIdx.x * a.units / gridDim.x;
+  const long long u1 = (long long)(blockIdx.x + 1) * a.units / gridDim.x;
+  if (u0 >= u1) return;
+  if (tid == 0) {
+    for (int q = 0; q < kTNBuf; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    *abort_flag = 0u;
+    fence_mbar_init();
+  }
+  for (int i = tid; i < a.m; i += blockDim.x) {
+    const int r = a.rows[i];
+    rows_s[i] = make_int2((r & (kTB - 1)) * kW, r >> a.LB);
+  }
+  __syncthreads();
+
+  if (warp == NC) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      for (long long u = u0; u < u1; ++u) {
+        const int j = (int)(u - u0), q = j % kTNBuf;
+        if (j >= kTNBuf && !mbar_wait(&empty[q], ((uint32_t)(j / kTNBuf) & 1u) ^ 1u, kWaitLimitNs)) {
+          atomicExch(&g_srht_error, MIHS_ERR_TIMEOUT);
+          break;
+        }
+        const long long slice = u / a.nblk;
+        const int blk = (int)(u - slice * a.nblk);
+        float* dst = ring + (size_t)q * (kTB * kW);
+        mbar_arrive_expect_tx(&full[q], kTUnitBytes);
+        for (int h = 0; h < kTB / kTBoxRows; ++h)
+          tma_load_2d(dst + h * kTBoxRows * kW, &tmap, (int)slice * kW, blk * kTB + h * kTBoxRows, &full[q]);
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  constexpr int N1 = 1 << kTL1, N2 = 1 << kTL2;
+  const size_t slot_elems = (size_t)a.m * kW;
+  float* part_base = a.partial + (size_t)blockIdx.x * a.smax * slot_elems;
+  int slot = 0;
+  float* acc = a.acc_in_smem ? acc_s : part_base;
+  for (size_t e = tid; e < slot_elems; e += NT) acc[e] = 0.f;
+  long long cur_slice = u0 / a.nblk;
+  const int nwords = (a.n + 31) >> 5;
+  named_sync(1, NT);
+
+  for (long long u = u0; u < u1; ++u) {
+    const int j = (int)(u - u0), q = j % kTNBuf;
+    const long long slice = u / a.nblk;
+    const int blk = (int)(u - slice * a.nblk);
+    if (slice != cur_slice) {  // flush the finished slice into its slot
+      float* dst = part_base + (size_t)slot * slot_elems;
+      if (a.acc_in_smem) {
+        for (size_t e = tid; e < slot_elems; e += NT) {
+          dst[e] = acc[e];
+          acc[e] = 0.f;
+        }
+      }
+      ++slot;
+      if (!a.acc_in_smem) {
+        acc = part_base + (size_t)slot * slot_elems;
+        for (size_t e = tid; e < slot_elems; e += NT) acc[e] = 0.f;
+      }
+      cur_slice = slice;
+      named_sync(1, NT);
+    }
+    // One thread waits (bounded) for the unit; every consumer takes its verdict.
+    if (tid == 0 && !mbar_wait(&full[q], (uint32_t)(j / kTNBuf) & 1u, kWaitLimitNs)) {
+      atomicExch(&g_srht_error, MIHS_ERR_TIMEOUT);
+      *abort_flag = 1u;
+    }
+    named_sync(1, NT);
+    if (*abort_flag) return;
+    float* Y = ring + (size_t)q * (kTB * kW);
+    // D: word w of the unit's 16 sign words covers rows 32w … 32w + 31, so
+    // row t + 16k (k = 2w + h) is bit t + 16h of word w: gathered into two
+    // masks, bit w of neg_h = the sign of row t + 16(2w + h).
+    const int wi = blk * (kTB / 32) + (lane & 15);
+    const uint32_t sw = (lane < 16 && wi < nwords) ? __ldg(a.signs + wi) : 0u;
+
+    // Stage 1 (with D): rows t + 16k, k = 0 … 31 (the high 5 bits of the row).
+    for (int t = warp; t < N2; t += NC) {
+      const uint32_t neg0 = __ballot_sync(0xffffffffu, (sw >> t) & 1u);
+      const uint32_t neg1 = __ballot_sync(0xffffffffu, (sw >> (t + 16)) & 1u);
+      float x[N1];
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const uint32_t nm = (k & 1) ? neg1 : neg0;
+        const uint32_t flip = (nm << (31 - (k >> 1))) & 0x80000000u;
+        x[k] = __uint_as_float(__float_as_uint(Y[(t + (k << kTL2)) * kW + lane]) ^ flip);
+      }
+      fwht_reg<N1>(x);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) Y[(t + (k << kTL2)) * kW + lane] = x[k];
+    }
+    named_sync(1, NT);
+    // Stage 2: rows 16t + k, k = 0 … 15 (the low 4 bits).
+    for (int t = warp; t < N1; t += NC) {
+      float y[N2];
+#pragma unroll
+      for (int k = 0; k < N2; ++k) y[k] = Y[((t << kTL2) + k) * kW + lane];
+      fwht_reg<N2>(y);
+#pragma unroll
+      for (int k = 0; k < N2; ++k) Y[((t << kTL2) + k) * kW + lane] = y[k];
+    }
+    named_sync(1, NT);
+    // Signed sampled rows into the accumulator: row r = (r_hi, r_lo) takes
+    // entry r_lo of this block's transform with the sign (−1)^popc(r_hi ∧ blk).
+    const float* Yl = Y + lane;
+    float* accl = acc + lane;
+#pragma unroll 4
+    for (int i = warp; i < a.m; i += NC) {
+      const int2 r = rows_s[i];
+      const uint32_t flip = (uint32_t)__popc(r.y & blk) << 31;
+      accl[(size_t)i * kW] += __uint_as_float(__float_as_uint(Yl[r.x]) ^ flip);
+    }
+    fence_async_shared();            // this thread's writes to the unit → before the next TMA write
+    named_sync(1, NT);
+    if (tid == 0) mbar_arrive(&empty[q]);
+  }
+  if (a.acc_in_smem) {
+    float* dst = part_base + (size_t)slot * slot_elems;
+    for (size_t e = tid; e < slot_elems; e += NT) dst[e] = acc[e];
+  }
+}
+
 // SA[i][slice·32 + c] = (1/√m) Σ_b partial[b][slice − first_slice(b)][i][c],
 // summed over the blocks b whose unit range meets the slice, in order of b.
 __global__ void __launch_bounds__(256)
@@ -180,9 +351,14 @@ srht_reduce_kernel(const float* __restrict__ partial, int NB, int smax, long lon
   if (i >= m || c >= d) return;
   const long long s0 = (long long)slice * nblk, s1 = s0 + nblk;
   float s = 0.f;
-  for (int b = 0; b < NB; ++b) {
+  // Blocks b own units [⌊b·units/NB⌋, ⌊(b+1)·units/NB⌋): start one block below
+  // the owner of unit s0 and stop past the slice, in order of b.
+  int b = (int)((s0 * NB) / units);
+  if (b > 0) --b;
+  for (; b < NB; ++b) {
     const long long u0 = (long long)b * units / NB, u1 = (long long)(b + 1) * units / NB;
-    if (u1 <= s0 || u0 >= s1 || u0 >= u1) continue;
+    if (u0 >= s1) break;
+    if (u1 <= s0 || u0 >= u1) continue;
     const int slot = (int)(slice - u0 / nblk);
     s += partial[(((size_t)b * smax + slot) * m + i) * kW + lane];
   }
@@ -209,13 +385,35 @@ KernelFn pick_kernel(int LB) {
 
 }  // namespace
 
+int srht_device_error(int* code) {
+  int v = 0, zero = 0;
+  MIHS_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_srht_error, sizeof(int)));
+  if (v != 0) MIHS_CUDA_TRY(cudaMemcpyToSymbol(g_srht_error, &zero, sizeof(int)));
+  *code = v;
+  return MIHS_OK;
+}
+
 int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
                 float* SA, int64_t ldsa, cudaStream_t s) {
   int L = 0;
   while ((1LL << L) < n) ++L;
-  const int LB = L < kMaxLB ? L : kMaxLB;
+  int dev_max = 0, dev = 0;
+  MIHS_CUDA_TRY(cudaGetDevice(&dev));
+  MIHS_CUDA_TRY(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // The pipelined form needs n > 256, TMA-compatible rows and room for its
+  // ring (the accumulator goes to global memory when it does not fit too).
+  static const bool force_plain = [] {
+    const char* e = std::getenv("MIHS_SRHT_PLAIN");
+    return e != nullptr && std::atoi(e) == 1;
+  }();
+  CUtensorMap tmap;
+  const bool tma = !force_plain && L >= 9 && lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0 &&
+                   srht_tma_smem((int)m, false) <= (size_t)dev_max &&
+                   encode_tmap_2d_f32(&tmap, A, n, d, lda, kW, kTBoxRows, 128) == MIHS_OK;
+  const int LB = tma ? 9 : (L < kMaxLB ? L : kMaxLB);
   const int B = 1 << LB;
-  const int nblk = (int)((1LL << L) / B);
+  // n_p/B blocks of rows; the pipelined form skips those wholly past n.
+  const int nblk = tma ? (int)((n + B - 1) / B) : (int)((1LL << L) / B);
   const int ncs = (int)((d + kW - 1) / kW);
   const long long units = (long long)ncs * nblk;
   int NB = num_sms();
@@ -229,13 +427,17 @@ int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, ui
       if (k > smax) smax = k;
     }
   }
-  const size_t base_smem = (size_t)B * kW * sizeof(float) + 2 * sizeof(int) * (size_t)m;
-  const size_t acc_bytes = (size_t)m * kW * sizeof(float);
-  int dev_max = 0, dev = 0;
-  MIHS_CUDA_TRY(cudaGetDevice(&dev));
-  MIHS_CUDA_TRY(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const bool acc_in_smem = base_smem + acc_bytes <= (size_t)dev_max;
-  const size_t smem = base_smem + (acc_in_smem ? acc_bytes : 0);
+  bool acc_in_smem;
+  size_t smem;
+  if (tma) {
+    acc_in_smem = srht_tma_smem((int)m, true) <= (size_t)dev_max;
+    smem = srht_tma_smem((int)m, acc_in_smem);
+  } else {
+    const size_t base_smem = (size_t)B * kW * sizeof(float) + 2 * sizeof(int) * (size_t)m;
+    const size_t acc_bytes = (size_t)m * kW * sizeof(float);
+    acc_in_smem = base_smem + acc_bytes <= (size_t)dev_max;
+    smem = base_smem + (acc_in_smem ? acc_bytes : 0);
+  }
   if (smem > (size_t)dev_max) {
     set_error("srht: m=%lld needs %zu bytes of shared memory", (long long)m, smem);
     return MIHS_ERR_UNSUPPORTED;
@@ -271,10 +473,15 @@ int sketch_srht(const float* A, int64_t n, int64_t d, int64_t lda, int64_t m, ui
   a.partial = partial;
   a.smax = smax;
   a.acc_in_smem = acc_in_smem ? 1 : 0;
-  KernelFn fn = pick_kernel(LB);
-  MIHS_CUDA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-  fn<<<NB, kThreads, smem, s>>>(a);
+  if (tma) {
+    MIHS_CUDA_TRY(cudaFuncSetAttribute((const void*)srht_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    srht_tma_kernel<<<NB, kTThreads, smem, s>>>(tmap, a);
+  } else {
+    KernelFn fn = pick_kernel(LB);
+    MIHS_CUDA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<NB, kThreads, smem, s>>>(a);
+  }
   MIHS_CHECK_LAUNCH();
   dim3 rg((unsigned)ncs, (unsigned)((m + 7) / 8));
   srht_reduce_kernel<<<rg, 256, 0, s>>>(partial, NB, smax, units, nblk, (int)m, (int)d,

@@ -213,10 +213,11 @@ def _sketch_bound(family, A, m, seed, n):
         cnt = np.bincount(h, minlength=m).max()
         return gamma(cnt + 1) * (S @ absA)
     if family == o.SRHT:
+        # depth: log₂B transform levels + the n_p/B blocks + the blocks' partials;
+        # B is 1024 in the plain form and 512 in the pipelined one (more blocks)
         L = max(0, math.ceil(math.log2(n)))
-        LB = min(L, 10)
-        nblk = 2 ** (L - LB)
-        return gamma(LB + nblk + _sms() + 4) * (np.ones((m, 1)) * absA.sum(0, keepdims=True)) / math.sqrt(m)
+        nblk = 2 ** max(0, L - 9)
+        return gamma(10 + nblk + _sms() + 4) * (np.ones((m, 1)) * absA.sum(0, keepdims=True)) / math.sqrt(m)
     S = np.abs(o.gaussian_sketch_matrix(m, n, seed))
     ks = 16 + n  # per-split sequential depth ≤ n, plus the split-K sum
     # tensor-core path: A enters as tf32 (≤ 2⁻¹⁰ relative), S is rounded to tf32
@@ -254,6 +255,29 @@ def test_countsketch_integer_exact():
     A = W.randint_matrix((n, d), 9, -100, 100)
     SA = mihs.sketch_apply(A.to(DEV), o.COUNTSKETCH, m, 77).cpu().numpy().astype(np.float64)
     assert np.array_equal(SA, o.sketch_apply(o.COUNTSKETCH, A.numpy(), m, 77))
+
+
+@pytest.mark.parametrize("n,d,lda,m", [(5000, 64, 64, 1000), (256, 100, 100, 64), (70000, 40, 40, 300),
+                                       (300, 33, 36, 20), (257, 1, 4, 3)])
+def test_srht_forms_match_oracle(n, d, lda, m):
+    """The SRHT's other forms: the pipelined kernel with its accumulator in
+    global memory (m too large for shared memory), the plain kernel (n ≤ 256,
+    one block of B = n_p rows), a long ragged n (137 blocks of 512 rows,
+    70000 = 136·512 + 368, n_p = 2¹⁷: the padding blocks are skipped), and
+    the shortest n of the pipelined form with one column."""
+    A = W.padded_matrix(n, d, lda, seed=n + d + lda)
+    seed = 0x5A47 + n
+    Ad = A.to(DEV).as_strided((n, d), (lda, 1))
+    SA = mihs.sketch_apply(Ad, o.SRHT, m, seed)
+    SA2 = mihs.sketch_apply(Ad, o.SRHT, m, seed)
+    torch.cuda.synchronize()
+    An = A[:, :d].numpy().astype(np.float64)
+    ref = o.sketch_apply(o.SRHT, An, m, seed)
+    err = np.abs(_np(SA) - ref)
+    bound = _sketch_bound(o.SRHT, An, m, seed, n)
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound)}"
+    assert torch.equal(SA, SA2)
+    assert mihs.device_status() == 0
 
 
 def test_srht_integer_exact():

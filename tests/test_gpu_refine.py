@@ -51,6 +51,26 @@ def test_refined_solve_reaches_1e10_on_small_problem(family):
     assert o.rel_error(x.cpu().numpy(), xs) <= 1e-10
 
 
+def test_plain_fp32_gradient_never_stops_a_refined_solve():
+    """A = [1; 1], b = [1, 2⁻³⁰], λ = 2: x* = (1 + 2⁻³⁰)/4 = ¼ + 2⁻³², and at
+    the warm start x = ¼ (x*'s fp32 rounding) the plain fp32 gradient is
+    exactly 0 (b₂ − x rounds to −¼, so Aᵀr = ½ = λx) while the true one is
+    2⁻³⁰.  A refinement solve must not stop on that zero (a plain gradient
+    certifies nothing below its own rounding floor): it goes on with
+    compensated gradients and reaches x* to fp64 accuracy."""
+    A = torch.zeros(2, 4)
+    A[:, 0] = 1.0
+    Ad = A.to(DEV).as_strided((2, 1), (4, 1))
+    b = torch.tensor([1.0, 2.0 ** -30]).to(DEV)
+    lam, xs = 2.0, 0.25 + 2.0 ** -32
+    assert mihs.gradient(Ad, b, torch.tensor([0.25], device=DEV), lam).item() == 0.0  # the premise
+    with mihs.Sketch(Ad, "gaussian", 2, seed=5) as sk:
+        x = torch.tensor([0.25], dtype=torch.float64, device=DEV)
+        x, info = sk.solve_refined(Ad, b, lam, 0.5, tol=1e-14, max_outer=50, x=x, warm_start=True)
+    assert info.converged, info
+    assert abs(x.item() - xs) <= 1e-13 * xs, (x.item(), xs)
+
+
 def test_refined_solve_switches_phase_once():
     """Refinement solves take plain fp32 gradients until the relative residual
     is below 1e-7 or stops improving, then compensated ones.  The host-driven loop (per-kernel
