@@ -8,8 +8,8 @@
 //   * the split-K partials are pairs, summed in fp64 by the finalize kernel,
 //     which also subtracts λx in fp64.
 // The stream of A is the same as the plain A-pass (bulk-copy ring, one read
-// of A); the extra fp32 arithmetic (~10 operations per element and phase)
-// hides under the memory time.  This is the accuracy-critical step of M-IHS:
+// of A); the extra fp32 arithmetic (11 operations per element and phase)
+// runs as packed .f32x2 instructions, two independent chains at a time.  This is the accuracy-critical step of M-IHS:
 // the iteration's fixed point is where this gradient vanishes, while the
 // sketch and AAb_Solver only precondition.
 #include "internal.h"
@@ -18,16 +18,17 @@ namespace mihs {
 
 namespace {
 
-// Consumer warps per block: 8, or 7 for rows wider than 1024 so that the
-// block has 256 threads and each may hold 255 registers (the double-float
-// column accumulators need 8 registers per float4 column group).  Rows up to
-// 1024 wide run two blocks per SM (≤ 112 registers a thread): the pass is
-// bound by the latency of its dependent TwoSum chains, and one block of
-// eight consumer warps left each scheduler without an eligible warp 45% of
-// the time.
+// Seven consumer warps and the producer: 256 threads, so that each thread may
+// hold 255 registers with one block per SM (rows wider than 1024: the
+// double-float column accumulators need 8 registers per float4 column
+// group), or 128 with two (rows up to 1024 wide).  Two blocks per SM keep 14
+// consumer warps on the schedulers: the pass is bound by the latency of its
+// dependent TwoSum chains (one block of eight consumer warps left each
+// scheduler without an eligible warp 45% of the time; two blocks of nine
+// warps get only 96 registers and spill).
 template <int CH>
 struct DdCfg {
-  static constexpr int NC = CH > 8 ? 7 : 8;
+  static constexpr int NC = 7;
   static constexpr int kThreads = (NC + 1) * 32;
   static constexpr int kBlocksPerSm = CH > 8 ? 1 : 2;
   static constexpr size_t kRingBudget = CH > 8 ? 150 * 1024 : 96 * 1024;
@@ -60,6 +61,61 @@ __device__ __forceinline__ void df_prod(float a, float xh, float xl, float& p, f
   e = fmaf(a, xl, e);
 }
 
+// Packed pairs of fp32 (PTX .f32x2, sm_100 and later): one instruction does
+// the same IEEE round-to-nearest operation on both halves, so two
+// independent double-float chains advance per instruction.
+typedef unsigned long long P2;
+__device__ __forceinline__ P2 p2_add(P2 a, P2 b) {
+  P2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ P2 p2_sub(P2 a, P2 b) {
+  P2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ P2 p2_mul(P2 a, P2 b) {
+  P2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ P2 p2_fma(P2 a, P2 b, P2 c) {
+  P2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ P2 p2_pack(float x, float y) {
+  P2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x), "f"(y));
+  return d;
+}
+__device__ __forceinline__ float2 p2_unpack(P2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+struct DF2 {  // two double-float values, hi halves and lo halves packed
+  P2 hi, lo;
+};
+
+// (s.hi + s.lo) += a·(yh + yl) for both halves, given nyh = −yh: the
+// product's rounded part is p = −fl(a·nyh) (rounding is symmetric), its
+// error fma(a, yh, −p) + a·yl (TwoProduct), the sum by TwoSum(s.hi, p) with
+// its error and the product's added to s.lo — the same operations and
+// roundings, half by half, as df_prod followed by df_add.
+__device__ __forceinline__ void df2_madd(DF2& s, P2 a, P2 yh, P2 nyh, P2 yl) {
+  const P2 pn = p2_mul(a, nyh);                    // −p
+  P2 e = p2_fma(a, yh, pn);                        // a·yh − p, exact
+  e = p2_fma(a, yl, e);
+  const P2 t = p2_sub(s.hi, pn);                   // s.hi + p
+  const P2 z = p2_sub(t, s.hi);
+  const P2 e2 = p2_sub(p2_sub(s.hi, p2_sub(t, z)), p2_add(pn, z));  // (s.hi − (t − z)) + (p − z)
+  s.hi = t;
+  s.lo = p2_add(s.lo, p2_add(e2, e));
+}
+
 __device__ __forceinline__ DF df_shfl_xor_sum(DF v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -85,8 +141,9 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
   float* ring = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)stages * R * dpad);
   uint64_t* empty = full + stages;
-  float* xh = reinterpret_cast<float*>(empty + stages);  // CH·128 each
+  float* xh = reinterpret_cast<float*>(empty + stages);  // CH·128 each: x_hi, x_lo, −x_hi
   float* xl = xh + CH * 128;
+  float* nxh = xl + CH * 128;
   __shared__ int issued;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long r0 = (long long)blockIdx.x * rows_per_cta;
@@ -105,6 +162,7 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
     const float h = (float)xv;
     xh[j] = h;
     xl[j] = (float)(xv - (double)h);
+    nxh[j] = -h;
   }
   __syncthreads();
 
@@ -135,11 +193,12 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
     return;
   }
 
-  DF acc[CH][4];
+  // Column accumulators: group c's components (x, y) and (z, w), packed.
+  DF2 acc[CH][2];
 #pragma unroll
   for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[c][q] = DF{0.f, 0.f};
+    for (int q = 0; q < 2; ++q) acc[c][q] = DF2{0ull, 0ull};
   int consumed = 0;
   for (int it = 0; it < nst; ++it) {
     const int s = it % stages;
@@ -169,27 +228,25 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
         }
         return t;
       };
-      // Four independent double-float chains (one per float4 component) so
-      // that consecutive TwoSums do not wait on each other.
-      DF sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sw = {0.f, 0.f};
+      // Four independent double-float chains (one per float4 component, two
+      // per packed instruction) so that consecutive TwoSums do not wait on
+      // each other.
+      DF2 sxy = {0ull, 0ull}, szw = {0ull, 0ull};
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int col = 4 * lane + 128 * c;
         const float4 t = chunk(c);
-        const float4 h4 = *reinterpret_cast<const float4*>(xh + col);
-        const float4 l4 = *reinterpret_cast<const float4*>(xl + col);
-        float p, e;
-        df_prod(t.x, h4.x, l4.x, p, e);
-        df_add(sx, p, e);
-        df_prod(t.y, h4.y, l4.y, p, e);
-        df_add(sy, p, e);
-        df_prod(t.z, h4.z, l4.z, p, e);
-        df_add(sz, p, e);
-        df_prod(t.w, h4.w, l4.w, p, e);
-        df_add(sw, p, e);
+        const ulonglong2 h2 = *reinterpret_cast<const ulonglong2*>(xh + col);
+        const ulonglong2 l2 = *reinterpret_cast<const ulonglong2*>(xl + col);
+        const ulonglong2 n2 = *reinterpret_cast<const ulonglong2*>(nxh + col);
+        df2_madd(sxy, p2_pack(t.x, t.y), h2.x, n2.x, l2.x);
+        df2_madd(szw, p2_pack(t.z, t.w), h2.y, n2.y, l2.y);
       }
-      df_add(sx, sy.hi, sy.lo);
-      df_add(sz, sw.hi, sw.lo);
+      const float2 xyh = p2_unpack(sxy.hi), xyl = p2_unpack(sxy.lo);
+      const float2 zwh = p2_unpack(szw.hi), zwl = p2_unpack(szw.lo);
+      DF sx = {xyh.x, xyl.x}, sz = {zwh.x, zwl.x};
+      df_add(sx, xyh.y, xyl.y);
+      df_add(sz, zwh.y, zwl.y);
       df_add(sx, sz.hi, sz.lo);
       DF sum = sx;
       sum = df_shfl_xor_sum(sum);
@@ -198,18 +255,12 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
       two_sum(bi, -sum.hi, rh, re);
       float r_hi, r_lo;
       two_sum(rh, re - sum.lo, r_hi, r_lo);
+      const P2 rh2 = p2_pack(r_hi, r_hi), nrh2 = p2_pack(-r_hi, -r_hi), rl2 = p2_pack(r_lo, r_lo);
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const float4 t = chunk(c);
-        float p, e;
-        df_prod(t.x, r_hi, r_lo, p, e);
-        df_add(acc[c][0], p, e);
-        df_prod(t.y, r_hi, r_lo, p, e);
-        df_add(acc[c][1], p, e);
-        df_prod(t.z, r_hi, r_lo, p, e);
-        df_add(acc[c][2], p, e);
-        df_prod(t.w, r_hi, r_lo, p, e);
-        df_add(acc[c][3], p, e);
+        df2_madd(acc[c][0], p2_pack(t.x, t.y), rh2, nrh2, rl2);
+        df2_madd(acc[c][1], p2_pack(t.z, t.w), rh2, nrh2, rl2);
       }
     }
     __syncwarp();
@@ -233,8 +284,11 @@ apass_dd_kernel(const float* __restrict__ A, int n, int d, long long lda, const 
   for (int c = 0; c < CH; ++c) {
     const int col = 4 * lane + 128 * c;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (col + q < dpad) wpart[(size_t)warp * dpad + col + q] = make_float2(acc[c][q].hi, acc[c][q].lo);
+    for (int q = 0; q < 2; ++q) {
+      const float2 h = p2_unpack(acc[c][q].hi), l = p2_unpack(acc[c][q].lo);
+      if (col + 2 * q < dpad) wpart[(size_t)warp * dpad + col + 2 * q] = make_float2(h.x, l.x);
+      if (col + 2 * q + 1 < dpad) wpart[(size_t)warp * dpad + col + 2 * q + 1] = make_float2(h.y, l.y);
+    }
   }
   named_sync(1, NC * 32);
   float2* out = partials + (size_t)blockIdx.x * dpad;
@@ -330,7 +384,7 @@ int launch_apass_dd(const float* A, int64_t n, int64_t d, int64_t lda, const flo
   // The ring must also hold the NC × dpad float2 warp pairs at the end.
   while ((size_t)stages * stage_bytes < (size_t)k.nc * dpad * sizeof(float2)) ++stages;
   const size_t smem = (size_t)stages * stage_bytes + 2 * sizeof(uint64_t) * stages +
-                      2 * (size_t)k.chunks * 128 * sizeof(float);
+                      3 * (size_t)k.chunks * 128 * sizeof(float);
   MIHS_CUDA_TRY(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int n32 = (int)n, d32 = (int)d, dp32 = (int)dpad;
   long long lda64 = lda;
