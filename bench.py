@@ -11,8 +11,10 @@ from HBM.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mihs|reference]
 
 Prints one JSON line (rank 0).  `value` is device time with A and b resident;
-`e2e` is the one-call API with host (pinned) inputs, copies inside the timed
-region; `roofline` is the gradient A-pass kernel, timed with CUDA events on
+`e2e` takes every step's A and b from pinned host memory and returns each x
+to the host, copies inside the timed region (by default double-buffered:
+problem k+1 is copied in by a copy engine while problem k solves;
+`--e2e-mode serial` copies, then solves); `roofline` is the gradient A-pass kernel, timed with CUDA events on
 its stream; `cpu_baseline` is the oracle on the host cores (bounded sample).
 Under torchrun (N > 1) every rank solves its own replica (weak scaling; the
 method needs no collective on one problem per GPU).
@@ -58,6 +60,14 @@ def parse():
     ap.add_argument("--d", "--cols", dest="d", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-mode", choices=["pipelined", "serial"], default="pipelined",
+                    help="pipelined: problem k+1's inputs are copied in (two device buffers) while problem k "
+                         "solves; serial: copy, then solve, one problem at a time")
+    ap.add_argument("--e2e-copy", choices=["auto", "sm", "dma"], default="auto",
+                    help="host-to-device copy of the e2e leg: the SMs (mihs_copy_to_device) or a copy engine "
+                         "(mihs_copy_to_device_dma); auto: dma when pipelined, sm when serial")
+    ap.add_argument("--h2d-blocks", type=int, default=0,
+                    help="SMs the SM copy may use in the e2e leg (MIHS_H2D_BLOCKS; 0: all)")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-refined", action="store_true", help="skip the compensated-refinement leg")
     ap.add_argument("--refined-tol", type=float, default=1e-10)
@@ -484,43 +494,89 @@ def main():
             A_host, b_host = A.cpu(), b.cpu()
         A_pin, b_pin = A_host.pin_memory(), b_host.pin_memory()
         outs = {f: torch.empty(d, dtype=torch.float32, pin_memory=True) for f in families}
-        A_dev = torch.empty(n, d, dtype=torch.float32, device=dev)
-        b_dev = torch.empty(n, dtype=torch.float32, device=dev)
+        A_devs = [torch.empty(n, d, dtype=torch.float32, device=dev) for _ in range(2)]
+        b_devs = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(2)]
+        h2d_env = os.environ.get("MIHS_H2D_BLOCKS")
+        if args.h2d_blocks > 0:
+            os.environ["MIHS_H2D_BLOCKS"] = str(args.h2d_blocks)
 
-        def e2e_step():
-            # One problem per step: A and b go to the device once (the SMs
-            # read the pinned host memory, mihs_copy_to_device), the three
-            # family solves run on that copy, each x comes back to the host.
-            mihs.copy_to_device(A_dev, A_pin)
-            mihs.copy_to_device(b_dev, b_pin)
-            ev = torch.cuda.Event()
-            ev.record(main_stream)
-            for f in families:
-                streams[f].wait_event(ev)
-                with torch.cuda.stream(streams[f]):
-                    xf, _ = mihs.solve(A_dev, b_dev, p.lam, f, m, p.sd, seed=seed, want_info=False, aab=aab, **kw)
-                    outs[f].copy_(xf, non_blocking=True)
-            for f in families:
-                main_stream.wait_stream(streams[f])
+        def measure_e2e(mode):
+            """ms per step of `mode`: 'pipelined' (two device buffers, problem
+            k+1 copied in on its own stream while problem k solves) or
+            'serial' (copy, then solve, one problem at a time)."""
+            nbuf = 2 if mode == "pipelined" else 1
+            copy_stream = torch.cuda.Stream() if nbuf > 1 else main_stream
+            free_ev = [[] for _ in range(nbuf)]  # events of the solves that last read each buffer
+            engine = args.e2e_copy if args.e2e_copy != "auto" else ("dma" if nbuf > 1 else "sm")
 
-        for _ in range(max(args.warmup, 1)):
-            e2e_step()
-        torch.cuda.synchronize()
-        barrier(ws)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(ws)
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+            def e2e_step(k):
+                # One problem per step: its A and b go to the device (the SMs
+                # read the pinned host memory, or a copy engine does the copy),
+                # the three family solves run on that copy and each x comes back
+                # to the host.
+                q = k % nbuf
+                for e in free_ev[q]:
+                    copy_stream.wait_event(e)
+                mihs.copy_to_device(A_devs[q], A_pin, stream=copy_stream, engine=engine)
+                mihs.copy_to_device(b_devs[q], b_pin, stream=copy_stream, engine=engine)
+                ready = torch.cuda.Event()
+                ready.record(copy_stream)
+                done = []
+                for f in families:
+                    streams[f].wait_event(ready)
+                    with torch.cuda.stream(streams[f]):
+                        xf, _ = mihs.solve(A_devs[q], b_devs[q], p.lam, f, m, p.sd, seed=seed, want_info=False,
+                                           aab=aab, **kw)
+                        outs[f].copy_(xf, non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(streams[f])
+                        done.append(ev)
+                free_ev[q] = done
+
+            def drain():
+                for f in families:
+                    main_stream.wait_stream(streams[f])
+                main_stream.wait_stream(copy_stream)
+
+            for k in range(max(args.warmup, 1)):
+                e2e_step(k)
+            drain()
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            copy_stream.wait_stream(main_stream)
+            for k in range(args.steps):
+                e2e_step(k)
+            drain()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(ws)
+            ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+            how = ("a copy engine, mihs_copy_to_device_dma" if engine == "dma" else
+                   f"the SMs, mihs_copy_to_device on {args.h2d_blocks or 'all'} SMs")
+            return ms, how
+
+        ms_e2e, how = measure_e2e(args.e2e_mode)
+        other = "serial" if args.e2e_mode == "pipelined" else "pipelined"
+        ms_other, how_other = measure_e2e(other)
+        if h2d_env is None:
+            os.environ.pop("MIHS_H2D_BLOCKS", None)
+        else:
+            os.environ["MIHS_H2D_BLOCKS"] = h2d_env
+        desc = {"pipelined": "two device buffers: problem k+1 is copied in on its own stream while problem k's "
+                             "three solves run",
+                "serial": "copy, then the three solves, one problem at a time"}
         e2e = {"value": round(ws * len(families) / (ms_e2e / 1e3), 3), "unit": "solves/s",
                "ms_per_step": round(ms_e2e, 4),
                "h2d_bytes_per_step": 4 * (n * d + n),
                "d2h_bytes_per_step": len(families) * 4 * d,
-               "copies": "A and b copied in once per step (the step's three solves share them), "
-                         "each family's x copied out"}
+               "mode": args.e2e_mode,
+               "copies": (f"each step copies its problem's A and b in (1.07 GB from pinned host memory, {how}) "
+                          f"and each family's x out; {desc[args.e2e_mode]}"),
+               other: {"value": round(ws * len(families) / (ms_other / 1e3), 3),
+                       "ms_per_step": round(ms_other, 4),
+                       "copies": f"{how_other}; {desc[other]}"}}
 
     # ---------------- the 4096 × 256 problem (L2-resident, latency-bound)
     small = None

@@ -217,9 +217,11 @@ struct mihs_sketch_s {
   SolveCtl* ctl_host; // pinned
   // Device-side outer loop: a CUDA graph holding one conditional WHILE node
   // whose body is (A-pass, partial-sum reduce, AAb + heavy ball); the AAb
-  // kernel clears the condition when the stop test fires.  One graph per
-  // kind of solve (plain, refinement, adjoint), each rebuilt when that
-  // solve's pointers or scalars change.
+  // kernel clears the condition when the stop test fires.  Up to
+  // kGraphWays graphs per kind of solve (plain, refinement, adjoint), keyed
+  // by the solve's pointers and scalars and replaced least recently used, so
+  // that a caller alternating between input buffers (a copy of the next
+  // problem landing while this one solves) relaunches instead of rebuilding.
   cudaStream_t cap = nullptr;
   struct Key {
     const float* A; int64_t lda; const float* b; void* x;
@@ -234,12 +236,15 @@ struct mihs_sketch_s {
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
   };
+  static constexpr int kGraphWays = 4;
   struct GraphSlot {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     Key key = {};
-    bool failed = false;  // capture failed once: host-driven steps from then on
-  } slots[4];  // indexed by (refined ? 1 : 0) + (adjoint ? 2 : 0)
+    uint64_t used = 0;  // launch tick of the last use (0: empty)
+  } slots[4][kGraphWays];      // kind = (refined ? 1 : 0) + (adjoint ? 2 : 0)
+  bool graph_failed[4] = {};   // capture failed once: host-driven steps for that kind from then on
+  uint64_t graph_tick = 0;
   // λ-path workspace (allocated on the first path solve): split-K partials
   // (P_path × 16 × dp), G and X⁻ (16 × dp each), 16 control blocks and the
   // path's stop counter / flag.
@@ -910,7 +915,8 @@ int mihs_sketch_copy(mihs_sketch_t sk, float* dst, int64_t ldd, void* stream) {
 int mihs_sketch_destroy(mihs_sketch_t sk) {
   if (sk == nullptr) return MIHS_OK;
   cudaDeviceSynchronize();
-  for (auto& gs : sk->slots) drop_graph(gs);
+  for (auto& kind : sk->slots)
+    for (auto& gs : kind) drop_graph(gs);
   if (sk->path_exec) cudaGraphExecDestroy(sk->path_exec);
   if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
   if (sk->cap) cudaStreamDestroy(sk->cap);
@@ -1043,17 +1049,26 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
                                   alpha,     beta,        a.eps,      a.max_passes, rhs,
                                   sk->sa_prec, sk->aab_form, sk->aab_grid_blocks};
   bool graph_ran = false;
-  mihs_sketch_s::GraphSlot& gs = sk->slots[(refined ? 1 : 0) + (rhs != nullptr ? 2 : 0)];
-  if (!timing_on() && !gs.failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
-    if (!(gs.exec && gs.key == key)) {
-      if (build_graph(sk, key, a, refined, gs) != MIHS_OK) {
-        drop_graph(gs);
-        gs.failed = true;  // keep the message; use host-driven steps from now on
+  const int kind = (refined ? 1 : 0) + (rhs != nullptr ? 2 : 0);
+  if (!timing_on() && !sk->graph_failed[kind] && std::getenv("MIHS_NO_GRAPH") == nullptr) {
+    mihs_sketch_s::GraphSlot* ways = sk->slots[kind];
+    mihs_sketch_s::GraphSlot* gs = nullptr;
+    for (int w = 0; w < mihs_sketch_s::kGraphWays && gs == nullptr; ++w)
+      if (ways[w].exec && ways[w].key == key) gs = &ways[w];
+    if (gs == nullptr) {  // an empty way, else the least recently used one
+      gs = &ways[0];
+      for (int w = 1; w < mihs_sketch_s::kGraphWays; ++w)
+        if (ways[w].used < gs->used) gs = &ways[w];
+      if (build_graph(sk, key, a, refined, *gs) != MIHS_OK) {
+        drop_graph(*gs);
+        gs->used = 0;
+        sk->graph_failed[kind] = true;  // keep the message; use host-driven steps from now on
         cudaGetLastError();
       }
     }
-    if (gs.exec) {
-      MIHS_CUDA_TRY(cudaGraphLaunch(gs.exec, s));
+    if (gs->exec) {
+      MIHS_CUDA_TRY(cudaGraphLaunch(gs->exec, s));
+      gs->used = ++sk->graph_tick;
       graph_ran = true;
     }
   }

@@ -74,3 +74,16 @@ int mihs_copy_to_device(void* dst, const void* src, int64_t bytes, void* stream)
                                   cudaMemcpyDefault, s));
   return MIHS_OK;
 }
+
+int mihs_copy_to_device_dma(void* dst, const void* src, int64_t bytes, void* stream) {
+  set_error("");
+  MIHS_ARG(bytes >= 0, "mihs_copy_to_device_dma: bytes %lld < 0", (long long)bytes);
+  if (bytes == 0) return MIHS_OK;
+  MIHS_ARG(dst != nullptr && src != nullptr, "mihs_copy_to_device_dma: null pointer");
+  cudaPointerAttributes ad = {};
+  MIHS_CUDA_TRY(cudaPointerGetAttributes(&ad, dst));
+  MIHS_ARG(ad.type == cudaMemoryTypeDevice || ad.type == cudaMemoryTypeManaged,
+           "mihs_copy_to_device_dma: dst is not device memory");
+  MIHS_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, static_cast<cudaStream_t>(stream)));
+  return MIHS_OK;
+}

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
         "mihs_device_status": (_int, [ctypes.POINTER(_int)]),
         "mihs_selftest_wait": (_int, [_int, _i64, ctypes.POINTER(_int), _vp]),
         "mihs_copy_to_device": (_int, [_vp, _vp, _i64, _vp]),
+        "mihs_copy_to_device_dma": (_int, [_vp, _vp, _i64, _vp]),
         "mihs_sketch_apply": (_int, [_vp, _i64, _i64, _i64, _int, _i64, _u64, _vp, _i64, _vp]),
         "mihs_sketch_gaussian_bf16": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
         "mihs_sketch_gaussian_fp8": (_int, [_vp, _i64, _i64, _i64, _i64, _u64, _vp, _i64, _vp]),
@@ -174,16 +175,20 @@ def selftest_wait(which: int, limit_s: float = 0.05, stream=None) -> int:
     return st.value
 
 
-def copy_to_device(dst: torch.Tensor, src: torch.Tensor, stream=None) -> torch.Tensor:
+def copy_to_device(dst: torch.Tensor, src: torch.Tensor, stream=None, engine: str = "sm") -> torch.Tensor:
     """dst ← src for a contiguous host tensor src and a contiguous CUDA
-    tensor dst of the same dtype and size (mihs_copy_to_device: the SMs read
-    pinned host memory directly)."""
+    tensor dst of the same dtype and size.  engine "sm": the SMs read pinned
+    host memory directly (mihs_copy_to_device, the faster copy alone); "dma":
+    a copy engine, no SM work (mihs_copy_to_device_dma, for copies that
+    overlap solves on other streams)."""
     if src.is_cuda or not dst.is_cuda or src.dtype != dst.dtype or src.numel() != dst.numel():
         raise ValueError("copy_to_device: host src and CUDA dst of one dtype and size")
     if not (src.is_contiguous() and dst.is_contiguous()):
         raise ValueError("copy_to_device: contiguous tensors only")
-    _check(lib().mihs_copy_to_device(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(),
-                                     _stream(stream)))
+    if engine not in ("sm", "dma"):
+        raise ValueError(f"copy_to_device: engine {engine!r} is not 'sm' or 'dma'")
+    fn = lib().mihs_copy_to_device if engine == "sm" else lib().mihs_copy_to_device_dma
+    _check(fn(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(), _stream(stream)))
     return dst
 
 

@@ -1,5 +1,6 @@
 """mihs_copy_to_device: pinned, aligned host memory read by the SMs; pageable,
-unaligned and tail bytes through cudaMemcpyAsync.  Byte-exact in every case."""
+unaligned and tail bytes through cudaMemcpyAsync.  mihs_copy_to_device_dma:
+a copy engine for all of it.  Byte-exact in every case."""
 import pytest
 import torch
 
@@ -58,3 +59,21 @@ def test_copy_rejects_bad_arguments():
         mihs.copy_to_device(torch.empty(4), torch.empty(4))
     with pytest.raises(mihs.MihsError):  # destination on the host
         mihs._check(mihs.lib().mihs_copy_to_device(torch.empty(4).data_ptr(), torch.empty(4).data_ptr(), 16, None))
+
+
+@pytest.mark.parametrize("numel", [1, 1001, (1 << 22) + 5])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_copy_engine_form_is_exact_and_launches_nothing(numel, pinned):
+    src = W.randn((numel,), 70 + numel)
+    if pinned:
+        src = src.pin_memory()
+    dst = torch.full((numel,), float("nan"), device=DEV)
+    c0 = mihs.launch_count()
+    mihs.copy_to_device(dst, src, engine="dma")
+    torch.cuda.synchronize()
+    assert torch.equal(dst.cpu(), src)
+    assert mihs.launch_count() == c0
+    with pytest.raises(ValueError):
+        mihs.copy_to_device(dst, src, engine="tma")
+    with pytest.raises(mihs.MihsError):  # destination on the host
+        mihs._check(mihs.lib().mihs_copy_to_device_dma(torch.empty(4).data_ptr(), src.data_ptr(), 4, None))

@@ -334,6 +334,29 @@ def test_solve_edge_shapes_match_exact(n, d, decades, lam, family):
     assert o.rel_error(xr.cpu().numpy(), xs) <= 1e-9
 
 
+def test_graph_cache_with_alternating_buffers():
+    """A handle keeps several solve graphs per kind, keyed by pointers: solves
+    that alternate between two copies of A and b (and between more x
+    buffers than the cache holds, so that ways are replaced) give the same
+    bytes as the same solve on one buffer."""
+    p = W.problem_small()
+    A1, b1 = p.A.to(DEV), p.b.to(DEV)
+    A2, b2 = A1.clone(), b1.clone()
+    xs = [torch.empty(p.d, device=DEV) for _ in range(6)]
+    with mihs.Sketch(A1, "countsketch", p.m, seed=4) as sk:
+        ref, _ = sk.solve(A1, b1, p.lam, p.sd, tol=1e-6, max_outer=100)
+        ref = ref.clone()
+        for k in range(12):
+            A, b = (A1, b1) if k % 2 == 0 else (A2, b2)
+            x, info = sk.solve(A, b, p.lam, p.sd, tol=1e-6, max_outer=100, x=xs[k % 6])
+            assert info.converged and torch.equal(x, ref), k
+        xr0, _ = sk.solve_refined(A1, b1, p.lam, p.sd, tol=1e-12)
+        xr0 = xr0.clone()
+        xr1, _ = sk.solve_refined(A2, b2, p.lam, p.sd, tol=1e-12)
+        xr2, _ = sk.solve_refined(A1, b1, p.lam, p.sd, tol=1e-12)
+    assert torch.equal(xr1, xr0) and torch.equal(xr2, xr0)
+
+
 def test_solve_history_matches_info():
     p = W.problem_scaled(20000, 300, seed=8)
     A, b = p.A.to(DEV), p.b.to(DEV)

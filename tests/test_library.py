@@ -66,6 +66,9 @@ def test_host_side_argument_checks(L):
     assert L.mihs_copy_to_device(FAKE, FAKE, -1, None) == EINVAL
     assert L.mihs_copy_to_device(None, FAKE, 16, None) == EINVAL
     assert L.mihs_copy_to_device(FAKE, FAKE, 0, None) == 0  # nothing to copy
+    assert L.mihs_copy_to_device_dma(FAKE, FAKE, -1, None) == EINVAL
+    assert L.mihs_copy_to_device_dma(FAKE, None, 16, None) == EINVAL
+    assert L.mihs_copy_to_device_dma(FAKE, FAKE, 0, None) == 0
     assert L.mihs_sketch_destroy(None) == 0
 
 
