@@ -790,12 +790,15 @@ def run_batched(args, dev, ws, peaks, peak_src):
     Xs = [torch.empty(len(lams), q.d, device=dev) for q in probs]
     entries = [(sk, q.A, q.b, X) for sk, q, X in zip(handles, probs, Xs)]
 
-    def step(want_info=False, sub=None):
+    def step(want_info=False, sub=None, marks=None):
         ent = entries if sub is None else entries[:sub]
         for i, (sk, q) in enumerate(zip(handles[:len(ent)], probs)):
             sk.resketch(q.A, 100 + i)
         sd_ = sds[:len(ent)]
         inf = mihs.solve_batched(ent, lams, sds=sd_, tol=tol, max_outer=200, want_info=want_info)
+        if marks is not None:  # end of the fp32 path phase, on the caller's stream
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(torch.cuda.current_stream())
         rinf = mihs.refine_batched(ent, lams, tols, sds=sd_, max_outer=200, want_info=want_info)
         return inf, rinf
 
@@ -806,11 +809,19 @@ def run_batched(args, dev, ws, peaks, peak_src):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        step()
+    marks = []
+    starts = [e0]
+    for k in range(steps):
+        step(marks=marks)
+        if k + 1 < steps:
+            starts.append(torch.cuda.Event(enable_timing=True))
+            starts[-1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, ws)
+    ends = starts[1:] + [e1]
+    path_ms = sum(a.elapsed_time(b) for a, b in zip(starts, marks)) / steps
+    refine_ms = sum(a.elapsed_time(b) for a, b in zip(marks, ends)) / steps
     # per-kernel split and the fused pass's arithmetic rate (host-driven, timed)
     mihs.timing(True)
     for i, (sk, q) in enumerate(zip(handles, probs)):
@@ -828,6 +839,7 @@ def run_batched(args, dev, ws, peaks, peak_src):
     rflat = [i for row in rinfos for i in row if i is not None]
     out = {"value": round(ws * len(probs) * len(lams) / (ms / 1e3), 2), "unit": "(matrix, λ) solves/s",
            "ms_per_step": round(ms, 3), "steps": steps,
+           "phase_ms": {"sketch_and_fp32_paths": round(path_ms, 1), "refinement": round(refine_ms, 1)},
            "workload": f"{len(probs)} matrices (n log-uniform 8192–262144, d in 64–1024, "
                        f"{sum(4 * q.n * q.d for q in probs) / 1e9:.2f} GB of A), 16 λ in [1e-6, 1e-1], "
                        f"Gaussian m = 4·sd(λ_min); fp32 path to residual {tol:g}, then the "
