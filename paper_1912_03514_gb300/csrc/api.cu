@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -221,7 +222,13 @@ struct mihs_sketch_s {
   // kGraphWays graphs per kind of solve (plain, refinement, adjoint), keyed
   // by the solve's pointers and scalars and replaced least recently used, so
   // that a caller alternating between input buffers (a copy of the next
-  // problem landing while this one solves) relaunches instead of rebuilding.
+  // problem landing while this one solves) or refining several λ relaunches
+  // instead of rebuilding.  A replaced executable is retired, not destroyed:
+  // cudaGraphExecDestroy holds the host until the work in flight has
+  // finished (measured: 17.6 ms behind one solve, 2.6 ms behind another even
+  // when the destroyed graph's own launch had ended), which serialises every
+  // stream.  Retired executables are freed with the handle, or all at once
+  // when more than kMaxRetired have gathered.
   cudaStream_t cap = nullptr;
   struct Key {
     const float* A; int64_t lda; const float* b; void* x;
@@ -236,13 +243,15 @@ struct mihs_sketch_s {
              alpha == o.alpha && beta == o.beta && eps == o.eps && max_passes == o.max_passes;
     }
   };
-  static constexpr int kGraphWays = 4;
+  static constexpr int kGraphWays = 8;
+  static constexpr size_t kMaxRetired = 64;
   struct GraphSlot {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     Key key = {};
     uint64_t used = 0;  // launch tick of the last use (0: empty)
   } slots[4][kGraphWays];      // kind = (refined ? 1 : 0) + (adjoint ? 2 : 0)
+  std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> retired;  // replaced, not yet destroyed
   bool graph_failed[4] = {};   // capture failed once: host-driven steps for that kind from then on
   uint64_t graph_tick = 0;
   // λ-path workspace (allocated on the first path solve): split-K partials
@@ -333,6 +342,27 @@ void drop_graph(mihs_sketch_s::GraphSlot& gs) {
   if (gs.graph) cudaGraphDestroy(gs.graph);
   gs.exec = nullptr;
   gs.graph = nullptr;
+}
+
+// Destroys every retired executable (this waits for the work in flight).
+void free_retired(mihs_sketch_s* sk) {
+  for (auto& r : sk->retired) {
+    cudaGraphExecDestroy(r.first);
+    cudaGraphDestroy(r.second);
+  }
+  sk->retired.clear();
+}
+
+// Moves a graph out of the way it occupies into the retired list.
+void retire_graph(mihs_sketch_s* sk, cudaGraphExec_t& exec, cudaGraph_t& graph) {
+  if (exec != nullptr) {
+    if (sk->retired.size() >= mihs_sketch_s::kMaxRetired) free_retired(sk);
+    sk->retired.push_back({exec, graph});
+  } else if (graph != nullptr) {
+    cudaGraphDestroy(graph);  // never instantiated: nothing can be running it
+  }
+  exec = nullptr;
+  graph = nullptr;
 }
 
 // One outer step of Algorithm 1 (gradient, partial-sum reduce, AAb_Solver +
@@ -917,6 +947,7 @@ int mihs_sketch_destroy(mihs_sketch_t sk) {
   cudaDeviceSynchronize();
   for (auto& kind : sk->slots)
     for (auto& gs : kind) drop_graph(gs);
+  free_retired(sk);
   if (sk->path_exec) cudaGraphExecDestroy(sk->path_exec);
   if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
   if (sk->cap) cudaStreamDestroy(sk->cap);
@@ -1059,8 +1090,10 @@ static int solve_impl(mihs_sketch_t sk, const float* A, int64_t lda, const float
       gs = &ways[0];
       for (int w = 1; w < mihs_sketch_s::kGraphWays; ++w)
         if (ways[w].used < gs->used) gs = &ways[w];
+      retire_graph(sk, gs->exec, gs->graph);
+      gs->used = 0;
       if (build_graph(sk, key, a, refined, *gs) != MIHS_OK) {
-        drop_graph(*gs);
+        retire_graph(sk, gs->exec, gs->graph);
         gs->used = 0;
         sk->graph_failed[kind] = true;  // keep the message; use host-driven steps from now on
         cudaGetLastError();
@@ -1268,6 +1301,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
     bool graph_ran = false;
     if (!timing_on() && !sk->path_graph_failed && std::getenv("MIHS_NO_GRAPH") == nullptr) {
       if (!(sk->path_exec && sk->path_key == key)) {
+        retire_graph(sk, sk->path_exec, sk->path_graph);
         const int brc = build_while_graph(sk, (int)sk->m, (int)d, sk->path_graph, sk->path_exec,
                                           [&](unsigned long long cond, cudaStream_t cs) {
                                             AabLaunch b2 = a;
@@ -1277,10 +1311,7 @@ static int path_enqueue(mihs_sketch_t sk, const float* A, int64_t lda, const flo
         if (brc == MIHS_OK) {
           sk->path_key = key;
         } else {
-          if (sk->path_exec) cudaGraphExecDestroy(sk->path_exec);
-          if (sk->path_graph) cudaGraphDestroy(sk->path_graph);
-          sk->path_exec = nullptr;
-          sk->path_graph = nullptr;
+          retire_graph(sk, sk->path_exec, sk->path_graph);
           sk->path_graph_failed = true;  // host-driven steps from now on
           cudaGetLastError();
         }

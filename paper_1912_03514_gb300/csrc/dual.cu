@@ -11,6 +11,9 @@
 #include <cmath>
 #include <cstdlib>
 
+#include <utility>
+#include <vector>
+
 #include "internal.h"
 
 using namespace mihs;
@@ -227,6 +230,9 @@ struct mihs_dual_s {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // Replaced executables, destroyed with the handle (or all at once past 64):
+  // cudaGraphExecDestroy holds the host until the work in flight finishes.
+  std::vector<std::pair<cudaGraphExec_t, cudaGraph_t>> retired;
   bool graph_failed = false;
   struct Key {
     const float* A; int64_t lda; const float* b; float* nu; double lam, alpha, beta; float eps; int max_passes;
@@ -271,7 +277,21 @@ void drop_dual_graph(mihs_dual_t dk) {
   dk->graph = nullptr;
 }
 
+void free_dual_retired(mihs_dual_t dk) {
+  for (auto& r : dk->retired) {
+    cudaGraphExecDestroy(r.first);
+    cudaGraphDestroy(r.second);
+  }
+  dk->retired.clear();
+}
+
 int build_dual_graph(mihs_dual_t dk, const mihs_dual_s::Key& key, const AabLaunch& proto) {
+  if (dk->exec != nullptr) {  // retire the replaced executable rather than wait for the GPU
+    if (dk->retired.size() >= 64) free_dual_retired(dk);
+    dk->retired.push_back({dk->exec, dk->graph});
+    dk->exec = nullptr;
+    dk->graph = nullptr;
+  }
   drop_dual_graph(dk);
   if (!dk->cap) MIHS_CUDA_TRY(cudaStreamCreateWithFlags(&dk->cap, cudaStreamNonBlocking));
   MIHS_CUDA_TRY(cudaGraphCreate(&dk->graph, 0));
@@ -375,6 +395,7 @@ int mihs_dual_destroy(mihs_dual_t dk) {
   if (dk == nullptr) return MIHS_OK;
   cudaDeviceSynchronize();
   drop_dual_graph(dk);
+  free_dual_retired(dk);
   if (dk->cap) cudaStreamDestroy(dk->cap);
   if (dk->grid_ws) cudaFree(dk->grid_ws);
   cudaFree(dk->SAt);

@@ -357,6 +357,40 @@ def test_graph_cache_with_alternating_buffers():
     assert torch.equal(xr1, xr0) and torch.equal(xr2, xr0)
 
 
+def test_graph_rebuild_does_not_wait_for_a_running_solve():
+    """Replacing a cached solve graph while its last launch still runs must
+    not hold the host until that launch ends (a rebuild retires the old
+    executable instead of destroying it).  Nine λ on one handle, one more
+    than the cache holds, cycled twice: every call rebuilds, and in the
+    second cycle the graph it replaces was launched in the first and is
+    still queued.  The 18 solves enqueue in a fraction of their device time,
+    and each λ's result is the same bytes as a fresh handle's solve."""
+    import time
+    p = W.problem_scaled(131072, 512, seed=31)
+    A, b = p.A.to(DEV), p.b.to(DEV)
+    lams = [p.lam * (1.0 + 0.1 * k) for k in range(9)]
+    xs = [torch.empty(p.d, device=DEV) for _ in lams]
+    with mihs.Sketch(A, "countsketch", p.m, seed=6) as sk:
+        for lam, x in zip(lams, xs):  # build and cache (warm-up)
+            sk.solve(A, b, lam, p.sd, tol=1e-7, max_outer=60, x=x, want_info=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            for lam, x in zip(lams, xs):
+                sk.solve(A, b, lam, p.sd, tol=1e-7, max_outer=60, x=x, want_info=False)
+        host_ms = 1e3 * (time.perf_counter() - t0)
+        e1.record()
+        torch.cuda.synchronize()
+        dev_ms = e0.elapsed_time(e1)
+    assert host_ms < 0.5 * dev_ms, (host_ms, dev_ms)
+    for lam, x in zip(lams, xs):
+        with mihs.Sketch(A, "countsketch", p.m, seed=6) as fresh:
+            xf, _ = fresh.solve(A, b, lam, p.sd, tol=1e-7, max_outer=60)
+        assert torch.equal(x, xf)
+
+
 def test_solve_history_matches_info():
     p = W.problem_scaled(20000, 300, seed=8)
     A, b = p.A.to(DEV), p.b.to(DEV)
