@@ -77,3 +77,56 @@ def test_copy_engine_form_is_exact_and_launches_nothing(numel, pinned):
         mihs.copy_to_device(dst, src, engine="tma")
     with pytest.raises(mihs.MihsError):  # destination on the host
         mihs._check(mihs.lib().mihs_copy_to_device_dma(torch.empty(4).data_ptr(), src.data_ptr(), 4, None))
+
+
+def test_double_buffered_solves_match_serial_solves():
+    """The serving pattern of the benchmark's e2e leg: problem k+1's A and b
+    are copied in by a copy engine on their own stream into the other of two
+    device buffers while problem k's three family solves (one-call API,
+    cached handles) run on three streams.  Every x equals the one a serial
+    copy-then-solve gives, byte for byte."""
+    p = W.problem_small()
+    n, d = p.A.shape
+    probs = [(p.A, p.b * (1.0 + 0.25 * k) + 0.01 * k) for k in range(4)]  # same A and sd, new right-hand sides
+    pins = [(A.contiguous().pin_memory(), b.contiguous().pin_memory()) for A, b in probs]
+    fams = ["gaussian", "countsketch", "srht"]
+
+    def serial(A, b, f):
+        x, _ = mihs.solve(A.to(DEV), b.to(DEV), p.lam, f, p.m, p.sd, seed=11, want_info=False, tol=1e-6,
+                          max_outer=100)
+        return x.clone()
+
+    ref = [[serial(A, b, f) for f in fams] for A, b in probs]
+    torch.cuda.synchronize()  # the handles move to other streams below
+    A_dev = [torch.empty(n, d, device=DEV) for _ in range(2)]
+    b_dev = [torch.empty(n, device=DEV) for _ in range(2)]
+    cs = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in fams]
+    free = [[], []]
+    outs = []
+    for rep in range(2):
+        for k, (Ap, bp) in enumerate(pins):
+            q = (4 * rep + k) % 2
+            for e in free[q]:
+                cs.wait_event(e)
+            mihs.copy_to_device(A_dev[q], Ap, stream=cs, engine="dma")
+            mihs.copy_to_device(b_dev[q], bp, stream=cs, engine="dma")
+            ready = torch.cuda.Event()
+            ready.record(cs)
+            done, xs = [], []
+            for f, st in zip(fams, streams):
+                st.wait_event(ready)
+                with torch.cuda.stream(st):
+                    x, _ = mihs.solve(A_dev[q], b_dev[q], p.lam, f, p.m, p.sd, seed=11, want_info=False,
+                                      tol=1e-6, max_outer=100)
+                    xs.append(x.clone())
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    done.append(ev)
+            free[q] = done
+            outs.append((k, xs))
+    torch.cuda.synchronize()
+    assert mihs.device_status() == 0
+    for k, xs in outs:
+        for f, x, r in zip(fams, xs, ref[k]):
+            assert torch.equal(x, r), (k, f)
