@@ -372,8 +372,13 @@ mihs_opts mihs_default_opts(void);
  * The outer loop runs on the device: a CUDA graph with a conditional WHILE
  * node (body: gradient A-pass, partial-sum reduce, AAb_Solver + heavy ball)
  * that the AAb kernel stops when the test fires, so a solve costs one graph
- * launch plus two small launches.  The graph is cached in the handle and
- * rebuilt when A, lda, b, x, λ, α, β, eps_sub or max_inner change.  Setting
+ * launch plus two small launches.  Up to eight graphs per kind of solve are
+ * cached in the handle, keyed by A, lda, b, x, λ, α, β, eps_sub and
+ * max_inner and replaced least recently used, so that solves alternating
+ * between input buffers or cycling through a few λ relaunch cached graphs.
+ * A replaced graph is kept until the handle is destroyed (or until 64 have
+ * gathered, when they are freed together, which waits for the GPU):
+ * destroying an executable graph waits for the work in flight.  Setting
  * the environment variable MIHS_NO_GRAPH makes the host drive the steps.
  *   A     n×d (same n, d as the handle), leading dimension lda.
  *   b     n-vector.  0 < λ ≤ FLT_MAX (AAb_Solver computes in fp32).
