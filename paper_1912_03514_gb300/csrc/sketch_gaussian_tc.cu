@@ -438,7 +438,7 @@ gauss_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const GaussTcArgs a)
       const int s = kb % NSTAGE;
       const uint32_t ph = (uint32_t)(kb / NSTAGE) & 1u;
       if (kb >= NSTAGE) {
-        // One thread waits (bounded) and every generator takes its verdict, so
+        // One thread waits (bounded) and every generator takes its decision, so
         // that all of them reach the same named barriers.
         if (g == 0) *gen_abort = mbar_wait(&empty[s], ph ^ 1u, kWaitLimitNs) ? 0u : 1u;
         named_sync(1, kGenWarps * 32);

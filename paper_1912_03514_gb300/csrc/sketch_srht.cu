@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kTThreads, 1) srht_tma_kernel(const __grid_con
       cur_slice = slice;
       named_sync(1, NT);
     }
-    // One thread waits (bounded) for the unit; every consumer takes its verdict.
+    // One thread waits (bounded) for the unit; every consumer takes its decision.
     if (tid == 0 && !mbar_wait(&full[q], (uint32_t)(j / kTNBuf) & 1u, kWaitLimitNs)) {
       atomicExch(&g_srht_error, MIHS_ERR_TIMEOUT);
       *abort_flag = 1u;
